@@ -1,0 +1,171 @@
+/*
+ * qram_sim.h -- C ABI of the B300 (sm_103a) trajectory simulator for
+ * amplitude-damped bucket-brigade QRAM queries with branch pruning.
+ *
+ * Method: Chen et al., "Classical simulation of amplitude-damped
+ * bucket-brigade quantum random access memories via predictable branch
+ * evolution" (arXiv 2609.34935).  Every call below names the passage that
+ * defines the operation it performs.
+ *
+ * Conventions shared by all calls
+ *   - Tree: nodes v = 0 .. 2^n - 2, layer l(v) = floor(log2(v + 1)),
+ *     children 2v+1 (left) and 2v+2 (right); each node has a router slot and
+ *     a data slot, site id = 2v + slot (0 = router, 1 = data), M = 2(2^n - 1)
+ *     sites (Sec. II.A).  The bit routed at layer l is address bit n-1-l
+ *     (most significant bit at the root; leaf ranges of Eq. (7)).
+ *   - Schedule: T = 6n + 2k slices; slices 1 .. T-1 carry gates, each
+ *     followed by one joint damping layer over all M sites (Sec. II.B).
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed
+ *     and counter (node or 0, slice | stream << 24, traj_lo, traj_hi);
+ *     stream 1 draws the candidate set of Theorem 3 (router site from words
+ *     0-1, data site from words 2-3, candidate iff the 64-bit word is below
+ *     floor(gamma 2^64)), stream 2 the auxiliary draw of each damping layer,
+ *     stream 3 the final tree measurement.  A trajectory is a pure function
+ *     of (seed, trajectory index, gamma).
+ *   - Memory: "host" pointers are read during the call only; "device"
+ *     pointers are CUDA global memory owned by the caller.  The library
+ *     owns only its scratch, allocated on the device of the simulator.
+ *   - Streams: every call is stream-ordered on the stream given at creation
+ *     (NULL = legacy default stream).  Calls return once work is enqueued,
+ *     except where stated; device-side failures are reported per trajectory
+ *     in qram_result_t.status and summarised by qram_sync().
+ *   - Errors: every int-returning call returns a QRAM_* code; no call
+ *     aborts the process or throws across this boundary.
+ */
+#ifndef QRAM_SIM_H
+#define QRAM_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    QRAM_OK = 0,
+    QRAM_E_ARG = 1,      /* invalid argument (sizes, gamma, duplicate address, norm) */
+    QRAM_E_OOM = 2,      /* device or host allocation failed */
+    QRAM_E_CUDA = 3,     /* a CUDA runtime call failed */
+    QRAM_E_TIMEOUT = 4,  /* a bounded device wait gave up */
+    QRAM_E_BUSY = 5,     /* server queue full / resource busy */
+    QRAM_E_CAP = 6,      /* a per-trajectory capacity was exceeded (result marked) */
+    QRAM_E_STATE = 7     /* call not valid in the current state */
+};
+
+enum { QRAM_QUTRIT = 0, QRAM_QUBIT = 1 };
+
+/* One QRAM query problem (Sec. II.A; input class of Sec. IV.D: a coherent
+ * superposition over addresses with one bus column per address). */
+typedef struct {
+    int32_t encoding;          /* QRAM_QUTRIT (Prop. 1) or QRAM_QUBIT (Theorems 1-2) */
+    int32_t n, k;              /* 1 <= k <= n <= 14, k <= 8 (the schedule needs k <= n) */
+    const uint8_t *memory;     /* host, 2^n cells; bit t of memory[i] is d_i^(t) (Eq. (1)) */
+    int32_t num_branches;      /* D, 1 <= D <= 2^n */
+    const uint32_t *addr;      /* host, D distinct addresses */
+    const uint32_t *bus;       /* host, D bus words < 2^k */
+    const double *amp_re;      /* host, D; sum |amp|^2 = 1 within 1e-12 */
+    const double *amp_im;      /* host, D */
+    uint64_t seed;             /* Philox key */
+    uint32_t sampler_version;  /* must be 1 (per-node Philox candidate draw) */
+} qram_problem_t;
+
+/* Per-trajectory result, written by qram_run_pruned / qram_run_full. */
+typedef struct {
+    double fidelity;            /* |<psi_id,0|psi>|^2/<psi_Q|psi_Q> if the sampled tree
+                                   configuration Q is the ground one, else 0 (App. C) */
+    double fidelity_unsampled;  /* |<psi_id,0|psi>|^2 / <psi|psi> */
+    double p_ground;            /* probability of the ground tree configuration */
+    uint32_t bad;               /* B: input branches in the bad union R (Algorithm 1) */
+    int32_t ref;                /* reference branch = first good branch, -1 if none */
+    uint32_t ncand;             /* candidate sites drawn over all slices */
+    uint32_t explicit_comps;    /* components evolved explicitly */
+    uint16_t jumps;             /* damping layers whose joint outcome J was non-empty */
+    uint16_t first_jump_slice;  /* slice of the first non-empty J, 0 if none */
+    uint16_t jump_sites;        /* sum of |J| */
+    uint8_t q_ground;           /* 1 if the sampled Q is the ground configuration */
+    uint8_t status;             /* QRAM_OK or a QRAM_E_* code for this trajectory */
+} qram_result_t;
+
+typedef struct qram_sim qram_sim_t;
+
+/* Create a simulator for one problem on CUDA device `device`, stream
+ * `cuda_stream` (a cudaStream_t, may be NULL).  Inputs are validated
+ * (QRAM_E_ARG) and copied to the device; the caller keeps ownership of the
+ * host arrays.  On success *out owns device memory until qram_sim_destroy. */
+int qram_sim_create(const qram_problem_t *problem, int device, void *cuda_stream, qram_sim_t **out);
+
+/* Release everything the simulator owns (waits for its stream). */
+void qram_sim_destroy(qram_sim_t *sim);
+
+/* Candidate sampling and classification only (Algorithm 1, steps 1-2;
+ * Theorem 3 step 1; Eq. (7) qutrit, Eq. (9) qubit).  For trajectories
+ * traj0 .. traj0 + ntraj - 1 with damping rates gamma[t] (device, ntraj):
+ *   cand[t * cap + c]  (device, ntraj * cap) packed (slice << 16) | site, in
+ *                      increasing (slice, site) order;
+ *   ncand[t]           (device) number of candidates (may exceed cap: then
+ *                      only cap are written and status is QRAM_E_CAP);
+ *   bad_bits[t * W + w] (device, W = ceil(2^n / 32)) bit a of the bitmap is
+ *                      set iff address a is in the bad union R;
+ *   bad[t], ref[t]     (device) B and the reference branch index (-1: none).
+ * Returns QRAM_E_ARG for gamma outside [0, 1) (checked on the device: the
+ * affected trajectory gets ncand = 0xFFFFFFFF). */
+int qram_sample_faults(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double *gamma,
+                       uint32_t cap, uint32_t *cand, uint32_t *ncand, uint32_t *bad_bits,
+                       uint32_t *bad, int32_t *ref);
+
+/* Pruned simulation (Algorithm 1): bad branches plus the reference branch
+ * are evolved explicitly with the joint damping sampler of Sec. IV.D; the
+ * good branches enter the mask weights (Eq. (18)) and the final state
+ * through their closed forms (Prop. 1, Eq. (8); Theorem 2, Eq. (14)), and
+ * are annihilated once a non-empty jump fires (Sec. V.A).  gamma: device,
+ * ntraj values in [0, 1); out: device, ntraj results. */
+int qram_run_pruned(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double *gamma,
+                    qram_result_t *out);
+
+/* Full simulation: every branch evolved explicitly from the same noise
+ * history (the comparison mode of Sec. V.A).  Same arguments. */
+int qram_run_full(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double *gamma,
+                  qram_result_t *out);
+
+/* Test hook (fixed noise histories of Sec. V.A): while set, trajectory
+ * traj0 + t of the next runs takes its candidate set from
+ * cand[off[t] .. off[t+1]) (device, packed as in qram_sample_faults, sorted)
+ * instead of the FAULT stream, for t < nhist; the auxiliary and final draws
+ * still come from the Philox streams.  Pass nhist = 0 to clear.  The arrays
+ * must stay valid while the hook is set. */
+int qram_set_fault_history(qram_sim_t *sim, uint32_t nhist, const uint32_t *cand, const uint32_t *off);
+
+/* Ensemble mean and standard error of results[0 .. ntraj).fidelity
+ * (device array), reduced on the device in a fixed order; blocks until the
+ * two host doubles are written. */
+int qram_fidelity(qram_sim_t *sim, const qram_result_t *results, uint32_t ntraj, double *mean,
+                  double *stderr_out);
+
+/* Final normalised state of one trajectory (parity checks, Sec. V.A
+ * "matching their complete complex amplitudes"): every explicitly evolved
+ * component after the second Hadamard wall plus, in pruned mode, the
+ * predicted good branches.  Host outputs, capacity cap entries:
+ * addr[c], bus[c], config_hash[c] (64-bit hash of the sorted excited-site
+ * list, 0 for the ground configuration), re[c], im[c]; *count receives the
+ * number of entries (QRAM_E_CAP if it exceeds cap).  mode: 0 pruned, 1 full.
+ * Blocks until done. */
+int qram_dump_state(qram_sim_t *sim, int mode, uint64_t traj, double gamma, uint32_t cap,
+                    uint32_t *addr, uint32_t *bus, uint64_t *config_hash, double *re, double *im,
+                    uint32_t *count);
+
+/* Waits for the simulator's stream; returns QRAM_E_CUDA on an asynchronous
+ * CUDA error, else QRAM_OK. */
+int qram_sync(qram_sim_t *sim);
+
+/* Number of kernel launches issued by this simulator since creation. */
+uint64_t qram_launch_count(const qram_sim_t *sim);
+
+/* Static message for a QRAM_* code. */
+const char *qram_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QRAM_SIM_H */

@@ -1,0 +1,219 @@
+"""B300 (sm_103a) trajectory simulator for amplitude-damped bucket-brigade QRAM
+with branch pruning (arXiv 2609.34935).
+
+This module is a thin ctypes binding over the C ABI of ``include/qram_sim.h``
+(shared library ``libqram_b300.so``, built by ``build.py``).  It only
+marshals arguments: every step of the simulation runs in the CUDA kernels.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if
+the library is missing or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["QramSim", "RESULT_DTYPE", "QramError", "load_library", "QUTRIT", "QUBIT"]
+
+QUTRIT, QUBIT = 0, 1
+OK = 0
+ERRORS = {1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_TIMEOUT", 5: "E_BUSY", 6: "E_CAP", 7: "E_STATE"}
+
+RESULT_DTYPE = np.dtype([("fidelity", "<f8"), ("fidelity_unsampled", "<f8"), ("p_ground", "<f8"),
+                         ("bad", "<u4"), ("ref", "<i4"), ("ncand", "<u4"), ("explicit_comps", "<u4"),
+                         ("jumps", "<u2"), ("first_jump_slice", "<u2"), ("jump_sites", "<u2"),
+                         ("q_ground", "u1"), ("status", "u1")])
+assert RESULT_DTYPE.itemsize == 48
+
+
+class QramError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ERRORS.get(code, code)}")
+        self.code = code
+
+
+class _Problem(C.Structure):
+    _fields_ = [("encoding", C.c_int32), ("n", C.c_int32), ("k", C.c_int32), ("memory", C.c_void_p),
+                ("num_branches", C.c_int32), ("addr", C.c_void_p), ("bus", C.c_void_p),
+                ("amp_re", C.c_void_p), ("amp_im", C.c_void_p), ("seed", C.c_uint64),
+                ("sampler_version", C.c_uint32)]
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libqram_b300.so (building it with nvcc when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        try:
+            path = _build.build()
+        except Exception as e:  # pragma: no cover
+            if not os.path.exists(path):
+                raise RuntimeError(f"cannot build {path}: {e}") from e
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} missing: run `python -m paper_2609_34935_b300.build`")
+    L = C.CDLL(path)
+    vp, u32, u64, i32, f64 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_double
+    L.qram_sim_create.argtypes = [vp, C.c_int, vp, C.POINTER(vp)]
+    L.qram_sim_destroy.argtypes = [vp]
+    L.qram_sim_destroy.restype = None
+    L.qram_sample_faults.argtypes = [vp, u64, u32, vp, u32, vp, vp, vp, vp, vp]
+    L.qram_run_pruned.argtypes = [vp, u64, u32, vp, vp]
+    L.qram_run_full.argtypes = [vp, u64, u32, vp, vp]
+    L.qram_set_fault_history.argtypes = [vp, u32, vp, vp]
+    L.qram_fidelity.argtypes = [vp, vp, u32, C.POINTER(f64), C.POINTER(f64)]
+    L.qram_dump_state.argtypes = [vp, C.c_int, u64, f64, u32, vp, vp, vp, vp, vp, C.POINTER(u32)]
+    L.qram_sync.argtypes = [vp]
+    L.qram_launch_count.argtypes = [vp]
+    L.qram_launch_count.restype = u64
+    L.qram_strerror.argtypes = [C.c_int]
+    L.qram_strerror.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise QramError(rc, what)
+
+
+def _dptr(t) -> int:
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+    return t.data_ptr()
+
+
+class QramSim:
+    """One QRAM problem resident on a CUDA device.
+
+    ``problem`` needs ``encoding, n, k, memory, addr, bus, amp`` (numpy);
+    ``seed`` keys the Philox streams."""
+
+    def __init__(self, problem, seed: int, device: int = 0, stream=None):
+        import torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("QramSim needs a CUDA device (no CPU fallback)")
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.problem = problem
+        self.n, self.k, self.encoding = int(problem.n), int(problem.k), int(problem.encoding)
+        mem = np.ascontiguousarray(problem.memory, dtype=np.uint8)
+        addr = np.ascontiguousarray(problem.addr, dtype=np.uint32)
+        bus = np.ascontiguousarray(problem.bus, dtype=np.uint32)
+        amp = np.asarray(problem.amp, dtype=np.complex128)
+        re = np.ascontiguousarray(amp.real)
+        im = np.ascontiguousarray(amp.imag)
+        p = _Problem(self.encoding, self.n, self.k, mem.ctypes.data, len(addr), addr.ctypes.data,
+                     bus.ctypes.data, re.ctypes.data, im.ctypes.data, int(seed) & (2 ** 64 - 1), 1)
+        h = C.c_void_p()
+        _check(self.lib.qram_sim_create(C.byref(p), device, self.stream.cuda_stream, C.byref(h)), "qram_sim_create")
+        self.h = h
+        self._hist = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qram_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def D(self) -> int:
+        return int(len(self.problem.addr))
+
+    def _gam(self, gammas):
+        import torch
+        g = torch.as_tensor(gammas, dtype=torch.float64)
+        if not g.is_cuda:
+            g = g.to(f"cuda:{self.device}")
+        return g.contiguous()
+
+    def run(self, mode: str, traj0: int, gammas, out=None):
+        """Launch trajectories traj0..traj0+len(gammas)-1; returns a uint8
+        device tensor [ntraj, 48] (layout RESULT_DTYPE)."""
+        import torch
+        g = self._gam(gammas)
+        nt = g.numel()
+        if out is None:
+            out = torch.empty((nt, RESULT_DTYPE.itemsize), dtype=torch.uint8, device=g.device)
+        fn = self.lib.qram_run_pruned if mode == "pruned" else self.lib.qram_run_full
+        _check(fn(self.h, traj0, nt, _dptr(g), _dptr(out)), f"qram_run_{mode}")
+        return out
+
+    def run_pruned(self, traj0: int, gammas, out=None):
+        return self.run("pruned", traj0, gammas, out)
+
+    def run_full(self, traj0: int, gammas, out=None):
+        return self.run("full", traj0, gammas, out)
+
+    @staticmethod
+    def results(raw) -> np.ndarray:
+        """Copy a result tensor to the host as a structured numpy array."""
+        return raw.cpu().numpy().view(RESULT_DTYPE).reshape(-1)
+
+    def sample_faults(self, traj0: int, gammas, cap: int = 1 << 14):
+        import torch
+        g = self._gam(gammas)
+        nt = g.numel()
+        W = ((1 << self.n) + 31) // 32
+        dev = g.device
+        cand = torch.zeros((nt, cap), dtype=torch.int32, device=dev)
+        ncand = torch.zeros(nt, dtype=torch.int32, device=dev)
+        bits = torch.zeros((nt, W), dtype=torch.int32, device=dev)
+        bad = torch.zeros(nt, dtype=torch.int32, device=dev)
+        ref = torch.zeros(nt, dtype=torch.int32, device=dev)
+        _check(self.lib.qram_sample_faults(self.h, traj0, nt, _dptr(g), cap, _dptr(cand), _dptr(ncand),
+                                           _dptr(bits), _dptr(bad), _dptr(ref)), "qram_sample_faults")
+        return dict(cand=cand, ncand=ncand, bad_bits=bits, bad=bad, ref=ref)
+
+    def set_fault_history(self, cand=None, off=None):
+        """cand: int32 device tensor of packed (slice << 16 | site); off: int32 [nhist+1]."""
+        if cand is None:
+            _check(self.lib.qram_set_fault_history(self.h, 0, None, None), "qram_set_fault_history")
+            self._hist = None
+            return
+        self._hist = (cand, off)          # keep alive while set
+        _check(self.lib.qram_set_fault_history(self.h, off.numel() - 1, _dptr(cand), _dptr(off)),
+               "qram_set_fault_history")
+
+    def fidelity(self, raw):
+        m, s = C.c_double(), C.c_double()
+        _check(self.lib.qram_fidelity(self.h, _dptr(raw), raw.shape[0], C.byref(m), C.byref(s)), "qram_fidelity")
+        return m.value, s.value
+
+    def dump_state(self, mode: str, traj: int, gamma: float, cap: int = 1 << 18):
+        while True:
+            addr = np.zeros(cap, np.uint32)
+            bus = np.zeros(cap, np.uint32)
+            hsh = np.zeros(cap, np.uint64)
+            re = np.zeros(cap, np.float64)
+            im = np.zeros(cap, np.float64)
+            cnt = C.c_uint32(0)
+            rc = self.lib.qram_dump_state(self.h, 0 if mode == "pruned" else 1, traj, gamma, cap,
+                                          addr.ctypes.data, bus.ctypes.data, hsh.ctypes.data, re.ctypes.data,
+                                          im.ctypes.data, C.byref(cnt))
+            if rc == 6 and cnt.value > cap:
+                cap = cnt.value + 16
+                continue
+            _check(rc, "qram_dump_state")
+            m = cnt.value
+            return addr[:m], bus[:m], hsh[:m], re[:m] + 1j * im[:m]
+
+    def sync(self):
+        _check(self.lib.qram_sync(self.h), "qram_sync")
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.qram_launch_count(self.h))

@@ -1,0 +1,432 @@
+// qram_api.cu -- host implementation of the C ABI declared in include/qram_sim.h.
+//
+// Owns the device copies of a problem, builds the slice gate table of the
+// time-sliced bucket-brigade schedule (Sec. II.A, Eqs. (2)-(4); App. C gate
+// list), sizes the per-CTA scratch and launches the kernels of
+// qram_kernels.cu.  No CPU computation of the method happens here.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "qram_internal.h"
+
+using namespace qram;
+
+struct qram_sim {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int enc = 0, n = 0, k = 0, D = 0, T = 0;
+    uint64_t seed = 0;
+    uint8_t *d_mem = nullptr;
+    uint32_t *d_addr = nullptr, *d_bus = nullptr;
+    double *d_re = nullptr, *d_im = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    Scratch scr{};
+    int slots = 0;
+    uint32_t *d_work = nullptr;
+    double *d_fid2 = nullptr;
+    double *d_gmax = nullptr;
+    const uint32_t *hist_cand = nullptr, *hist_off = nullptr;
+    uint32_t nhist = 0;
+    SliceOps ops[kMaxT]{};
+    uint64_t launches = 0;
+    int sms = 0, blocks_per_sm = 0;
+};
+
+namespace {
+
+bool ok(cudaError_t e) { return e == cudaSuccess; }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+// Slot bookkeeping for the disjointness check of one slice: tree sites,
+// then address bits, then bus qubits.
+struct SlotUse {
+    std::vector<uint8_t> used;
+    bool take(size_t s) { if (used[s]) return false; used[s] = 1; return true; }
+};
+
+// Schedule of Sec. II.A: address bit l (routed at layer l) enters d_0 at
+// 2l+1, walks down one layer per slice, settles in the router of layer l at
+// 3l+2 and returns along the mirror image s -> T-s; data qubit t enters at
+// 2n+2t+1, is fetched at the leaf layer at 3n+2t+1 and leaves at 4n+2t+1.
+int build_ops(int n, int k, SliceOps *ops) {
+    const int T = 6 * n + 2 * k;
+    for (int s = 0; s < kMaxT; ++s) { ops[s].load = -1; ops[s].bus = -1; ops[s].fetch = -1; ops[s].pad = 0; ops[s].iswap = 0; ops[s].cswap = 0; }
+    auto set8 = [](int8_t &f, int v) { if (f >= 0 && f != v) return false; f = (int8_t)v; return true; };
+    for (int l = 0; l < n; ++l) {
+        if (!set8(ops[2 * l + 1].load, l) || !set8(ops[T - 2 * l - 1].load, l)) return QRAM_E_ARG;
+        for (int m = 1; m <= l; ++m) {
+            ops[2 * l + 1 + m].cswap |= 1u << (m - 1);
+            ops[T - 2 * l - 1 - m].cswap |= 1u << (m - 1);
+        }
+        ops[3 * l + 2].iswap |= 1u << l;
+        ops[T - 3 * l - 2].iswap |= 1u << l;
+    }
+    for (int t = 0; t < k; ++t) {
+        if (!set8(ops[2 * n + 2 * t + 1].bus, t) || !set8(ops[4 * n + 2 * t + 1].bus, t)) return QRAM_E_ARG;
+        for (int m = 1; m <= n - 1; ++m) {
+            ops[2 * n + 2 * t + 1 + m].cswap |= 1u << (m - 1);
+            ops[3 * n + 2 * t + 1 + m].cswap |= 1u << (n - 1 - m);
+        }
+        if (!set8(ops[3 * n + 2 * t + 1].fetch, t)) return QRAM_E_ARG;
+    }
+    // every gate of a slice must act on its own slots (controls included)
+    const size_t M = 2 * ((size_t(1) << n) - 1);
+    SlotUse U;
+    for (int s = 1; s < T; ++s) {
+        U.used.assign(M + n + k, 0);
+        const SliceOps &o = ops[s];
+        if (o.load >= 0 && o.bus >= 0) return QRAM_E_ARG;      // both need d_0
+        if (o.load >= 0 && (!U.take(1) || !U.take(M + o.load))) return QRAM_E_ARG;
+        if (o.bus >= 0 && (!U.take(1) || !U.take(M + n + o.bus))) return QRAM_E_ARG;
+        for (int L = 0; L < n; ++L) {
+            const size_t lo = (size_t(1) << L) - 1, hi = (size_t(2) << L) - 1;
+            if ((o.iswap >> L) & 1u)
+                for (size_t v = lo; v < hi; ++v) if (!U.take(2 * v) || !U.take(2 * v + 1)) return QRAM_E_ARG;
+            if ((o.cswap >> L) & 1u) {
+                if (L + 1 >= n) return QRAM_E_ARG;
+                for (size_t v = lo; v < hi; ++v)
+                    if (!U.take(2 * v) || !U.take(2 * v + 1) || !U.take(2 * (2 * v + 1) + 1) || !U.take(2 * (2 * v + 2) + 1))
+                        return QRAM_E_ARG;
+            }
+        }
+        if (o.fetch >= 0)
+            for (size_t v = (size_t(1) << (n - 1)) - 1; v < (size_t(1) << n) - 1; ++v)
+                if (!U.take(2 * v) || !U.take(2 * v + 1)) return QRAM_E_ARG;
+    }
+    return QRAM_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// per-slot candidate capacities for a damping-rate bound gmax: mean + 12 sigma
+void cand_caps(int n, int k, double gmax, uint32_t *cand_cap, uint32_t *seg_cap) {
+    const int NWARP = kernel_threads() / 32;
+    const double items = (double)(6 * n + 2 * k - 1) * (double)((1u << n) - 1);
+    const double per = std::ceil(items / NWARP);
+    auto cap = [&](double m) {
+        const double p = std::min(1.0, std::max(gmax, 0.0));
+        const double mean = 2.0 * m * p, sd = std::sqrt(2.0 * m * p * (1.0 - p) + 1.0);
+        double c = mean + 12.0 * sd + 64.0;
+        c = std::min(c, 2.0 * m + 64.0);
+        return (uint32_t)(std::ceil(c / 32.0) * 32.0);
+    };
+    *cand_cap = cap(items);
+    *seg_cap = cap(per);
+}
+
+int ensure_scratch(qram_sim *S, double gmax) {
+    uint32_t cc, sc;
+    cand_caps(S->n, S->k, gmax, &cc, &sc);
+    const uint32_t ecap = (uint32_t)S->D << (S->enc == QRAM_QUBIT ? S->k : 0);
+    if (S->scratch && S->scr.cand_cap >= cc && S->scr.seg_cap >= sc && S->scr.ecap >= ecap) return QRAM_OK;
+    if (S->scratch) { cudaFree(S->scratch); S->scratch = nullptr; }
+    const int NWARP = kernel_threads() / 32;
+    const size_t slots = (size_t)S->slots;
+    size_t off = 0;
+    const size_t o_cand = off; off = align_up(off + slots * cc * 4);
+    const size_t o_seg = off; off = align_up(off + slots * NWARP * (size_t)sc * 4);
+    const size_t o_expl = off; off = align_up(off + slots * (size_t)S->D * 4);
+    const size_t o_pw = off; off = align_up(off + slots * (size_t)ecap * 4);
+    const size_t o_pwR = off; off = align_up(off + slots * (size_t)ecap * 4);
+    const size_t o_ex = off; off = align_up(off + slots * (size_t)ecap * 4);
+    const size_t o_lab = off; off = align_up(off + slots * (size_t)ecap * 4);
+    const size_t o_st = off; off = align_up(off + slots * (size_t)ecap * 4);
+    const size_t o_exc = off; off = align_up(off + slots * (size_t)ecap * kXcap * 2);
+    void *p = nullptr;
+    if (!ok(cudaMalloc(&p, off))) { cudaGetLastError(); return QRAM_E_OOM; }
+    char *b = (char *)p;
+    S->scratch = p;
+    S->scratch_bytes = off;
+    S->scr.cand = (uint32_t *)(b + o_cand);
+    S->scr.wseg = (uint32_t *)(b + o_seg);
+    S->scr.expl = (uint32_t *)(b + o_expl);
+    S->scr.pw = (uint32_t *)(b + o_pw);
+    S->scr.pwR = (uint32_t *)(b + o_pwR);
+    S->scr.ex = (int32_t *)(b + o_ex);
+    S->scr.lab = (uint32_t *)(b + o_lab);
+    S->scr.st = (uint32_t *)(b + o_st);
+    S->scr.exc = (uint16_t *)(b + o_exc);
+    S->scr.cand_cap = cc;
+    S->scr.seg_cap = sc;
+    S->scr.ecap = ecap;
+    return QRAM_OK;
+}
+
+__global__ void gmax_kernel(const double *g, uint32_t n, double *out) {
+    __shared__ double m[256];
+    double x = 0.0;
+    for (uint32_t i = threadIdx.x; i < n; i += 256) { const double v = g[i]; if (!(v <= x)) x = v; }
+    m[threadIdx.x] = x;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) { const double v = m[threadIdx.x + s]; if (!(v <= m[threadIdx.x])) m[threadIdx.x] = v; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = m[0];
+}
+
+Params base_params(qram_sim *S) {
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.enc = S->enc; P.n = S->n; P.k = S->k; P.T = S->T; P.D = S->D;
+    P.nodes = (1 << S->n) - 1; P.M = 2 * P.nodes; P.nthreads = kernel_threads();
+    P.mem = S->d_mem; P.addr = S->d_addr; P.bus = S->d_bus; P.amp_re = S->d_re; P.amp_im = S->d_im;
+    P.seed = S->seed;
+    P.hist_cand = S->hist_cand; P.hist_off = S->hist_off; P.nhist = S->nhist;
+    P.scr = S->scr;
+    P.work = S->d_work;
+    std::memcpy(P.ops, S->ops, sizeof(P.ops));
+    return P;
+}
+
+int bound_gamma(qram_sim *S, const double *gamma, uint32_t ntraj, double *gmax) {
+    gmax_kernel<<<1, 256, 0, S->stream>>>(gamma, ntraj, S->d_gmax);
+    S->launches++;
+    if (!ok(cudaGetLastError())) return QRAM_E_CUDA;
+    double g = 0;
+    if (!ok(cudaMemcpyAsync(&g, S->d_gmax, sizeof(double), cudaMemcpyDeviceToHost, S->stream))) return QRAM_E_CUDA;
+    if (!ok(cudaStreamSynchronize(S->stream))) return QRAM_E_CUDA;
+    if (!(g >= 0.0 && g < 1.0)) g = 1.0;           // invalid rates are flagged per trajectory
+    *gmax = g;
+    return QRAM_OK;
+}
+
+int launch(qram_sim *S, Params &P, uint32_t ntraj) {
+    if (!ok(cudaMemsetAsync(S->d_work, 0, sizeof(uint32_t), S->stream))) return QRAM_E_CUDA;
+    const int grid = (int)std::min<uint32_t>((uint32_t)S->slots, std::max<uint32_t>(ntraj, 1u));
+    if (!ok(launch_trajectories(P, grid, kernel_threads(), 0, S->stream))) return QRAM_E_CUDA;
+    S->launches++;
+    return QRAM_OK;
+}
+
+int run_mode(qram_sim *S, int mode, uint64_t traj0, uint32_t ntraj, const double *gamma, qram_result_t *out) {
+    if (!S || !gamma || !out) return QRAM_E_ARG;
+    if (ntraj == 0) return QRAM_OK;
+    DeviceGuard g(S->device);
+    double gmax;
+    int rc = bound_gamma(S, gamma, ntraj, &gmax);
+    if (rc) return rc;
+    if ((rc = ensure_scratch(S, gmax))) return rc;
+    Params P = base_params(S);
+    P.traj0 = traj0; P.ntraj = ntraj; P.gamma = gamma; P.mode = mode; P.out = out;
+    return launch(S, P, ntraj);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qram_strerror(int code) {
+    switch (code) {
+    case QRAM_OK: return "ok";
+    case QRAM_E_ARG: return "invalid argument";
+    case QRAM_E_OOM: return "out of memory";
+    case QRAM_E_CUDA: return "CUDA runtime error";
+    case QRAM_E_TIMEOUT: return "bounded device wait timed out";
+    case QRAM_E_BUSY: return "busy";
+    case QRAM_E_CAP: return "per-trajectory capacity exceeded";
+    case QRAM_E_STATE: return "invalid state";
+    default: return "unknown error";
+    }
+}
+
+int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram_sim_t **out) {
+    if (!p || !out) return QRAM_E_ARG;
+    *out = nullptr;
+    if (p->encoding != QRAM_QUTRIT && p->encoding != QRAM_QUBIT) return QRAM_E_ARG;
+    if (p->n < 1 || p->n > kMaxN || p->k < 1 || p->k > kMaxK || p->k > p->n) return QRAM_E_ARG;
+    if (p->sampler_version != 1) return QRAM_E_ARG;
+    const uint32_t N = 1u << p->n;
+    if (p->num_branches < 1 || (uint32_t)p->num_branches > N) return QRAM_E_ARG;
+    if (!p->memory || !p->addr || !p->bus || !p->amp_re || !p->amp_im) return QRAM_E_ARG;
+    std::vector<uint8_t> seen(N, 0);
+    double nrm = 0.0;
+    for (int b = 0; b < p->num_branches; ++b) {
+        if (p->addr[b] >= N || seen[p->addr[b]]) return QRAM_E_ARG;    // one column per address
+        seen[p->addr[b]] = 1;
+        if (p->bus[b] >= (1u << p->k)) return QRAM_E_ARG;
+        if (!std::isfinite(p->amp_re[b]) || !std::isfinite(p->amp_im[b])) return QRAM_E_ARG;
+        nrm += p->amp_re[b] * p->amp_re[b] + p->amp_im[b] * p->amp_im[b];
+    }
+    if (std::fabs(nrm - 1.0) > 1e-12) return QRAM_E_ARG;
+    for (uint32_t i = 0; i < N; ++i) if (p->memory[i] >= (1u << p->k)) return QRAM_E_ARG;
+
+    qram_sim *S = new (std::nothrow) qram_sim();
+    if (!S) return QRAM_E_OOM;
+    S->device = device;
+    S->stream = (cudaStream_t)cuda_stream;
+    S->enc = p->encoding; S->n = p->n; S->k = p->k; S->D = p->num_branches; S->T = 6 * p->n + 2 * p->k;
+    S->seed = p->seed;
+    if (build_ops(S->n, S->k, S->ops) != QRAM_OK) { delete S; return QRAM_E_ARG; }
+    DeviceGuard g(device);
+    int rc = QRAM_OK;
+    const size_t D = (size_t)S->D;
+    if (!ok(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, device))) { delete S; return QRAM_E_CUDA; }
+    S->blocks_per_sm = 2;
+    S->slots = S->sms * S->blocks_per_sm;
+    if (!ok(cudaMalloc(&S->d_mem, N)) || !ok(cudaMalloc(&S->d_addr, D * 4)) || !ok(cudaMalloc(&S->d_bus, D * 4)) ||
+        !ok(cudaMalloc(&S->d_re, D * 8)) || !ok(cudaMalloc(&S->d_im, D * 8)) ||
+        !ok(cudaMalloc(&S->d_work, 64)) || !ok(cudaMalloc(&S->d_fid2, 16)) || !ok(cudaMalloc(&S->d_gmax, 8))) {
+        cudaGetLastError();
+        qram_sim_destroy(S);
+        return QRAM_E_OOM;
+    }
+    if (!ok(cudaMemcpy(S->d_mem, p->memory, N, cudaMemcpyHostToDevice)) ||
+        !ok(cudaMemcpy(S->d_addr, p->addr, D * 4, cudaMemcpyHostToDevice)) ||
+        !ok(cudaMemcpy(S->d_bus, p->bus, D * 4, cudaMemcpyHostToDevice)) ||
+        !ok(cudaMemcpy(S->d_re, p->amp_re, D * 8, cudaMemcpyHostToDevice)) ||
+        !ok(cudaMemcpy(S->d_im, p->amp_im, D * 8, cudaMemcpyHostToDevice)))
+        rc = QRAM_E_CUDA;
+    if (rc) { qram_sim_destroy(S); return rc; }
+    *out = S;
+    return QRAM_OK;
+}
+
+void qram_sim_destroy(qram_sim_t *S) {
+    if (!S) return;
+    {
+        DeviceGuard g(S->device);
+        if (S->stream) cudaStreamSynchronize(S->stream); else cudaDeviceSynchronize();
+        cudaFree(S->d_mem); cudaFree(S->d_addr); cudaFree(S->d_bus); cudaFree(S->d_re); cudaFree(S->d_im);
+        cudaFree(S->d_work); cudaFree(S->d_fid2); cudaFree(S->d_gmax);
+        if (S->scratch) cudaFree(S->scratch);
+        cudaGetLastError();
+    }
+    delete S;
+}
+
+int qram_sample_faults(qram_sim_t *S, uint64_t traj0, uint32_t ntraj, const double *gamma, uint32_t cap,
+                       uint32_t *cand, uint32_t *ncand, uint32_t *bad_bits, uint32_t *bad, int32_t *ref) {
+    if (!S || !gamma || !cand || !ncand || !bad_bits || !bad || !ref) return QRAM_E_ARG;
+    if (ntraj == 0) return QRAM_OK;
+    DeviceGuard g(S->device);
+    double gmax;
+    int rc = bound_gamma(S, gamma, ntraj, &gmax);
+    if (rc) return rc;
+    if ((rc = ensure_scratch(S, gmax))) return rc;
+    Params P = base_params(S);
+    P.traj0 = traj0; P.ntraj = ntraj; P.gamma = gamma; P.mode = kSampleOnly;
+    P.o_cand = cand; P.o_ncand = ncand; P.o_badbits = bad_bits; P.o_bad = bad; P.o_ref = ref; P.o_cap = cap;
+    return launch(S, P, ntraj);
+}
+
+int qram_run_pruned(qram_sim_t *S, uint64_t traj0, uint32_t ntraj, const double *gamma, qram_result_t *out) {
+    return run_mode(S, kPruned, traj0, ntraj, gamma, out);
+}
+
+int qram_run_full(qram_sim_t *S, uint64_t traj0, uint32_t ntraj, const double *gamma, qram_result_t *out) {
+    return run_mode(S, kFull, traj0, ntraj, gamma, out);
+}
+
+int qram_set_fault_history(qram_sim_t *S, uint32_t nhist, const uint32_t *cand, const uint32_t *off) {
+    if (!S) return QRAM_E_ARG;
+    if (nhist > 0 && (!cand || !off)) return QRAM_E_ARG;
+    S->nhist = nhist;
+    S->hist_cand = nhist ? cand : nullptr;
+    S->hist_off = nhist ? off : nullptr;
+    return QRAM_OK;
+}
+
+int qram_fidelity(qram_sim_t *S, const qram_result_t *res, uint32_t ntraj, double *mean, double *se) {
+    if (!S || !res || !mean || !se) return QRAM_E_ARG;
+    DeviceGuard g(S->device);
+    if (!ok(launch_fidelity(res, ntraj, S->d_fid2, S->stream))) return QRAM_E_CUDA;
+    S->launches++;
+    double h[2];
+    if (!ok(cudaMemcpyAsync(h, S->d_fid2, 16, cudaMemcpyDeviceToHost, S->stream))) return QRAM_E_CUDA;
+    if (!ok(cudaStreamSynchronize(S->stream))) return QRAM_E_CUDA;
+    *mean = h[0];
+    *se = h[1];
+    return QRAM_OK;
+}
+
+int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32_t cap, uint32_t *addr,
+                    uint32_t *bus, uint64_t *hash, double *re, double *im, uint32_t *count) {
+    if (!S || !count || (mode != 0 && mode != 1) || !(gamma >= 0.0 && gamma < 1.0)) return QRAM_E_ARG;
+    if (cap && (!addr || !bus || !hash || !re || !im)) return QRAM_E_ARG;
+    DeviceGuard g(S->device);
+    int rc = ensure_scratch(S, gamma);
+    if (rc) return rc;
+    const uint32_t ecap = S->scr.ecap;
+    const uint32_t W = ((1u << S->n) + 31u) >> 5;
+    const uint32_t ocap = ecap * 2 + ((uint32_t)S->D << S->k) + 16;
+    // one device block: gamma, dump buffers, outputs
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    const size_t o_g = take(8), o_cnt = take(8), o_scal = take(32), o_col = take(ecap * 4ull), o_bus = take(ecap * 4ull),
+                 o_hash = take(ecap * 8ull), o_re = take(ecap * 8ull), o_im = take(ecap * 8ull), o_bb = take(W * 4ull),
+                 o_ref = take(8), o_res = take(sizeof(qram_result_t)), o_n = take(8), o_oa = take(ocap * 4ull),
+                 o_ob = take(ocap * 4ull), o_oh = take(ocap * 8ull), o_ore = take(ocap * 8ull), o_oim = take(ocap * 8ull);
+    char *b = nullptr;
+    if (!ok(cudaMalloc((void **)&b, off))) { cudaGetLastError(); return QRAM_E_OOM; }
+    rc = QRAM_OK;
+    do {
+        if (!ok(cudaMemsetAsync(b, 0, off, S->stream))) { rc = QRAM_E_CUDA; break; }
+        if (!ok(cudaMemcpyAsync(b + o_g, &gamma, 8, cudaMemcpyHostToDevice, S->stream))) { rc = QRAM_E_CUDA; break; }
+        Params P = base_params(S);
+        P.traj0 = traj; P.ntraj = 1; P.gamma = (const double *)(b + o_g);
+        P.mode = mode == 0 ? kPruned : kFull;
+        P.out = (qram_result_t *)(b + o_res);
+        P.dump_mode = 1;
+        P.dump.col = (uint32_t *)(b + o_col); P.dump.bus = (uint32_t *)(b + o_bus); P.dump.hash = (uint64_t *)(b + o_hash);
+        P.dump.re = (double *)(b + o_re); P.dump.im = (double *)(b + o_im); P.dump.cap = ecap;
+        P.dump.count = (uint32_t *)(b + o_cnt); P.dump.scal = (double *)(b + o_scal);
+        P.o_badbits = (uint32_t *)(b + o_bb); P.o_ref = (int32_t *)(b + o_ref);
+        if ((rc = launch(S, P, 1))) break;
+        uint32_t nin = 0;
+        if (!ok(cudaMemcpyAsync(&nin, b + o_cnt, 4, cudaMemcpyDeviceToHost, S->stream)) ||
+            !ok(cudaStreamSynchronize(S->stream))) { rc = QRAM_E_CUDA; break; }
+        if (nin > ecap) { rc = QRAM_E_CAP; break; }
+        if (!ok(launch_dump_finalize(P, nin, (uint32_t *)(b + o_n), ocap, (uint32_t *)(b + o_oa), (uint32_t *)(b + o_ob),
+                                     (uint64_t *)(b + o_oh), (double *)(b + o_ore), (double *)(b + o_oim), S->stream))) {
+            rc = QRAM_E_CUDA; break;
+        }
+        S->launches++;
+        uint32_t nout = 0;
+        if (!ok(cudaMemcpyAsync(&nout, b + o_n, 4, cudaMemcpyDeviceToHost, S->stream)) ||
+            !ok(cudaStreamSynchronize(S->stream))) { rc = QRAM_E_CUDA; break; }
+        *count = nout;
+        const uint32_t m = std::min(nout, std::min(cap, ocap));
+        if (m) {
+            if (!ok(cudaMemcpyAsync(addr, b + o_oa, m * 4ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(bus, b + o_ob, m * 4ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(hash, b + o_oh, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(re, b + o_ore, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(im, b + o_oim, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaStreamSynchronize(S->stream))) { rc = QRAM_E_CUDA; break; }
+        }
+        qram_result_t R;
+        if (!ok(cudaMemcpy(&R, b + o_res, sizeof(R), cudaMemcpyDeviceToHost))) { rc = QRAM_E_CUDA; break; }
+        if (R.status != QRAM_OK) { rc = R.status; break; }
+        if (nout > cap || nout > ocap) rc = QRAM_E_CAP;
+    } while (0);
+    cudaFree(b);
+    return rc;
+}
+
+int qram_sync(qram_sim_t *S) {
+    if (!S) return QRAM_E_ARG;
+    DeviceGuard g(S->device);
+    if (!ok(S->stream ? cudaStreamSynchronize(S->stream) : cudaDeviceSynchronize())) return QRAM_E_CUDA;
+    if (!ok(cudaGetLastError())) return QRAM_E_CUDA;
+    return QRAM_OK;
+}
+
+uint64_t qram_launch_count(const qram_sim_t *S) { return S ? S->launches : 0; }
+
+}  // extern "C"

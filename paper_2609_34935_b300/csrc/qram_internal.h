@@ -1,0 +1,85 @@
+// qram_internal.h -- launch parameters shared by the host API and the kernels
+// of the sm_103a trajectory simulator.  Not part of the C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qram_sim.h"
+
+namespace qram {
+
+constexpr int kMaxN = 14;
+constexpr int kMaxK = 8;
+constexpr int kMaxT = 6 * kMaxN + 2 * kMaxK;   // 100
+constexpr int kXcap = 32;                      // off-path excitations per component
+constexpr int kMaxJ = 64;                      // elements of one joint outcome J
+
+enum Mode : int { kPruned = 0, kFull = 1, kSampleOnly = 2 };
+
+// Gates of one time slice (Sec. II.A; App. C).  All act on disjoint slots.
+struct SliceOps {
+    int8_t load;     // address bit routed at layer `load` is copied into / out of d_0, -1: none
+    int8_t bus;      // bus qubit swapped with d_0, -1: none
+    int8_t fetch;    // data qubit fetched at the leaf layer, -1: none
+    int8_t pad;
+    uint32_t iswap;  // bit L: router/data swap on every node of layer L
+    uint32_t cswap;  // bit L: controlled swap between layers L and L+1
+};
+
+// Per-CTA-slot scratch (device), sized at launch for the worst case.
+struct Scratch {
+    uint32_t *cand;      // [slots][cand_cap]  packed (slice << 16) | site
+    uint32_t *wseg;      // [slots][nwarps][seg_cap] per-warp candidate segments
+    uint32_t *expl;      // [slots][D] explicit input columns
+    uint32_t *pw;        // [slots][ecap] on-path excitation bits (2 per layer)
+    uint32_t *pwR;       // [slots][ecap] on-path level-R bits (qutrit)
+    int32_t *ex;         // [slots][ecap] damping exponent (number of K0 factors a)
+    uint32_t *lab;       // [slots][ecap] (column << 8) | first-wall bus word c
+    uint32_t *st;        // [slots][ecap] bus word (bits 0-7) | sign (bit 8) | nexc (bits 16-23)
+    uint16_t *exc;       // [slots][ecap][kXcap] off-path sites (site << 1 | isR)
+    uint32_t cand_cap, seg_cap, ecap;
+};
+
+struct DumpOut {
+    uint32_t *col;       // [cap] explicit components at the end
+    uint32_t *bus;
+    uint64_t *hash;
+    double *re, *im;
+    uint32_t cap;
+    uint32_t *count;
+    double *scal;        // [4]: W, jump fired, good scale flag
+};
+
+struct Params {
+    int enc, n, k, T, D, nodes, M, nthreads;
+    const uint8_t *mem;
+    const uint32_t *addr, *bus;
+    const double *amp_re, *amp_im;
+    uint64_t seed;
+    uint64_t traj0;
+    uint32_t ntraj;
+    const double *gamma;
+    int mode;
+    const uint32_t *hist_cand, *hist_off;
+    uint32_t nhist;
+    qram_result_t *out;
+    // sample-only outputs
+    uint32_t *o_cand, *o_ncand, *o_badbits, *o_bad;
+    int32_t *o_ref;
+    uint32_t o_cap;
+    Scratch scr;
+    uint32_t *work;       // work-stealing counter
+    DumpOut dump;
+    int dump_mode;
+    SliceOps ops[kMaxT];
+};
+
+cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s);
+cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n, uint32_t cap,
+                                 uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
+                                 double *o_im, cudaStream_t s);
+int kernel_threads();
+size_t kernel_smem(int n);
+
+}  // namespace qram

@@ -1,0 +1,1141 @@
+// qram_kernels.cu -- sm_103a kernels of the pruned trajectory simulator.
+//
+// One CTA simulates one trajectory at a time and takes the next trajectory
+// index from a global counter (persistent, work-stealing launch).  Per
+// trajectory (Algorithm 1):
+//   1. candidate sampling (Theorem 3 step 1): one Philox4x32-10 call per
+//      (slice, node); each warp scans a contiguous range of (slice, node)
+//      pairs, so concatenating the per-warp segments yields the candidates
+//      in (slice, site) order without a sort;
+//   2. marking (Algorithm 1 step 1): every candidate marks bad(v), Eq. (7)
+//      for qutrits and Eq. (9) for qubits, into a shared-memory bitmap;
+//   3. explicit set: bad branches + the first good branch (pruned) or every
+//      branch (full); the qubit encoding splits each into 2^k components
+//      at creation (the first Hadamard wall only signs them, Lemma 1);
+//   4. evolution in epochs that end at slices with candidates.  A component
+//      is the path word of its address (2 bits per tree layer: router/data
+//      slot on the address path) plus a short list of off-path excitations;
+//      gates on the path word are a few bit operations, anything else takes
+//      a generic slow path.  K0 is applied lazily as an integer exponent.
+//   5. at a slice with candidates: mask weights (Eq. (18)), including the
+//      closed-form weight of the predicted good branches before the first
+//      jump; one auxiliary draw picks J in the canonical order (empty mask
+//      first, then sorted (site, level) lists lexicographically, a proper
+//      prefix first) by a deterministic block-wide descent;
+//   6. final tree measurement and fidelity; the second Hadamard wall enters
+//      only through the Walsh coefficient (-1)^(bus . b_out).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qram_internal.h"
+
+namespace qram {
+
+constexpr int NT = 256;            // threads per CTA
+constexpr int NW = NT / 32;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 from its published definition (Salmon et al., SC'11).
+__device__ __forceinline__ void philox(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                       uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ double uniform53(uint64_t seed, uint32_t slice, uint32_t stream, uint64_t traj) {
+    uint32_t c0 = 0, c1 = slice | (stream << 24), c2 = (uint32_t)traj, c3 = (uint32_t)(traj >> 32);
+    philox(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t w = (uint64_t)c0 | ((uint64_t)c1 << 32);
+    return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ---------------------------------------------------------------------------
+// tree helpers
+__device__ __forceinline__ int layer_of(uint32_t v) { return 31 - __clz(v + 1); }
+__device__ __forceinline__ uint32_t path_node(uint32_t i, int n, int L) {
+    return ((1u << L) - 1u) + (i >> (n - L));
+}
+__device__ __forceinline__ uint32_t routed_bit(uint32_t i, int n, int l) { return (i >> (n - 1 - l)) & 1u; }
+// spread bit L of x to bit 2L
+__device__ __forceinline__ uint32_t spread2(uint32_t x) {
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// bad(v): subtree(v) (Eq. (7)) or, for qubits, the family-divergence range
+// of Eq. (9).  Returns the leaf range [lo, hi).
+__device__ void bad_range(int enc, int n, uint32_t v, uint32_t &lo, uint32_t &hi) {
+    if (enc == QRAM_QUBIT) {
+        while (v != 0) {
+            const uint32_t par = (v - 1) >> 1;
+            const bool right = (v & 1u) == 0u;
+            if (right || par == 0) break;
+            v = par;
+        }
+        if (v == 0) { lo = 0; hi = 1u << n; return; }
+    }
+    const int l = layer_of(v);
+    const uint32_t p = v - ((1u << l) - 1u);
+    lo = p << (n - l);
+    hi = (p + 1u) << (n - l);
+}
+
+// ---------------------------------------------------------------------------
+// block reductions (fixed order: deterministic for a given block size)
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+struct Smem {
+    uint32_t badbits[512];         // 2^14 addresses
+    uint32_t candbits[1024];       // M <= 32766 sites, candidates of the current slice
+    uint32_t slice_off[kMaxT + 2];
+    double powlo[64], powhi[64];   // a^j, a^(64 j)
+    double redA[NW], redB[NW], redC[NW];
+    uint32_t scanw[NW];
+    uint32_t wcount[NW];
+    uint32_t J[kMaxJ];
+    int nJ;
+    uint32_t nexpl, ncomp, ncand;
+    int refcol;
+    uint32_t nbad;
+    int t;
+    int status;
+    double sA, sB, sC;
+};
+
+__device__ double block_sum(double x, double *red, Smem &S) {
+    x = warp_sum(x);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = x;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < NW; ++i) r += red[i];
+    return r;
+}
+
+// three sums at once
+__device__ void block_sum3(double &a, double &b, double &c, Smem &S) {
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { S.redA[w] = a; S.redB[w] = b; S.redC[w] = c; }
+    __syncthreads();
+    double ra = 0.0, rb = 0.0, rc = 0.0;
+    for (int i = 0; i < NW; ++i) { ra += S.redA[i]; rb += S.redB[i]; rc += S.redC[i]; }
+    a = ra; b = rb; c = rc;
+}
+
+// exclusive scan of a 0/1 flag over the block; returns prefix, total in *tot
+__device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem &S) {
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, f);
+    const uint32_t pre = __popc(b & ((1u << lane) - 1u));
+    __syncthreads();
+    if (lane == 0) S.scanw[w] = __popc(b);
+    __syncthreads();
+    uint32_t base = 0, all = 0;
+    for (uint32_t i = 0; i < NW; ++i) { if (i < w) base += S.scanw[i]; all += S.scanw[i]; }
+    *tot = all;
+    return base + pre;
+}
+
+// ---------------------------------------------------------------------------
+// component state in registers
+struct Comp {
+    uint32_t pw, pwR;    // path word: bit 2L router, 2L+1 data slot of path node at layer L
+    int32_t e;           // number of K0 factors a collected
+    uint32_t cb;         // bus word (register outside the tree)
+    uint32_t sign;       // phase (-1)^sign
+    uint32_t nexc;       // off-path excitations in x[]
+    uint16_t x[kXcap];   // sorted (site << 1 | isR)
+};
+
+struct Ctx {
+    int enc, n, k, T;
+    uint32_t i;          // address of the component's branch
+    uint32_t PB;         // bit 2L = routed bit of layer L (path direction)
+    const uint8_t *mem;
+};
+
+// ---- generic slow path: sorted list of (site << 2 | level) ----------------
+struct Ents {
+    uint32_t v[2 * kXcap + 8];
+    int n;
+};
+
+__device__ __forceinline__ int ent_get(const Ents &E, uint32_t site) {
+    for (int j = 0; j < E.n; ++j) if ((E.v[j] >> 2) == site) return (int)(E.v[j] & 3u);
+    return 0;
+}
+__device__ void ent_sort(Ents &E) {
+    for (int a = 1; a < E.n; ++a) {
+        uint32_t x = E.v[a]; int b = a - 1;
+        while (b >= 0 && (E.v[b] >> 2) > (x >> 2)) { E.v[b + 1] = E.v[b]; --b; }
+        E.v[b + 1] = x;
+    }
+}
+__device__ bool ent_set(Ents &E, uint32_t site, int lvl) {
+    for (int j = 0; j < E.n; ++j)
+        if ((E.v[j] >> 2) == site) {
+            if (lvl == 0) { for (int q = j; q + 1 < E.n; ++q) E.v[q] = E.v[q + 1]; --E.n; }
+            else E.v[j] = (site << 2) | (uint32_t)lvl;
+            return true;
+        }
+    if (lvl == 0) return true;
+    if (E.n >= 2 * kXcap + 8) return false;
+    E.v[E.n++] = (site << 2) | (uint32_t)lvl;
+    ent_sort(E);
+    return true;
+}
+
+__device__ void to_ents(const Comp &c, const Ctx &C, Ents &E) {
+    E.n = 0;
+    uint32_t w = c.pw;
+    int xi = 0;
+    while (w || xi < (int)c.nexc) {
+        uint32_t sp = 0xFFFFFFFFu, lp = 0;
+        if (w) {
+            const int b = __ffs(w) - 1;
+            const int L = b >> 1;
+            sp = 2u * path_node(C.i, C.n, L) + (uint32_t)(b & 1);
+            lp = (C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 2u : 1u;
+        }
+        uint32_t sx = 0xFFFFFFFFu, lx = 0;
+        if (xi < (int)c.nexc) { sx = c.x[xi] >> 1; lx = (c.x[xi] & 1u) ? 2u : 1u; }
+        if (sp < sx) { E.v[E.n++] = (sp << 2) | lp; w &= w - 1; }
+        else { E.v[E.n++] = (sx << 2) | lx; ++xi; }
+    }
+}
+
+__device__ bool from_ents(Comp &c, const Ctx &C, const Ents &E) {
+    c.pw = 0; c.pwR = 0; c.nexc = 0;
+    for (int j = 0; j < E.n; ++j) {
+        const uint32_t site = E.v[j] >> 2, lvl = E.v[j] & 3u;
+        const uint32_t u = site >> 1;
+        const int L = layer_of(u);
+        if (L < C.n && u == path_node(C.i, C.n, L)) {
+            const int b = 2 * L + (int)(site & 1u);
+            c.pw |= 1u << b;
+            if (lvl == 2u) c.pwR |= 1u << b;
+        } else {
+            if (c.nexc >= (uint32_t)kXcap) return false;
+            c.x[c.nexc++] = (uint16_t)((site << 1) | (lvl == 2u ? 1u : 0u));
+        }
+    }
+    return true;
+}
+
+// one slice of gates on the generic representation (App. C gate semantics)
+__device__ bool slow_slice(const SliceOps &op, Comp &c, const Ctx &C) {
+    Ents E;
+    to_ents(c, C, E);
+    const bool qubit = C.enc == QRAM_QUBIT;
+    const int n = C.n;
+    if (op.load >= 0) {
+        const uint32_t b = routed_bit(C.i, n, op.load);
+        const int d0 = ent_get(E, 1);
+        int nd;
+        if (qubit) nd = d0 ^ (int)b;
+        else { const int tgt = b ? 2 : 1; nd = d0 == 0 ? tgt : (d0 == tgt ? 0 : d0); }
+        if (!ent_set(E, 1, nd)) return false;
+    }
+    if (op.bus >= 0) {
+        const int d0 = ent_get(E, 1);
+        const uint32_t b = (c.cb >> op.bus) & 1u;
+        if (qubit) {
+            c.cb = (c.cb & ~(1u << op.bus)) | ((uint32_t)d0 << op.bus);
+            if (!ent_set(E, 1, (int)b)) return false;
+        } else if (d0 != 1) {
+            c.cb = (c.cb & ~(1u << op.bus)) | ((d0 == 2 ? 1u : 0u) << op.bus);
+            if (!ent_set(E, 1, b ? 2 : 0)) return false;
+        }
+    }
+    for (int L = 0; L < n; ++L) {
+        if (!((op.iswap >> L) & 1u)) continue;
+        const uint32_t lo = (1u << L) - 1u, hi = (2u << L) - 1u;
+        for (int j = 0; j < E.n; ++j) {
+            const uint32_t u = E.v[j] >> 3;
+            if (u >= lo && u < hi) E.v[j] ^= 4u;          // site ^= 1
+        }
+        ent_sort(E);
+    }
+    for (int L = 0; L + 1 < n; ++L) {
+        if (!((op.cswap >> L) & 1u)) continue;
+        const uint32_t lo = (1u << L) - 1u, hi = (2u << L) - 1u;
+        uint32_t nv[2 * kXcap + 8];
+        for (int j = 0; j < E.n; ++j) {
+            const uint32_t site = E.v[j] >> 2, u = site >> 1;
+            nv[j] = E.v[j];
+            if ((site & 1u) == 0u) continue;                // routers do not move
+            if (u >= lo && u < hi) {
+                const int r = ent_get(E, 2 * u);
+                if (!qubit && r == 0) continue;
+                const uint32_t child = qubit ? 2u * u + 1u + (uint32_t)r : 2u * u + (uint32_t)r;
+                nv[j] = ((2u * child + 1u) << 2) | (E.v[j] & 3u);
+            } else if (u >= hi && u < 2u * hi + 1u) {
+                const uint32_t par = (u - 1u) >> 1;
+                const int r = ent_get(E, 2 * par);
+                if (!qubit && r == 0) continue;
+                const uint32_t child = qubit ? 2u * par + 1u + (uint32_t)r : 2u * par + (uint32_t)r;
+                if (child == u) nv[j] = ((2u * par + 1u) << 2) | (E.v[j] & 3u);
+            }
+        }
+        for (int j = 0; j < E.n; ++j) E.v[j] = nv[j];
+        ent_sort(E);
+    }
+    if (op.fetch >= 0) {
+        const uint32_t lo = (1u << (n - 1)) - 1u, hi = (1u << n) - 1u;
+        if (qubit) {
+            for (int j = 0; j < E.n; ++j) {
+                const uint32_t site = E.v[j] >> 2, u = site >> 1;
+                if ((site & 1u) == 0u || u < lo || u >= hi) continue;
+                const uint32_t cell = 2u * (u - lo) + (uint32_t)ent_get(E, 2 * u);
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) c.sign ^= 1u;
+            }
+        } else {
+            uint32_t flip[2 * kXcap + 8];
+            int nf = 0;
+            for (int j = 0; j < E.n; ++j) {
+                const uint32_t site = E.v[j] >> 2, u = site >> 1;
+                if ((site & 1u) != 0u || u < lo || u >= hi) continue;
+                const uint32_t cell = 2u * (u - lo) + ((E.v[j] & 3u) == 2u ? 1u : 0u);
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) flip[nf++] = 2u * u + 1u;
+            }
+            for (int f = 0; f < nf; ++f) {
+                const int d = ent_get(E, flip[f]);
+                if (!ent_set(E, flip[f], d == 0 ? 2 : (d == 2 ? 0 : d))) return false;
+            }
+        }
+    }
+    return from_ents(c, C, E);
+}
+
+// ---- fast path on the path word ------------------------------------------
+__device__ __forceinline__ bool fast_slice(const SliceOps &op, Comp &c, const Ctx &C) {
+    if (c.nexc) return false;
+    const int n = C.n;
+    const uint32_t CM2 = spread2(op.cswap);
+    const bool qubit = C.enc == QRAM_QUBIT;
+    uint32_t mis;
+    if (qubit) mis = (c.pw ^ C.PB) & CM2;
+    else mis = CM2 & c.pw & (c.pwR ^ C.PB);
+    if (mis & (c.pw >> 1)) return false;               // a data item would leave the path
+    if (op.load >= 0) {
+        const uint32_t b = routed_bit(C.i, n, op.load);
+        if (qubit) c.pw ^= b << 1;
+        else {
+            const uint32_t e0 = (c.pw >> 1) & 1u, r0 = (c.pwR >> 1) & 1u;
+            if (!e0) { c.pw |= 2u; c.pwR = (c.pwR & ~2u) | (b << 1); }
+            else if (r0 == b) { c.pw &= ~2u; c.pwR &= ~2u; }
+        }
+    }
+    if (op.bus >= 0) {
+        const uint32_t e0 = (c.pw >> 1) & 1u, r0 = (c.pwR >> 1) & 1u;
+        const uint32_t b = (c.cb >> op.bus) & 1u;
+        if (qubit) {
+            c.pw = (c.pw & ~2u) | (b << 1);
+            c.cb = (c.cb & ~(1u << op.bus)) | (e0 << op.bus);
+        } else if (!(e0 && !r0)) {                          // a slot holding L is left alone
+            c.pw = (c.pw & ~2u) | (b << 1);
+            c.pwR = (c.pwR & ~2u) | (b << 1);
+            c.cb = (c.cb & ~(1u << op.bus)) | (e0 << op.bus);
+        }
+    }
+    if (op.iswap) {
+        const uint32_t IM2 = spread2(op.iswap);
+        uint32_t t = (c.pw ^ (c.pw >> 1)) & IM2;
+        c.pw ^= t | (t << 1);
+        t = (c.pwR ^ (c.pwR >> 1)) & IM2;
+        c.pwR ^= t | (t << 1);
+    }
+    if (CM2) {
+        // aligned controlled swaps move d(P_L) <-> d(P_{L+1}); a qutrit router at W swaps nothing
+        const uint32_t SM = (qubit ? (CM2 & ~mis) : (CM2 & c.pw & ~mis)) << 1;
+        uint32_t t = (c.pw ^ (c.pw >> 2)) & SM;
+        c.pw ^= t | (t << 2);
+        t = (c.pwR ^ (c.pwR >> 2)) & SM;
+        c.pwR ^= t | (t << 2);
+    }
+    if (op.fetch >= 0) {
+        const int L = n - 1;
+        const uint32_t re = (c.pw >> (2 * L)) & 1u, de = (c.pw >> (2 * L + 1)) & 1u;
+        if (qubit) {
+            if (de) {
+                const uint32_t cell = ((C.i >> 1) << 1) | re;
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) c.sign ^= 1u;
+            }
+        } else if (re) {
+            const uint32_t cell = ((C.i >> 1) << 1) | ((c.pwR >> (2 * L)) & 1u);
+            if ((__ldg(C.mem + cell) >> op.fetch) & 1u) {
+                const uint32_t dR = (c.pwR >> (2 * L + 1)) & 1u;
+                const uint32_t bit = 1u << (2 * L + 1);
+                if (!de) { c.pw |= bit; c.pwR |= bit; }
+                else if (dR) { c.pw &= ~bit; c.pwR &= ~bit; }
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool apply_slice(const SliceOps &op, Comp &c, const Ctx &C) {
+    if (fast_slice(op, c, C)) return true;
+    return slow_slice(op, c, C);
+}
+
+__device__ __forceinline__ int excited_count(const Comp &c) { return __popc(c.pw) + (int)c.nexc; }
+
+// iterate excited sites in increasing site order: returns code 2*site + isR,
+// state (w, xi) advanced.  Returns 0xFFFFFFFF at the end.
+__device__ __forceinline__ uint32_t next_site(const Comp &c, const Ctx &C, uint32_t &w, int &xi) {
+    uint32_t sp = 0xFFFFFFFFu, cp = 0;
+    if (w) {
+        const int b = __ffs(w) - 1;
+        sp = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
+        cp = (C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 1u : 0u;
+    }
+    uint32_t sx = 0xFFFFFFFFu, cx = 0;
+    if (xi < (int)c.nexc) { sx = c.x[xi] >> 1; cx = c.x[xi] & 1u; }
+    if (sp == 0xFFFFFFFFu && sx == 0xFFFFFFFFu) return 0xFFFFFFFFu;
+    if (sp < sx) { w &= w - 1; return (sp << 1) | cp; }
+    ++xi;
+    return (sx << 1) | cx;
+}
+
+// elements of the mask J(x) = C_s n X(x) in canonical order: ask for element
+// number `want` (0-based) after checking that elements 0..np-1 equal pref[].
+// Returns: -2 prefix mismatch, -1 no such element (mask == prefix), else code.
+__device__ long long mask_query(const Comp &c, const Ctx &C, const uint32_t *candbits,
+                                const uint32_t *pref, int np) {
+    uint32_t w = c.pw;
+    int xi = 0, got = 0;
+    for (;;) {
+        const uint32_t code = next_site(c, C, w, xi);
+        if (code == 0xFFFFFFFFu) return got == np ? -1 : -2;
+        const uint32_t site = code >> 1;
+        if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+        if (got < np) {
+            if (code != pref[got]) return -2;
+            ++got;
+            continue;
+        }
+        return (long long)code;
+    }
+}
+
+// does the component hold every element of J? (Theorem 3: K_J is nonzero)
+__device__ bool holds_all(const Comp &c, const Ctx &C, const uint32_t *J, int nJ) {
+    for (int j = 0; j < nJ; ++j) {
+        const uint32_t site = J[j] >> 1, isR = J[j] & 1u;
+        const uint32_t u = site >> 1;
+        const int L = layer_of(u);
+        bool ok = false;
+        if (L < C.n && u == path_node(C.i, C.n, L)) {
+            const int b = 2 * L + (int)(site & 1u);
+            ok = ((c.pw >> b) & 1u) && (C.enc == QRAM_QUBIT || ((c.pwR >> b) & 1u) == isR);
+        } else {
+            for (uint32_t q = 0; q < c.nexc; ++q)
+                if ((c.x[q] >> 1) == site) { ok = C.enc == QRAM_QUBIT || (c.x[q] & 1u) == isR; break; }
+        }
+        if (!ok) return false;
+    }
+    return true;
+}
+
+__device__ void clear_site(Comp &c, const Ctx &C, uint32_t site) {
+    const uint32_t u = site >> 1;
+    const int L = layer_of(u);
+    if (L < C.n && u == path_node(C.i, C.n, L)) {
+        const uint32_t bit = 1u << (2 * L + (int)(site & 1u));
+        c.pw &= ~bit; c.pwR &= ~bit;
+        return;
+    }
+    for (uint32_t q = 0; q < c.nexc; ++q)
+        if ((c.x[q] >> 1) == site) {
+            for (uint32_t r = q; r + 1 < c.nexc; ++r) c.x[r] = c.x[r + 1];
+            --c.nexc;
+            return;
+        }
+}
+
+// FNV-1a over the sorted (site << 2 | level) list; 0 for the ground state
+__device__ uint64_t config_hash(const Comp &c, const Ctx &C) {
+    if (c.pw == 0 && c.nexc == 0) return 0;
+    uint64_t h = 1469598103934665603ull;
+    uint32_t w = c.pw;
+    int xi = 0;
+    for (;;) {
+        const uint32_t code = next_site(c, C, w, xi);
+        if (code == 0xFFFFFFFFu) break;
+        const uint32_t v = ((code >> 1) << 2) | ((code & 1u) ? 2u : 1u);
+        for (int b = 0; b < 4; ++b) { h ^= (v >> (8 * b)) & 0xFFu; h *= 1099511628211ull; }
+    }
+    return h ? h : 1;
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double apow(const Smem &S, int e) {
+    return S.powlo[e & 63] * S.powhi[(e >> 6) & 63];
+}
+
+__device__ __forceinline__ void load_comp(const Scratch &scr, size_t base, uint32_t r, Comp &c, uint32_t &lab) {
+    const size_t g = base + r;
+    c.pw = scr.pw[g];
+    c.pwR = scr.pwR[g];
+    c.e = scr.ex[g];
+    lab = scr.lab[g];
+    const uint32_t st = scr.st[g];
+    c.cb = st & 0xFFu;
+    c.sign = (st >> 8) & 1u;
+    c.nexc = (st >> 16) & 0xFFu;
+    for (uint32_t q = 0; q < c.nexc; ++q) c.x[q] = scr.exc[g * kXcap + q];
+}
+
+__device__ __forceinline__ void store_comp(const Scratch &scr, size_t base, uint32_t r, const Comp &c, uint32_t lab) {
+    const size_t g = base + r;
+    scr.pw[g] = c.pw;
+    scr.pwR[g] = c.pwR;
+    scr.ex[g] = c.e;
+    scr.lab[g] = lab;
+    scr.st[g] = (c.cb & 0xFFu) | (c.sign << 8) | (c.nexc << 16);
+    for (uint32_t q = 0; q < c.nexc; ++q) scr.exc[g * kXcap + q] = c.x[q];
+}
+
+__device__ __forceinline__ void make_ctx(const Params &P, uint32_t col, Ctx &C) {
+    C.enc = P.enc; C.n = P.n; C.k = P.k; C.T = P.T; C.mem = P.mem;
+    C.i = __ldg(P.addr + col);
+    uint32_t pb = 0;
+    for (int L = 0; L < P.n; ++L) pb |= routed_bit(C.i, P.n, L) << (2 * L);
+    C.PB = pb;
+}
+
+__device__ __forceinline__ double col_w2(const Params &P, uint32_t col) {
+    const double re = __ldg(P.amp_re + col), im = __ldg(P.amp_im + col);
+    return re * re + im * im;
+}
+
+__device__ __forceinline__ int ov(int lo, int hi, int s) {   // |[lo,hi] n [1,s]|
+    const int top = s < hi ? s : hi;
+    return top >= lo ? top - lo + 1 : 0;
+}
+
+// closed-form exposure of a good branch after damping layers 1..s (Eq. (12);
+// Prop. 1 for the qutrit data slots)
+__device__ int good_exposure(const Params &P, uint32_t col, int s) {
+    const uint32_t i = __ldg(P.addr + col);
+    const int n = P.n, T = P.T;
+    int E = 0;
+    for (int l = 0; l < n; ++l)
+        if (P.enc == QRAM_QUTRIT || routed_bit(i, n, l)) E += ov(2 * l + 1, T - 2 * l - 2, s);
+    if (P.enc == QRAM_QUTRIT) {
+        const uint32_t j = __ldg(P.bus + col), d = __ldg(P.mem + i);
+        for (int t = 0; t < P.k; ++t) {
+            const int tin = 2 * n + 2 * t + 1, tf = 3 * n + 2 * t + 1, tout = 4 * n + 2 * t + 1;
+            if ((j >> t) & 1u) E += ov(tin, tf - 1, s);
+            if (((j ^ d) >> t) & 1u) E += ov(tf, tout - 1, s);
+        }
+    }
+    return E;
+}
+
+// qubit data-register norm^2 of a good branch after damping layers 1..s:
+// prod_t (1 + a^(2 m_t)) / 2 (Lemma 1)
+__device__ double data_norm2(const Params &P, const Smem &S, int s) {
+    if (P.enc != QRAM_QUBIT) return 1.0;
+    double r = 1.0;
+    for (int t = 0; t < P.k; ++t) {
+        const int m = ov(2 * P.n + 2 * t + 1, 4 * P.n + 2 * t, s);
+        const double am = apow(S, m);
+        r *= 0.5 * (1.0 + am * am);
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// one trajectory
+__device__ void run_one(const Params &P, Smem &S, uint32_t t) {
+    const uint64_t traj = P.traj0 + t;
+    const double gamma = P.gamma[t];
+    const int n = P.n, T = P.T;
+    const uint32_t nodes = (uint32_t)P.nodes;
+    const size_t slot = blockIdx.x;
+    const Scratch &scr = P.scr;
+    uint32_t *cand = scr.cand + slot * scr.cand_cap;
+    const bool valid = gamma >= 0.0 && gamma < 1.0;
+
+    if (threadIdx.x == 0) { S.status = valid ? QRAM_OK : QRAM_E_ARG; S.refcol = -1; S.nbad = 0; S.nJ = 0; }
+    for (int w = threadIdx.x; w < 512; w += NT) S.badbits[w] = 0;
+    for (int w = threadIdx.x; w < 1024; w += NT) S.candbits[w] = 0;
+    __syncthreads();
+
+    // ---- 1. candidates ------------------------------------------------------
+    const uint64_t thr = valid ? (uint64_t)__double2ull_rz(gamma * 18446744073709551616.0) : 0ull;
+    uint32_t ncand = 0;
+    const bool use_hist = P.nhist > t && P.hist_cand != nullptr;
+    if (use_hist) {
+        const uint32_t o0 = P.hist_off[t], o1 = P.hist_off[t + 1];
+        ncand = o1 - o0;
+        if (ncand > scr.cand_cap) { if (threadIdx.x == 0) S.status = QRAM_E_CAP; ncand = scr.cand_cap; }
+        for (uint32_t c = threadIdx.x; c < ncand; c += NT) {
+            // a fixed history must name slices 1..T-1 and tree sites, in (slice, site) order
+            const uint32_t v = P.hist_cand[o0 + c], hs = v >> 16, hq = v & 0xFFFFu;
+            if (hs == 0 || hs >= (uint32_t)T || hq >= (uint32_t)P.M || (c > 0 && P.hist_cand[o0 + c - 1] >= v))
+                S.status = QRAM_E_ARG;
+            cand[c] = v;
+        }
+    } else if (valid && thr > 0) {
+        const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+        const uint32_t total = (uint32_t)(T - 1) * nodes;
+        const uint32_t per = (total + NW - 1) / NW;
+        const uint32_t beg = w * per, end = min(total, beg + per);
+        uint32_t *seg = scr.wseg + (slot * NW + w) * scr.seg_cap;
+        uint32_t cnt = 0;
+        bool overflow = false;
+        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+        const uint32_t tl = (uint32_t)traj, th = (uint32_t)(traj >> 32);
+        // (slice, node) of item beg + lane
+        uint32_t idx = beg + lane;
+        uint32_t s = 1 + idx / nodes, v = idx % nodes;
+        const uint32_t step_s = 32u / nodes, step_v = 32u % nodes;
+        for (uint32_t base = beg; base < end; base += 32) {
+            bool cr = false, cd = false;
+            if (idx < end) {
+                uint32_t c0 = v, c1 = s | (1u << 24), c2 = tl, c3 = th;
+                philox(c0, c1, c2, c3, k0, k1);
+                const uint64_t ur = (uint64_t)c0 | ((uint64_t)c1 << 32);
+                const uint64_t ud = (uint64_t)c2 | ((uint64_t)c3 << 32);
+                cr = ur < thr;
+                cd = ud < thr;
+            }
+            const uint32_t br = __ballot_sync(0xFFFFFFFFu, cr), bd = __ballot_sync(0xFFFFFFFFu, cd);
+            if (br | bd) {
+                const uint32_t lt = (1u << lane) - 1u;
+                uint32_t pos = cnt + __popc(br & lt) + __popc(bd & lt);
+                if (cr) { if (pos < scr.seg_cap) seg[pos] = (s << 16) | (2u * v); else overflow = true; ++pos; }
+                if (cd) { if (pos < scr.seg_cap) seg[pos] = (s << 16) | (2u * v + 1u); else overflow = true; }
+                cnt += __popc(br) + __popc(bd);
+            }
+            idx += 32;
+            s += step_s; v += step_v;
+            if (v >= nodes) { v -= nodes; ++s; }
+        }
+        overflow = __any_sync(0xFFFFFFFFu, overflow);
+        if (lane == 0) S.wcount[w] = overflow ? 0xFFFFFFFFu : cnt;
+        __syncthreads();
+        uint32_t off = 0, tot = 0;
+        bool bad = false;
+        for (uint32_t q = 0; q < NW; ++q) {
+            if (S.wcount[q] == 0xFFFFFFFFu) bad = true;
+            else { if (q < w) off += S.wcount[q]; tot += S.wcount[q]; }
+        }
+        if (bad || tot > scr.cand_cap) {
+            if (threadIdx.x == 0) S.status = QRAM_E_CAP;
+            tot = 0;
+        } else {
+            for (uint32_t c = lane; c < cnt; c += 32) cand[off + c] = seg[c];
+        }
+        ncand = tot;
+    }
+    __syncthreads();
+    if (S.status == QRAM_E_ARG) ncand = 0;
+    if (threadIdx.x == 0) S.ncand = ncand;
+
+    // per-slice offsets (candidates are sorted by (slice, site))
+    for (int s = threadIdx.x; s <= T; s += NT) {
+        uint32_t lo = 0, hi = ncand;
+        const uint32_t key = (uint32_t)s << 16;
+        while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (cand[mid] < key) lo = mid + 1; else hi = mid; }
+        S.slice_off[s] = lo;
+    }
+    // ---- 2. marking: every candidate marks bad(v) ---------------------------
+    for (uint32_t c = threadIdx.x; c < ncand; c += NT) {
+        uint32_t lo, hi;
+        bad_range(P.enc, n, (cand[c] & 0xFFFFu) >> 1, lo, hi);
+        while (lo < hi) {
+            const uint32_t wd = lo >> 5, b0 = lo & 31u;
+            const uint32_t nb = min(32u - b0, hi - lo);
+            const uint32_t m = nb == 32u ? 0xFFFFFFFFu : (((1u << nb) - 1u) << b0);
+            atomicOr(&S.badbits[wd], m);
+            lo += nb;
+        }
+    }
+    __syncthreads();
+
+    // classification: B and the reference branch (first good input column)
+    {
+        uint32_t nb = 0;
+        int firstgood = 0x7FFFFFFF;
+        for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
+            const uint32_t i = __ldg(P.addr + b);
+            if ((S.badbits[i >> 5] >> (i & 31u)) & 1u) ++nb;
+            else if ((int)b < firstgood) firstgood = (int)b;
+        }
+        atomicAdd(&S.nbad, nb);
+        __syncthreads();
+        if (threadIdx.x == 0) S.refcol = 0x7FFFFFFF;
+        __syncthreads();
+        atomicMin(&S.refcol, firstgood);
+        __syncthreads();
+        if (threadIdx.x == 0 && S.refcol == 0x7FFFFFFF) S.refcol = -1;
+        __syncthreads();
+    }
+
+    if (P.dump_mode) {
+        const uint32_t W = ((1u << n) + 31u) >> 5;
+        for (uint32_t w = threadIdx.x; w < W; w += NT) P.o_badbits[w] = S.badbits[w];
+        if (threadIdx.x == 0) P.o_ref[0] = S.refcol;
+    }
+    if (P.mode == kSampleOnly) {
+        const uint32_t W = ((1u << n) + 31u) >> 5;
+        const uint32_t cap = P.o_cap;
+        for (uint32_t c = threadIdx.x; c < ncand && c < cap; c += NT) P.o_cand[(size_t)t * cap + c] = cand[c];
+        for (uint32_t w = threadIdx.x; w < W; w += NT) P.o_badbits[(size_t)t * W + w] = S.badbits[w];
+        if (threadIdx.x == 0) {
+            P.o_ncand[t] = S.status == QRAM_E_ARG ? 0xFFFFFFFFu : (S.status == QRAM_E_CAP ? 0xFFFFFFFEu : ncand);
+            P.o_bad[t] = S.nbad;
+            P.o_ref[t] = S.refcol;
+        }
+        __syncthreads();
+        return;
+    }
+
+    // ---- 3. explicit set ----------------------------------------------------
+    const double a = sqrt(1.0 - (valid ? gamma : 0.0));
+    if (threadIdx.x < 64) {
+        double p = 1.0;
+        for (int j = 0; j < (int)threadIdx.x; ++j) p *= a;
+        S.powlo[threadIdx.x] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const double a64 = S.powlo[63] * a;
+        double p = 1.0;
+        for (int j = 0; j < (int)threadIdx.x; ++j) p *= a64;
+        S.powhi[threadIdx.x] = p;
+    }
+    uint32_t *expl = scr.expl + slot * (size_t)P.D;
+    {
+        uint32_t base = 0;
+        for (uint32_t b0 = 0; b0 < (uint32_t)P.D; b0 += NT) {
+            const uint32_t b = b0 + threadIdx.x;
+            bool take = false;
+            if (b < (uint32_t)P.D) {
+                const uint32_t i = __ldg(P.addr + b);
+                take = P.mode == kFull || ((S.badbits[i >> 5] >> (i & 31u)) & 1u) || (int)b == S.refcol;
+            }
+            uint32_t tot;
+            const uint32_t pre = block_scan_flag(take, &tot, S);
+            if (take) expl[base + pre] = b;
+            base += tot;
+        }
+        if (threadIdx.x == 0) S.nexpl = base;
+    }
+    __syncthreads();
+    const bool qubit = P.enc == QRAM_QUBIT;
+    const int kb = qubit ? P.k : 0;
+    const uint32_t ncomp0 = S.nexpl << kb;
+    if (ncomp0 > scr.ecap) { if (threadIdx.x == 0) S.status = QRAM_E_CAP; }
+    __syncthreads();
+    const size_t cbase = slot * (size_t)scr.ecap;
+    if (S.status == QRAM_OK) {
+        for (uint32_t r = threadIdx.x; r < ncomp0; r += NT) {
+            const uint32_t col = expl[r >> kb], cw = r & ((1u << kb) - 1u);
+            Comp c;
+            c.pw = 0; c.pwR = 0; c.e = 0; c.nexc = 0;
+            const uint32_t j = __ldg(P.bus + col);
+            if (qubit) { c.cb = cw; c.sign = __popc(j & cw) & 1u; }   // first wall: (-1)^(j.c)
+            else { c.cb = j; c.sign = 0; }
+            store_comp(scr, cbase, r, c, (col << 8) | cw);
+        }
+    }
+    if (threadIdx.x == 0) S.ncomp = S.status == QRAM_OK ? ncomp0 : 0;
+    __syncthreads();
+
+    // ---- 4. epochs ----------------------------------------------------------
+    int s_prev = 0;              // slice whose damping is pending (0: none)
+    bool jumped = false;
+    uint32_t jumps = 0, first_jump = 0, jump_sites = 0;
+    const double k2 = qubit ? ldexp(1.0, -P.k) : 1.0;   // |first-wall factor|^2
+    for (;;) {
+        // next slice with candidates
+        int s1 = s_prev + 1;
+        while (s1 < T && S.slice_off[s1 + 1] == S.slice_off[s1]) ++s1;
+        const bool final_epoch = s1 >= T;
+        if (!final_epoch) {
+            for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {
+                const uint32_t site = cand[c] & 0xFFFFu;
+                atomicOr(&S.candbits[site >> 5], 1u << (site & 31u));
+            }
+        }
+        __syncthreads();
+        const uint32_t ncomp = S.ncomp;
+        const int nJ = S.nJ;
+        const bool compact = s_prev > 0 && nJ > 0;
+        double wsum = 0.0, wempty = 0.0, ovl = 0.0;
+        uint32_t wr = 0;        // write cursor (compaction)
+        bool capfail = false;
+        for (uint32_t r0 = 0; r0 < ncomp; r0 += NT) {
+            const uint32_t r = r0 + threadIdx.x;
+            bool alive = r < ncomp;
+            Comp c;
+            uint32_t lab = 0;
+            Ctx C;
+            if (alive) {
+                load_comp(scr, cbase, r, c, lab);
+                make_ctx(P, lab >> 8, C);
+                if (s_prev > 0) {                           // pending K_J of slice s_prev
+                    if (nJ > 0) {
+                        alive = holds_all(c, C, S.J, nJ);
+                        if (alive) for (int j = 0; j < nJ; ++j) clear_site(c, C, S.J[j] >> 1);
+                    }
+                    if (alive) c.e += excited_count(c);
+                }
+            }
+            if (alive) {
+                const int slast = final_epoch ? T - 1 : s1;
+                for (int s = s_prev + 1; s <= slast; ++s) {
+                    if (!apply_slice(P.ops[s], c, C)) { capfail = true; break; }
+                    if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
+                }
+                const double ae = apow(S, c.e);
+                const double w = col_w2(P, lab >> 8) * k2 * ae * ae;
+                if (!final_epoch) {
+                    wsum += w;
+                    if (mask_query(c, C, S.candbits, S.J, 0) == -1) wempty += w;
+                } else {
+                    wsum += w;
+                    if (c.pw == 0 && c.nexc == 0) {          // ground tree configuration
+                        wempty += w;
+                        const uint32_t col = lab >> 8;
+                        if (qubit) {
+                            const uint32_t bout = __ldg(P.bus + col) ^ __ldg(P.mem + C.i);
+                            const uint32_t par = (c.sign + __popc(c.cb & bout)) & 1u;
+                            const double term = col_w2(P, col) * k2 * ae;
+                            ovl += par ? -term : term;
+                        } else if (c.cb == (__ldg(P.bus + col) ^ __ldg(P.mem + C.i))) {
+                            ovl += col_w2(P, col) * ae;
+                        }
+                    }
+                    if (P.dump_mode && threadIdx.x < NT) {
+                        const uint32_t di = atomicAdd(P.dump.count, 1u);
+                        if (di < P.dump.cap) {
+                            const uint32_t col = lab >> 8;
+                            const double sc = (qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0) * ae * (c.sign ? -1.0 : 1.0);
+                            P.dump.col[di] = col;
+                            P.dump.bus[di] = c.cb;
+                            P.dump.hash[di] = config_hash(c, C);
+                            P.dump.re[di] = __ldg(P.amp_re + col) * sc;
+                            P.dump.im[di] = __ldg(P.amp_im + col) * sc;
+                        }
+                    }
+                }
+            }
+            if (compact) {
+                uint32_t tot;
+                const uint32_t pre = block_scan_flag(alive, &tot, S);
+                if (alive && !final_epoch) store_comp(scr, cbase, wr + pre, c, lab);
+                wr += tot;
+            } else if (alive && !final_epoch) {
+                store_comp(scr, cbase, r, c, lab);
+            }
+        }
+        if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
+        __syncthreads();
+        if (threadIdx.x == 0 && compact) S.ncomp = wr;
+        // good branches: closed-form weights before the first jump (Eq. (18))
+        double wg = 0.0, og = 0.0;
+        if (P.mode == kPruned && !jumped) {
+            const int sw = final_epoch ? T - 1 : s1 - 1;
+            const double dn = data_norm2(P, S, sw);
+            for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
+                const uint32_t i = __ldg(P.addr + b);
+                if ((S.badbits[i >> 5] >> (i & 31u)) & 1u) continue;
+                if ((int)b == S.refcol) continue;
+                const int E = good_exposure(P, b, sw);
+                const double ae = apow(S, E);
+                const double w2 = col_w2(P, b);
+                wg += w2 * ae * ae * dn;
+                if (final_epoch) {
+                    if (qubit) {
+                        const double an = apow(S, 2 * n);
+                        double al = 1.0;
+                        for (int q = 0; q < P.k; ++q) al *= 0.5 * (1.0 + an);
+                        og += w2 * ae * al;
+                    } else {
+                        og += w2 * ae;
+                    }
+                }
+            }
+        }
+        block_sum3(wsum, wempty, ovl, S);
+        double wgs = wg, ogs = og, dummy = 0.0;
+        block_sum3(wgs, ogs, dummy, S);
+        const double Wtot = wsum + wgs, Wemp = wempty + wgs;
+        if (final_epoch) {
+            const double ov_all = ovl + ogs;
+            if (threadIdx.x == 0) {
+                const double uf = uniform53(P.seed, 0, 3u, traj);
+                const bool ground = Wemp > uf * Wtot;
+                qram_result_t R;
+                R.fidelity = (ground && Wemp > 0.0) ? ov_all * ov_all / Wemp : 0.0;
+                R.fidelity_unsampled = Wtot > 0.0 ? ov_all * ov_all / Wtot : 0.0;
+                R.p_ground = Wtot > 0.0 ? Wemp / Wtot : 0.0;
+                R.bad = S.nbad;
+                R.ref = S.refcol;
+                R.ncand = S.ncand;
+                R.explicit_comps = ncomp0;
+                R.jumps = (uint16_t)jumps;
+                R.first_jump_slice = (uint16_t)first_jump;
+                R.jump_sites = (uint16_t)jump_sites;
+                R.q_ground = ground ? 1 : 0;
+                R.status = (uint8_t)S.status;
+                if (P.out) P.out[t] = R;
+                if (P.dump_mode) {
+                    P.dump.scal[0] = Wtot;
+                    P.dump.scal[1] = jumped ? 1.0 : 0.0;
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        // ---- 5. joint draw at slice s1 (Theorem 3 with Eq. (18) weights) ----
+        const double u = uniform53(P.seed, (uint32_t)s1, 2u, traj);
+        double tgt = u * Wtot;
+        int nsel = 0;
+        if (!(Wemp > tgt) && S.status == QRAM_OK) {
+            // descent over the canonical order; O = weight before the subtree
+            double O = Wemp;
+            const uint32_t cb0 = S.slice_off[s1], ncodes = 2u * (S.slice_off[s1 + 1] - cb0);
+            __shared__ uint32_t pref[kMaxJ];
+            for (int level = 0; level < kMaxJ; ++level) {
+                // weight of components whose mask equals the prefix exactly
+                if (level > 0) {
+                    double we = 0.0;
+                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
+                        Comp c; uint32_t lab; Ctx C;
+                        load_comp(scr, cbase, r, c, lab);
+                        make_ctx(P, lab >> 8, C);
+                        if (mask_query(c, C, S.candbits, pref, level) == -1) {
+                            const double ae = apow(S, c.e);
+                            we += col_w2(P, lab >> 8) * k2 * ae * ae;
+                        }
+                    }
+                    we = block_sum(we, S.redA, S);
+                    if (O + we > tgt) break;                  // J = prefix
+                    O += we;
+                }
+                // F(x): weight with next code <= code(x); find first x with O + F(x) > tgt
+                uint32_t lo = 0, hi = ncodes;                // answer in [lo, hi]; hi = none
+                double Flo = 0.0;                            // F(lo - 1)
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
+                    double f = 0.0;
+                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
+                        Comp c; uint32_t lab; Ctx C;
+                        load_comp(scr, cbase, r, c, lab);
+                        make_ctx(P, lab >> 8, C);
+                        const long long q = mask_query(c, C, S.candbits, pref, level);
+                        if (q >= 0 && (uint32_t)q <= cmid) {
+                            const double ae = apow(S, c.e);
+                            f += col_w2(P, lab >> 8) * k2 * ae * ae;
+                        }
+                    }
+                    f = block_sum(f, S.redA, S);
+                    if (O + f > tgt) hi = mid;
+                    else { lo = mid + 1; Flo = f; }
+                }
+                if (lo >= ncodes) {
+                    // rounding left the target above the total: take the last
+                    // group with weight (the oracle's rule); descend on the largest code
+                    uint32_t best = 0xFFFFFFFFu;
+                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
+                        Comp c; uint32_t lab; Ctx C;
+                        load_comp(scr, cbase, r, c, lab);
+                        make_ctx(P, lab >> 8, C);
+                        const long long q = mask_query(c, C, S.candbits, pref, level);
+                        if (q >= 0 && (best == 0xFFFFFFFFu || (uint32_t)q > best)) best = (uint32_t)q;
+                    }
+                    __shared__ uint32_t sbest;
+                    if (threadIdx.x == 0) sbest = 0u;
+                    __syncthreads();
+                    if (best != 0xFFFFFFFFu) atomicMax(&sbest, best + 1u);
+                    __syncthreads();
+                    const uint32_t sb = sbest;
+                    __syncthreads();
+                    if (sb == 0u) break;                                // mask == prefix
+                    const uint32_t code = sb - 1u;
+                    if (threadIdx.x == 0) pref[level] = code;
+                    __syncthreads();
+                    tgt = O + 1e308;                                    // keep taking the last group
+                    nsel = level + 1;
+                    continue;
+                }
+                const uint32_t code = 2u * (cand[cb0 + (lo >> 1)] & 0xFFFFu) + (lo & 1u);
+                if (threadIdx.x == 0) pref[level] = code;
+                __syncthreads();
+                O += Flo;
+                nsel = level + 1;
+            }
+            if (threadIdx.x == 0) {
+                for (int j = 0; j < nsel; ++j) S.J[j] = pref[j];
+            }
+        }
+        if (threadIdx.x == 0) S.nJ = nsel;
+        __syncthreads();
+        if (nsel > 0) {
+            if (!jumped) first_jump = (uint32_t)s1;
+            jumped = true;
+            ++jumps;
+            jump_sites += (uint32_t)nsel;
+        }
+        // clear the candidate bitmap of s1
+        for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {
+            const uint32_t site = cand[c] & 0xFFFFu;
+            atomicAnd(&S.candbits[site >> 5], ~(1u << (site & 31u)));
+        }
+        __syncthreads();
+        s_prev = s1;
+    }
+}
+
+__global__ void __launch_bounds__(NT) traj_kernel(const __grid_constant__ Params P) {
+    __shared__ Smem S;
+    for (;;) {
+        if (threadIdx.x == 0) S.t = (int)atomicAdd(P.work, 1u);
+        __syncthreads();
+        const uint32_t t = (uint32_t)S.t;
+        __syncthreads();
+        if (t >= P.ntraj) break;
+        run_one(P, S, t);
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s) {
+    (void)block; (void)smem;
+    traj_kernel<<<grid, NT, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+int kernel_threads() { return NT; }
+size_t kernel_smem(int) { return sizeof(Smem); }
+
+// ---------------------------------------------------------------------------
+// ensemble mean / standard error in a fixed order (one CTA)
+__global__ void __launch_bounds__(256) fidelity_kernel(const qram_result_t *res, uint32_t ntraj, double *out2) {
+    __shared__ double ra[8], rb[8];
+    double s = 0.0, q = 0.0;
+    for (uint32_t t = threadIdx.x; t < ntraj; t += 256) { const double f = res[t].fidelity; s += f; q += f * f; }
+    s = warp_sum(s); q = warp_sum(q);
+    if ((threadIdx.x & 31) == 0) { ra[threadIdx.x >> 5] = s; rb[threadIdx.x >> 5] = q; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S1 = 0.0, S2 = 0.0;
+        for (int i = 0; i < 8; ++i) { S1 += ra[i]; S2 += rb[i]; }
+        const double m = ntraj ? S1 / ntraj : 0.0;
+        double var = ntraj > 1 ? (S2 - S1 * m) / (ntraj - 1) : 0.0;
+        if (var < 0) var = 0;
+        out2[0] = m;
+        out2[1] = ntraj ? sqrt(var / ntraj) : 0.0;
+    }
+}
+
+cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s) {
+    fidelity_kernel<<<1, 256, 0, s>>>(res, ntraj, out2);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// dump: Walsh-Hadamard transform of each (column, configuration) group at the
+// second wall, plus the predicted good branches; normalised by sqrt(W).
+__global__ void dump_finalize_kernel(const Params P, uint32_t n_in, uint32_t *out_n, uint32_t cap,
+                                     uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
+                                     double *o_im) {
+    const DumpOut &d = P.dump;
+    const double W = d.scal[0];
+    const double inv = W > 0 ? 1.0 / sqrt(W) : 0.0;
+    const bool qubit = P.enc == QRAM_QUBIT;
+    const uint32_t nw = qubit ? (1u << P.k) : 1u;
+    const double hs = qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0;
+    // explicit groups: leader = first entry with the same (col, hash)
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_in; r += gridDim.x * blockDim.x) {
+        bool leader = true;
+        for (uint32_t q = 0; q < r; ++q)
+            if (d.col[q] == d.col[r] && d.hash[q] == d.hash[r]) { leader = false; break; }
+        if (!leader) continue;
+        for (uint32_t w = 0; w < nw; ++w) {
+            double re = 0.0, im = 0.0;
+            for (uint32_t q = r; q < n_in; ++q) {
+                if (d.col[q] != d.col[r] || d.hash[q] != d.hash[r]) continue;
+                if (qubit) {
+                    const double sg = (__popc(d.bus[q] & w) & 1u) ? -hs : hs;
+                    re += sg * d.re[q]; im += sg * d.im[q];
+                } else if (w == 0) { re += d.re[q]; im += d.im[q]; }
+            }
+            const uint32_t busw = qubit ? w : d.bus[r];
+            const uint32_t o = atomicAdd(out_n, 1u);
+            if (o < cap) {
+                o_addr[o] = __ldg(P.addr + d.col[r]); o_bus[o] = busw; o_hash[o] = d.hash[r];
+                o_re[o] = re * inv; o_im[o] = im * inv;
+            }
+        }
+    }
+    // predicted good branches (pruned mode, no jump fired)
+    if (P.mode != kPruned || d.scal[1] != 0.0) return;
+    const double g = P.gamma[0];
+    const double a = sqrt(1.0 - g);
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < (uint32_t)P.D; b += gridDim.x * blockDim.x) {
+        const uint32_t i = __ldg(P.addr + b);
+        // the reference and the bad branches were explicit
+        if (P.o_badbits && ((P.o_badbits[i >> 5] >> (i & 31u)) & 1u)) continue;
+        if ((int)b == *P.o_ref) continue;
+        int E = 0;
+        const int n = P.n, T = P.T;
+        for (int l = 0; l < n; ++l)
+            if (!qubit || routed_bit(i, n, l)) E += T - 4 * l - 2;
+        const uint32_t j = __ldg(P.bus + b), dm = __ldg(P.mem + i);
+        if (!qubit) for (int t = 0; t < P.k; ++t) E += n * ((int)((j >> t) & 1u) + (int)(((j ^ dm) >> t) & 1u));
+        double ae = 1.0;
+        for (int q = 0; q < E; ++q) ae *= a;
+        const double re0 = __ldg(P.amp_re + b), im0 = __ldg(P.amp_im + b);
+        if (qubit) {
+            double an = 1.0;
+            for (int q = 0; q < 2 * n; ++q) an *= a;
+            const double al = 0.5 * (1.0 + an), be = 0.5 * (1.0 - an);
+            const uint32_t bout = j ^ dm;
+            for (uint32_t w = 0; w < nw; ++w) {
+                const int hw = __popc(w ^ bout);
+                double A = ae;
+                for (int q = 0; q < P.k; ++q) A *= q < hw ? be : al;
+                const uint32_t o = atomicAdd(out_n, 1u);
+                if (o < cap) { o_addr[o] = i; o_bus[o] = w; o_hash[o] = 0; o_re[o] = re0 * A * inv; o_im[o] = im0 * A * inv; }
+            }
+        } else {
+            const uint32_t o = atomicAdd(out_n, 1u);
+            if (o < cap) { o_addr[o] = i; o_bus[o] = j ^ dm; o_hash[o] = 0; o_re[o] = re0 * ae * inv; o_im[o] = im0 * ae * inv; }
+        }
+    }
+}
+
+cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n, uint32_t cap,
+                                 uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
+                                 double *o_im, cudaStream_t s) {
+    dump_finalize_kernel<<<8, 128, 0, s>>>(p, n_in, out_n, cap, o_addr, o_bus, o_hash, o_re, o_im);
+    return cudaGetLastError();
+}
+
+}  // namespace qram

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, on the
+same seeded inputs.  Integer outputs (candidates, the bad union, B, the
+reference branch, jump records, the sampled tree outcome) must match
+bit-exactly; floating-point outputs within 1e-12 absolute (the tolerance the
+method's FP64 arithmetic allows: both sides carry ~1e-16 relative rounding
+per operation over at most a few thousand operations)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import core
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _sim(p, seed):
+    from paper_2609_34935_b300 import QramSim
+    return QramSim(p, seed=seed, device=0)
+
+
+def _cmp_results(got, ref, check_bad=True):
+    assert np.all(got["status"] == 0), np.unique(got["status"])
+    if check_bad:
+        assert np.array_equal(got["bad"], ref["bad"])
+        assert np.array_equal(got["ref"], ref["ref"])
+    assert np.array_equal(got["ncand"], ref["ncand"])
+    assert np.array_equal(got["jumps"], ref["jumps"])
+    assert np.array_equal(got["first_jump_slice"], ref["first_jump_slice"])
+    assert np.array_equal(got["jump_sites"], ref["jump_sites"])
+    assert np.array_equal(got["q_ground"], ref["q_ground"])
+    for f in ("fidelity", "fidelity_unsampled", "p_ground"):
+        d = np.abs(got[f] - ref[f])
+        assert np.max(d) < TOL, (f, np.max(d), int(np.argmax(d)))
+
+
+CASES = [
+    # encoding, n, k, gamma, ntraj, input
+    (W.QUTRIT, 3, 1, 1e-3, 1000, "load"),        # 8 cells, qutrit, k=1
+    (W.QUTRIT, 3, 1, 5e-2, 400, "load"),
+    (W.QUBIT, 6, 1, 1e-4, 300, "load"),          # 64 cells, phase-kickback fetch
+    (W.QUBIT, 6, 1, 1e-3, 300, "load"),
+    (W.QUBIT, 6, 1, 1e-2, 200, "load"),
+    (W.QUBIT, 4, 3, 6e-2, 300, "load"),          # several-element joint outcomes
+    (W.QUTRIT, 5, 2, 3e-2, 300, "rand"),
+    (W.QUBIT, 5, 4, 2e-2, 200, "rand"),          # complex amplitudes, random bus
+    (W.QUBIT, 1, 1, 0.2, 300, "load"),
+    (W.QUTRIT, 1, 1, 0.3, 300, "load"),
+    (W.QUBIT, 2, 1, 0.05, 400, "dm"),            # the Tab. IV setting
+]
+
+
+def _problem(enc, n, k, kind, seed):
+    if kind == "load":
+        return W.data_loading(enc, n, k, seed=seed)
+    if kind == "dm":
+        p = W.data_loading(enc, n, k, seed=seed)
+        p.memory = np.array([0, 1, 1, 0], np.uint8)
+        return p
+    return W.random_columns(enc, n, k, D=max(1, (1 << n) - 5), seed=seed)
+
+
+@pytest.mark.parametrize("enc,n,k,gamma,ntraj,kind", CASES)
+@pytest.mark.parametrize("mode", ["pruned", "full"])
+def test_trajectories_match_oracle(enc, n, k, gamma, ntraj, kind, mode):
+    seed = 1000 + 17 * n + k
+    p = _problem(enc, n, k, kind, seed)
+    g = np.full(ntraj, gamma)
+    ref = core.run(p, seed, 0, g)
+    sim = _sim(p, seed)
+    got = sim.results(sim.run(mode, 0, torch.tensor(g, device="cuda:0")))
+    _cmp_results(got, ref)
+    if mode == "pruned":
+        assert np.all(got["explicit_comps"] == (got["bad"] + (got["ref"] >= 0)) << (k if enc == W.QUBIT else 0))
+    sim.close()
+
+
+@pytest.mark.parametrize("enc,n,k,gamma", [(W.QUTRIT, 10, 1, 1e-3), (W.QUBIT, 12, 4, 1e-3), (W.QUBIT, 7, 3, 3e-3)])
+def test_sample_faults_bit_exact(enc, n, k, gamma):
+    seed = 3001 + n
+    p = W.data_loading(enc, n, k, seed=seed)
+    nt = 6
+    sim = _sim(p, seed)
+    out = sim.sample_faults(5, torch.full((nt,), gamma, dtype=torch.float64, device="cuda:0"), cap=1 << 13)
+    for t in range(nt):
+        sl, st, bad, B, ref = core.sample_faults(p, seed, 5 + t, gamma)
+        nc = int(out["ncand"][t])
+        assert nc == len(sl)
+        packed = out["cand"][t, :nc].cpu().numpy().astype(np.uint32)
+        assert np.array_equal(packed >> 16, sl.astype(np.uint32))
+        assert np.array_equal(packed & 0xFFFF, st.astype(np.uint32))
+        bits = out["bad_bits"][t].cpu().numpy().astype(np.uint32)
+        gbad = np.array([(bits[a >> 5] >> (a & 31)) & 1 for a in range(1 << n)], np.uint8)
+        assert np.array_equal(gbad, bad)
+        assert int(out["bad"][t]) == B and int(out["ref"][t]) == ref
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", ["pruned", "full"])
+def test_full_size_qubit_n12_k4_sampled(mode):
+    """The n=12, k=4 workload in the launch configuration of the benchmark,
+    on a sample of trajectories the oracle can afford, across the gamma
+    decades of the log-uniform draw."""
+    p = W.data_loading(W.QUBIT, 12, 4, seed=4001)
+    g = np.array([1e-5, 3e-5, 1e-4, 4e-4, 1e-3])
+    ref = core.run(p, 4001, 77, g)
+    sim = _sim(p, 4001)
+    got = sim.results(sim.run(mode, 77, torch.tensor(g, device="cuda:0")))
+    _cmp_results(got, ref)
+    sim.close()
+
+
+def _hash_cfg(cfg):
+    """FNV-1a 64 over (site << 2 | level) little-endian words (the dump's hash)."""
+    if not cfg:
+        return 0
+    h = 1469598103934665603
+    for q, lv in cfg:
+        v = (q << 2) | lv
+        for b in range(4):
+            h ^= (v >> (8 * b)) & 0xFF
+            h = (h * 1099511628211) & (2 ** 64 - 1)
+    return h or 1
+
+
+@pytest.mark.parametrize("enc,n,k,gamma,kind", [(W.QUBIT, 4, 3, 6e-2, "load"), (W.QUTRIT, 4, 2, 4e-2, "rand"),
+                                               (W.QUBIT, 5, 2, 1e-2, "rand"), (W.QUBIT, 3, 3, 0.0, "load")])
+@pytest.mark.parametrize("mode", ["pruned", "full"])
+def test_final_state_amplitudes(enc, n, k, gamma, kind, mode):
+    seed = 555 + n
+    p = _problem(enc, n, k, kind, seed)
+    sim = _sim(p, seed)
+    for traj in range(8):
+        _, d = core.run_one(p, seed, traj, gamma, None, cap=1 << 14)
+        want = {}
+        for a, b, cfg, amp in zip(d.addr, d.bus, d.configs, d.amp):
+            want[(int(a), int(b), _hash_cfg(cfg))] = amp
+        ga, gb, gh, gz = sim.dump_state(mode, traj, gamma)
+        got = {}
+        for a, b, h, z in zip(ga, gb, gh, gz):
+            key = (int(a), int(b), int(h))
+            got[key] = got.get(key, 0) + z
+        for key in set(want) | set(got):
+            assert abs(want.get(key, 0) - got.get(key, 0)) < TOL, (traj, key)
+    sim.close()
+
+
+def test_fixed_history_annihilation():
+    """A fired jump on the reference's path annihilates every predicted good
+    group (Sec. V.A); fixed histories exercise it independently of the FAULT
+    stream."""
+    n, k = 5, 2
+    p = W.data_loading(W.QUBIT, n, k, seed=9)
+    T = 6 * n + 2 * k
+    seed = 4242
+    hist = []
+    # candidates on d_0 while address bits travel: jump fires with high probability
+    for t in range(24):
+        s = 1 + (t % (T - 2))
+        hist.append([(s, 1), (min(T - 1, s + 3), 2 * ((t % 7) + 1))])
+    cand, off = [], [0]
+    refs = []
+    for h in hist:
+        h = sorted(h)
+        cand += [(s << 16) | q for s, q in h]
+        off.append(len(cand))
+        refs.append(h)
+    sim = _sim(p, seed)
+    sim.set_fault_history(torch.tensor(np.array(cand, np.int64).astype(np.int32), device="cuda:0"),
+                          torch.tensor(np.array(off, np.int32), device="cuda:0"))
+    g = np.full(len(hist), 0.02)
+    for mode in ("pruned", "full"):
+        got = sim.results(sim.run(mode, 0, torch.tensor(g, device="cuda:0")))
+        fired = 0
+        for t, h in enumerate(refs):
+            r, _ = core.run_one(p, seed, t, 0.02, core.History([s for s, _ in h], [q for _, q in h]), cap=1 << 12)
+            assert got["status"][t] == 0
+            assert got["jumps"][t] == r["jumps"] and got["first_jump_slice"][t] == r["first_jump_slice"]
+            assert got["bad"][t] == r["bad"] and got["ref"][t] == r["ref"]
+            assert abs(got["fidelity"][t] - r["fidelity"]) < TOL
+            assert abs(got["fidelity_unsampled"][t] - r["fidelity_unsampled"]) < TOL
+            fired += int(r["jumps"] > 0)
+        assert fired > 3
+    sim.set_fault_history()
+    sim.close()
+
+
+def test_no_jump_trajectories_closed_form():
+    """Qubit n=6, k=1: every trajectory without a fired jump returns the
+    closed-form no-jump fidelity (Theorems 1-2)."""
+    p = W.data_loading(W.QUBIT, 6, 1, seed=2001)
+    sim = _sim(p, 2001)
+    for gamma in (1e-4, 1e-3, 1e-2):
+        got = sim.results(sim.run_pruned(0, torch.full((10000,), gamma, dtype=torch.float64, device="cuda:0")))
+        F0 = cf.no_jump_fidelity(W.QUBIT, 6, 1, gamma, p.addr, p.bus, p.amp, p.memory)
+        nj = got[got["jumps"] == 0]
+        assert len(nj) > 100
+        assert np.max(np.abs(nj["fidelity"] - F0)) < TOL
+    sim.close()
+
+
+def test_deterministic_and_edge_cases():
+    p = W.data_loading(W.QUBIT, 5, 2, seed=3)
+    sim = _sim(p, 3)
+    g = torch.full((500,), 2e-2, dtype=torch.float64, device="cuda:0")
+    a = sim.run_pruned(10, g).cpu().numpy()
+    b = sim.run_pruned(10, g).cpu().numpy()
+    assert np.array_equal(a, b)
+    # gamma = 0: nothing is bad, one explicit branch, F = 1
+    r = sim.results(sim.run_pruned(0, torch.zeros(50, dtype=torch.float64, device="cuda:0")))
+    assert np.all(r["bad"] == 0) and np.all(r["ref"] == 0) and np.all(r["explicit_comps"] == 4)
+    assert np.max(np.abs(r["fidelity"] - 1.0)) < TOL
+    # invalid rates are reported per trajectory
+    r = sim.results(sim.run_pruned(0, torch.tensor([0.5, 1.0, -0.1], dtype=torch.float64, device="cuda:0")))
+    assert list(r["status"]) == [0, 1, 1]
+    sim.close()
+    # one branch, n = k = 1
+    q = W.Problem(W.QUBIT, 1, 1, np.array([1, 0], np.uint8), np.array([1], np.uint32), np.array([1], np.uint32),
+                  np.array([1.0 + 0j]))
+    ref = core.run(q, 8, 0, np.full(200, 0.1))
+    sim = _sim(q, 8)
+    _cmp_results(sim.results(sim.run_pruned(0, torch.full((200,), 0.1, dtype=torch.float64, device="cuda:0"))), ref)
+    sim.close()
+
+
+def test_fidelity_reduction():
+    p = W.data_loading(W.QUTRIT, 3, 1, seed=1001)
+    sim = _sim(p, 1001)
+    raw = sim.run_pruned(0, torch.full((1000,), 1e-3 * 20, dtype=torch.float64, device="cuda:0"))
+    m, s = sim.fidelity(raw)
+    f = sim.results(raw)["fidelity"]
+    assert abs(m - f.mean()) < 1e-13 and abs(s - f.std(ddof=1) / math.sqrt(len(f))) < 1e-12
+    sim.close()
