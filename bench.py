@@ -1,0 +1,332 @@
+"""Benchmark: pruned trajectories/s at n = 12 vs full on the same B300, with
+p50/p99 query latency.
+
+Workload: qubit encoding (phase-kickback fetch between two Hadamard walls),
+n = 12 (4096 cells), k = 4 data qubits per cell with i.i.d. random bits, the
+data-loading input (one branch per address, zero bus), gamma log-uniform in
+[1e-5, 1e-2] per batch of 1000 trajectories, 1e5 trajectories, complex FP64.
+A step is one pruned launch over the whole 1e5-trajectory batch (every row
+of the hot path: sampling, marking, explicit evolution with the joint
+sampler, closed-form good branches, final measurement).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank simulates its own 1e5 trajectories (weak scaling,
+replicas by trajectory range; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "pruned trajectories/s at n=12 vs full on same B300; p50/p99 query latency"
+N, K, NTRAJ, BATCH = 12, 4, 100_000, 1000
+G_LO, G_HI = 1e-5, 1e-2
+SEED = 4001
+WORKLOAD = ("qubit encoding n=12 (4096 cells), k=4 i.i.d. data bits, data-loading input, "
+            "gamma log-uniform [1e-5,1e-2] per batch of 1000 trajectories, 1e5 trajectories, complex FP64")
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _problem():
+    return W.data_loading(W.QUBIT, N, K, seed=SEED)
+
+
+def _gammas():
+    return W.gamma_batches(NTRAJ, BATCH, G_LO, G_HI, seed=SEED)
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_baseline(p, gam, budget_s=15.0):
+    """The oracle (plain CPU full evolution) on the host cores, on a bounded
+    sample: trajectories spread over the gamma batches of the workload."""
+    cores = os.cpu_count() or 1
+    idx = np.arange(0, NTRAJ, BATCH // 2)            # 2 per gamma batch, 200 in total
+    done, t0 = 0, time.perf_counter()
+    for start in range(0, len(idx), cores):
+        sel = idx[start:start + cores]
+        _oracle_chunk(p, gam, sel, cores)
+        done += len(sel)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} trajectories of the workload (every {BATCH // 2}th index, spanning the gamma "
+                      f"batches), full evolution, one trajectory per host thread"}
+
+
+def _oracle_chunk(p, gam, sel, cores):
+    """Run the given trajectory indices on `cores` threads (each trajectory
+    keeps its own index and damping rate)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import core
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        return list(ex.map(lambda t: core.run(p, SEED, int(t), gam[t:t + 1], nthreads=1), sel))
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    p = _problem()
+    gam = _gammas()
+    from oracle import core
+    core.build()
+    cores = os.cpu_count() or 1
+    per_step = max(cores, 16)
+    idx = np.arange(0, NTRAJ, NTRAJ // per_step)[:per_step]
+    for _ in range(args.warmup):
+        _oracle_chunk(p, gam, idx[:cores], cores)
+    times = []
+    for s in range(args.steps):
+        sel = (idx + s) % NTRAJ
+        t0 = time.perf_counter()
+        _oracle_chunk(p, gam, sel, cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * per_step / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trajectories/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": "oracle full evolution (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} trajectories per step spread over the gamma batches"},
+            "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--full-per-batch", type=int, default=5, help="full-mode trajectories per gamma batch")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_2609_34935_b300 import QramSim
+
+    p = _problem()
+    gam_h = _gammas()
+    stream = torch.cuda.Stream(device=dev)
+    sim = QramSim(p, seed=SEED, device=local, stream=stream)
+    sim.set_gamma_bound(G_HI)
+    gam = torch.tensor(gam_h, dtype=torch.float64, device=dev)
+    out = torch.empty((NTRAJ, 48), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # > 126 MB L2
+    base = rank * 1_000_000_000                                           # disjoint trajectory ranges
+
+    def step(j):
+        sim.run_pruned(base + j * NTRAJ, gam, out)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for j in range(args.warmup):
+            step(j)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = sim.launch_count
+    ev = []
+    barrier()
+    for j in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(j & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(args.warmup + j)
+            e1.record(stream)
+        ev.append((e0, e1))
+    barrier()
+    launches = sim.launch_count - l0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    cl = clocks.stop()
+    res = sim.results(out)
+    t_dev = sum(ms) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_dev], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt[0])
+    value = world * args.steps * NTRAJ / t_dev
+
+    # ---- pruned vs full on the same stratified subset --------------------
+    sub = np.concatenate([np.arange(b, b + args.full_per_batch) for b in range(0, NTRAJ, BATCH)])
+    gsub = torch.tensor(gam_h[sub], dtype=torch.float64, device=dev)
+    osub = torch.empty((len(sub), 48), dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps=1):
+        with torch.cuda.stream(stream):
+            fn()
+            stream.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    t_full = timed(lambda: sim.run_full(base + 7_000_000, gsub, osub))
+    full_res = sim.results(osub)
+    t_psub = timed(lambda: sim.run_pruned(base + 7_000_000, gsub, osub), reps=3)
+    pr_res = sim.results(osub)
+    agree = float(np.max(np.abs(full_res["fidelity"] - pr_res["fidelity"])))
+
+    # ---- per-query latency: one gamma batch (1000 trajectories) alone -----
+    lat = []
+    gb = torch.empty(BATCH, dtype=torch.float64, device=dev)
+    ob = torch.empty((BATCH, 48), dtype=torch.uint8, device=dev)
+    for b in range(0, NTRAJ, BATCH * 4):
+        gb.copy_(gam[b:b + BATCH])
+        lat.append(1e3 * timed(lambda: sim.run_pruned(base + 9_000_000 + b, gb, ob)))
+    lat = np.array(lat)
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    g_pin = torch.tensor(gam_h, dtype=torch.float64).pin_memory()
+    o_pin = torch.empty((NTRAJ, 48), dtype=torch.uint8).pin_memory()
+    e2e_t = []
+    for j in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            gam.copy_(g_pin, non_blocking=True)
+            sim.run_pruned(base + 5_000_000 + j * NTRAJ, gam, out)
+            o_pin.copy_(out, non_blocking=True)
+        stream.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = world * NTRAJ / float(np.mean(e2e_t))
+
+    # ---- roofline of the trajectory kernel ---------------------------------
+    nodes = (1 << N) - 1
+    T = 6 * N + 2 * K
+    philox_calls = NTRAJ * (T - 1) * nodes
+    ops_per_call = 84            # 10 rounds x (2 wide multiplies + 4 xor + 2 key adds) + 2 64-bit compares
+    sm_mhz = cl.get("sm_mhz") or 2032.0
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_int = nsm * 64 * sm_mhz * 1e6 / 1e12          # Tops/s: 64 INT32 lanes/SM/clock
+    achieved = philox_calls * ops_per_call / (t_dev / (world * args.steps)) / 1e12 / world
+    traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "Tops/s (INT32)",
+            "frac": achieved / peak_int, "traffic": traffic,
+            "note": "algorithmic INT32 ops of the Philox candidate draw per launch / launch time; "
+                    "peak = SMs x 64 INT32 lanes x median SM clock under load"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = _cpu_baseline(p, gam_h)
+        except Exception as e:           # pragma: no cover
+            cpu = {"value": None, "error": str(e)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": "pruned", "trajectories_per_step": NTRAJ,
+                       "l2": "256 MiB buffer written between timed steps",
+                       "parallelism": f"replicas x{world} (trajectory ranges)"},
+            "full": {"value": len(sub) / t_full, "unit": "trajectories/s",
+                     "pruned_same_subset": len(sub) / t_psub, "speedup_pruned_over_full": t_full / t_psub,
+                     "subset": f"{args.full_per_batch} trajectories per gamma batch ({len(sub)} total)",
+                     "max_abs_fidelity_diff_pruned_vs_full": agree},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "query": "one gamma batch of 1000 trajectories launched alone", "n": int(len(lat))},
+            "mean_fidelity": float(res["fidelity"].mean()), "status_ok": bool(np.all(res["status"] == 0)),
+            "mean_bad_fraction": float(res["bad"].mean() / (1 << N)),
+            "e2e": {"value": e2e_val, "unit": "trajectories/s", "h2d_bytes_per_step": int(g_pin.numel() * 8),
+                    "d2h_bytes_per_step": int(o_pin.numel())},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": cl,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,19 @@ int qram_run_full(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double 
  * must stay valid while the hook is set. */
 int qram_set_fault_history(qram_sim_t *sim, uint32_t nhist, const uint32_t *cand, const uint32_t *off);
 
+/* Upper bound on the damping rates of the next runs (0 < gmax < 1), used to
+ * size the per-trajectory candidate scratch without reading the rates back
+ * to the host; 0 clears it (each run then reduces gamma on the device and
+ * synchronises once).  A trajectory whose candidates overflow the sized
+ * scratch is reported with status QRAM_E_CAP, never truncated silently. */
+int qram_set_gamma_bound(qram_sim_t *sim, double gmax);
+
+/* Limit the persistent launch of this simulator to at most `nctas` CTAs
+ * (0 = one slot per resident CTA on every SM, the default).  Scratch memory
+ * scales with the number of CTAs; fewer CTAs leave room for other work on
+ * the same GPU.  Takes effect at the next run. */
+int qram_set_launch_ctas(qram_sim_t *sim, uint32_t nctas);
+
 /* Ensemble mean and standard error of results[0 .. ntraj).fidelity
  * (device array), reduced on the device in a fixed order; blocks until the
  * two host doubles are written. */

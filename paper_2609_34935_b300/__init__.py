@@ -70,6 +70,8 @@ def load_library(build_if_missing: bool = True):
     L.qram_set_fault_history.argtypes = [vp, u32, vp, vp]
     L.qram_fidelity.argtypes = [vp, vp, u32, C.POINTER(f64), C.POINTER(f64)]
     L.qram_dump_state.argtypes = [vp, C.c_int, u64, f64, u32, vp, vp, vp, vp, vp, C.POINTER(u32)]
+    L.qram_set_gamma_bound.argtypes = [vp, f64]
+    L.qram_set_launch_ctas.argtypes = [vp, u32]
     L.qram_sync.argtypes = [vp]
     L.qram_launch_count.argtypes = [vp]
     L.qram_launch_count.restype = u64
@@ -210,6 +212,12 @@ class QramSim:
             _check(rc, "qram_dump_state")
             m = cnt.value
             return addr[:m], bus[:m], hsh[:m], re[:m] + 1j * im[:m]
+
+    def set_gamma_bound(self, gmax: float):
+        _check(self.lib.qram_set_gamma_bound(self.h, gmax), "qram_set_gamma_bound")
+
+    def set_launch_ctas(self, nctas: int):
+        _check(self.lib.qram_set_launch_ctas(self.h, nctas), "qram_set_launch_ctas")
 
     def sync(self):
         _check(self.lib.qram_sync(self.h), "qram_sync")

@@ -37,6 +37,7 @@ struct qram_sim {
     SliceOps ops[kMaxT]{};
     uint64_t launches = 0;
     int sms = 0, blocks_per_sm = 0;
+    double gamma_bound = 0.0;
 };
 
 namespace {
@@ -83,6 +84,15 @@ int build_ops(int n, int k, SliceOps *ops) {
             ops[3 * n + 2 * t + 1 + m].cswap |= 1u << (n - 1 - m);
         }
         if (!set8(ops[3 * n + 2 * t + 1].fetch, t)) return QRAM_E_ARG;
+    }
+    for (int s = 0; s < kMaxT; ++s) {
+        uint32_t a = 0, b = 0;
+        for (int L = 0; L < 16; ++L) {
+            if ((ops[s].iswap >> L) & 1u) a |= 1u << (2 * L);
+            if ((ops[s].cswap >> L) & 1u) b |= 1u << (2 * L);
+        }
+        ops[s].iswap2 = a;
+        ops[s].cswap2 = b;
     }
     // every gate of a slice must act on its own slots (controls included)
     const size_t M = 2 * ((size_t(1) << n) - 1);
@@ -195,6 +205,7 @@ Params base_params(qram_sim *S) {
 }
 
 int bound_gamma(qram_sim *S, const double *gamma, uint32_t ntraj, double *gmax) {
+    if (S->gamma_bound > 0.0) { *gmax = S->gamma_bound; return QRAM_OK; }
     gmax_kernel<<<1, 256, 0, S->stream>>>(gamma, ntraj, S->d_gmax);
     S->launches++;
     if (!ok(cudaGetLastError())) return QRAM_E_CUDA;
@@ -277,7 +288,8 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     int rc = QRAM_OK;
     const size_t D = (size_t)S->D;
     if (!ok(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, device))) { delete S; return QRAM_E_CUDA; }
-    S->blocks_per_sm = 2;
+    S->blocks_per_sm = kernel_blocks_per_sm();
+    if (S->blocks_per_sm < 1) { delete S; return QRAM_E_CUDA; }
     S->slots = S->sms * S->blocks_per_sm;
     if (!ok(cudaMalloc(&S->d_mem, N)) || !ok(cudaMalloc(&S->d_addr, D * 4)) || !ok(cudaMalloc(&S->d_bus, D * 4)) ||
         !ok(cudaMalloc(&S->d_re, D * 8)) || !ok(cudaMalloc(&S->d_im, D * 8)) ||
@@ -339,6 +351,25 @@ int qram_set_fault_history(qram_sim_t *S, uint32_t nhist, const uint32_t *cand, 
     S->nhist = nhist;
     S->hist_cand = nhist ? cand : nullptr;
     S->hist_off = nhist ? off : nullptr;
+    return QRAM_OK;
+}
+
+int qram_set_launch_ctas(qram_sim_t *S, uint32_t nctas) {
+    if (!S) return QRAM_E_ARG;
+    const int full = S->sms * S->blocks_per_sm;
+    const int want = nctas == 0 ? full : (int)std::min<uint32_t>(nctas, (uint32_t)full);
+    if (want != S->slots) {
+        DeviceGuard g(S->device);
+        if (S->stream) cudaStreamSynchronize(S->stream); else cudaDeviceSynchronize();
+        if (S->scratch) { cudaFree(S->scratch); S->scratch = nullptr; }
+        S->slots = want;
+    }
+    return QRAM_OK;
+}
+
+int qram_set_gamma_bound(qram_sim_t *S, double gmax) {
+    if (!S || !(gmax >= 0.0 && gmax < 1.0)) return QRAM_E_ARG;
+    S->gamma_bound = gmax;
     return QRAM_OK;
 }
 

@@ -24,6 +24,8 @@ struct SliceOps {
     int8_t pad;
     uint32_t iswap;  // bit L: router/data swap on every node of layer L
     uint32_t cswap;  // bit L: controlled swap between layers L and L+1
+    uint32_t iswap2; // iswap with bit L moved to bit 2L (path-word layout)
+    uint32_t cswap2; // cswap with bit L moved to bit 2L
 };
 
 // Per-CTA-slot scratch (device), sized at launch for the worst case.
@@ -80,6 +82,7 @@ cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n
                                  uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
                                  double *o_im, cudaStream_t s);
 int kernel_threads();
+int kernel_blocks_per_sm();
 size_t kernel_smem(int n);
 
 }  // namespace qram

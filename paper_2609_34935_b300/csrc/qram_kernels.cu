@@ -154,22 +154,30 @@ __device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem &S) {
 }
 
 // ---------------------------------------------------------------------------
-// component state in registers
-struct Comp {
-    uint32_t pw, pwR;    // path word: bit 2L router, 2L+1 data slot of path node at layer L
+// component state: the hot part lives in registers; the off-path excitations
+// (rare: only after a jump moved an item off its address path) in a small
+// per-thread array xs[] that only the slow path and the mask queries touch.
+struct CompR {
+    uint32_t pw, pwR;    // path word: bit 2L router, 2L+1 data slot of the path node at layer L
     int32_t e;           // number of K0 factors a collected
     uint32_t cb;         // bus word (register outside the tree)
     uint32_t sign;       // phase (-1)^sign
-    uint32_t nexc;       // off-path excitations in x[]
-    uint16_t x[kXcap];   // sorted (site << 1 | isR)
+    uint32_t nexc;       // off-path excitations in xs[]
 };
 
 struct Ctx {
-    int enc, n, k, T;
+    int enc, n;
     uint32_t i;          // address of the component's branch
-    uint32_t PB;         // bit 2L = routed bit of layer L (path direction)
+    uint32_t PB;         // bit 2L = bit routed at layer L (path direction)
     const uint8_t *mem;
 };
+
+__device__ __forceinline__ Ctx make_ctx(int enc, int n, const uint8_t *mem, uint32_t i) {
+    Ctx C;
+    C.enc = enc; C.n = n; C.mem = mem; C.i = i;
+    C.PB = spread2(__brev(i) >> (32 - n));      // routed bit of layer L = bit n-1-L of i
+    return C;
+}
 
 // ---- generic slow path: sorted list of (site << 2 | level) ----------------
 struct Ents {
@@ -202,26 +210,35 @@ __device__ bool ent_set(Ents &E, uint32_t site, int lvl) {
     return true;
 }
 
-__device__ void to_ents(const Comp &c, const Ctx &C, Ents &E) {
+// the excited sites of a component in increasing site order, as codes
+// 2*site + isR; xi/w carry the iteration state
+__device__ __forceinline__ uint32_t next_site(uint32_t pw, uint32_t pwR, uint32_t nexc, const uint16_t *xs,
+                                              const Ctx &C, uint32_t &w, uint32_t &xi) {
+    uint32_t sp = 0xFFFFFFFFu, cp = 0;
+    if (w) {
+        const int b = __ffs(w) - 1;
+        sp = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
+        cp = (C.enc == QRAM_QUTRIT && ((pwR >> b) & 1u)) ? 1u : 0u;
+    }
+    uint32_t sx = 0xFFFFFFFFu, cx = 0;
+    if (xi < nexc) { sx = xs[xi] >> 1; cx = xs[xi] & 1u; }
+    if (sp == 0xFFFFFFFFu && sx == 0xFFFFFFFFu) return 0xFFFFFFFFu;
+    if (sp < sx) { w &= w - 1; return (sp << 1) | cp; }
+    ++xi;
+    return (sx << 1) | cx;
+}
+
+__device__ void to_ents(const CompR &c, const uint16_t *xs, const Ctx &C, Ents &E) {
     E.n = 0;
-    uint32_t w = c.pw;
-    int xi = 0;
-    while (w || xi < (int)c.nexc) {
-        uint32_t sp = 0xFFFFFFFFu, lp = 0;
-        if (w) {
-            const int b = __ffs(w) - 1;
-            const int L = b >> 1;
-            sp = 2u * path_node(C.i, C.n, L) + (uint32_t)(b & 1);
-            lp = (C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 2u : 1u;
-        }
-        uint32_t sx = 0xFFFFFFFFu, lx = 0;
-        if (xi < (int)c.nexc) { sx = c.x[xi] >> 1; lx = (c.x[xi] & 1u) ? 2u : 1u; }
-        if (sp < sx) { E.v[E.n++] = (sp << 2) | lp; w &= w - 1; }
-        else { E.v[E.n++] = (sx << 2) | lx; ++xi; }
+    uint32_t w = c.pw, xi = 0;
+    for (;;) {
+        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
+        if (code == 0xFFFFFFFFu) break;
+        E.v[E.n++] = ((code >> 1) << 2) | ((code & 1u) ? 2u : 1u);
     }
 }
 
-__device__ bool from_ents(Comp &c, const Ctx &C, const Ents &E) {
+__device__ bool from_ents(CompR &c, uint16_t *xs, const Ctx &C, const Ents &E) {
     c.pw = 0; c.pwR = 0; c.nexc = 0;
     for (int j = 0; j < E.n; ++j) {
         const uint32_t site = E.v[j] >> 2, lvl = E.v[j] & 3u;
@@ -233,35 +250,38 @@ __device__ bool from_ents(Comp &c, const Ctx &C, const Ents &E) {
             if (lvl == 2u) c.pwR |= 1u << b;
         } else {
             if (c.nexc >= (uint32_t)kXcap) return false;
-            c.x[c.nexc++] = (uint16_t)((site << 1) | (lvl == 2u ? 1u : 0u));
+            xs[c.nexc++] = (uint16_t)((site << 1) | (lvl == 2u ? 1u : 0u));
         }
     }
     return true;
 }
 
-// one slice of gates on the generic representation (App. C gate semantics)
-__device__ bool slow_slice(const SliceOps &op, Comp &c, const Ctx &C) {
+// One slice of gates on the generic representation (App. C gate semantics).
+// Takes and returns the register state by value so that callers keep it in
+// registers; *okp = 0 if a capacity was exceeded.
+__device__ __noinline__ CompR slow_slice(const SliceOps op, CompR c, uint16_t *xs, const Ctx C, int *okp) {
     Ents E;
-    to_ents(c, C, E);
+    to_ents(c, xs, C, E);
     const bool qubit = C.enc == QRAM_QUBIT;
     const int n = C.n;
+    *okp = 1;
     if (op.load >= 0) {
         const uint32_t b = routed_bit(C.i, n, op.load);
         const int d0 = ent_get(E, 1);
         int nd;
         if (qubit) nd = d0 ^ (int)b;
         else { const int tgt = b ? 2 : 1; nd = d0 == 0 ? tgt : (d0 == tgt ? 0 : d0); }
-        if (!ent_set(E, 1, nd)) return false;
+        if (!ent_set(E, 1, nd)) { *okp = 0; return c; }
     }
     if (op.bus >= 0) {
         const int d0 = ent_get(E, 1);
         const uint32_t b = (c.cb >> op.bus) & 1u;
         if (qubit) {
             c.cb = (c.cb & ~(1u << op.bus)) | ((uint32_t)d0 << op.bus);
-            if (!ent_set(E, 1, (int)b)) return false;
+            if (!ent_set(E, 1, (int)b)) { *okp = 0; return c; }
         } else if (d0 != 1) {
             c.cb = (c.cb & ~(1u << op.bus)) | ((d0 == 2 ? 1u : 0u) << op.bus);
-            if (!ent_set(E, 1, b ? 2 : 0)) return false;
+            if (!ent_set(E, 1, b ? 2 : 0)) { *okp = 0; return c; }
         }
     }
     for (int L = 0; L < n; ++L) {
@@ -317,22 +337,24 @@ __device__ bool slow_slice(const SliceOps &op, Comp &c, const Ctx &C) {
             }
             for (int f = 0; f < nf; ++f) {
                 const int d = ent_get(E, flip[f]);
-                if (!ent_set(E, flip[f], d == 0 ? 2 : (d == 2 ? 0 : d))) return false;
+                if (!ent_set(E, flip[f], d == 0 ? 2 : (d == 2 ? 0 : d))) { *okp = 0; return c; }
             }
         }
     }
-    return from_ents(c, C, E);
+    if (!from_ents(c, xs, C, E)) *okp = 0;
+    return c;
 }
 
 // ---- fast path on the path word ------------------------------------------
-__device__ __forceinline__ bool fast_slice(const SliceOps &op, Comp &c, const Ctx &C) {
+// Handles every slice in which nothing leaves or enters the address path:
+// no off-path excitation, and every active controlled swap whose on-path data
+// slot is occupied is aligned with the path.  Returns false otherwise.
+__device__ __forceinline__ bool fast_slice(const SliceOps &op, CompR &c, const Ctx &C) {
     if (c.nexc) return false;
     const int n = C.n;
-    const uint32_t CM2 = spread2(op.cswap);
+    const uint32_t CM2 = op.cswap2;
     const bool qubit = C.enc == QRAM_QUBIT;
-    uint32_t mis;
-    if (qubit) mis = (c.pw ^ C.PB) & CM2;
-    else mis = CM2 & c.pw & (c.pwR ^ C.PB);
+    const uint32_t mis = qubit ? ((c.pw ^ C.PB) & CM2) : (CM2 & c.pw & (c.pwR ^ C.PB));
     if (mis & (c.pw >> 1)) return false;               // a data item would leave the path
     if (op.load >= 0) {
         const uint32_t b = routed_bit(C.i, n, op.load);
@@ -355,11 +377,10 @@ __device__ __forceinline__ bool fast_slice(const SliceOps &op, Comp &c, const Ct
             c.cb = (c.cb & ~(1u << op.bus)) | (e0 << op.bus);
         }
     }
-    if (op.iswap) {
-        const uint32_t IM2 = spread2(op.iswap);
-        uint32_t t = (c.pw ^ (c.pw >> 1)) & IM2;
+    if (op.iswap2) {
+        uint32_t t = (c.pw ^ (c.pw >> 1)) & op.iswap2;
         c.pw ^= t | (t << 1);
-        t = (c.pwR ^ (c.pwR >> 1)) & IM2;
+        t = (c.pwR ^ (c.pwR >> 1)) & op.iswap2;
         c.pwR ^= t | (t << 1);
     }
     if (CM2) {
@@ -391,39 +412,24 @@ __device__ __forceinline__ bool fast_slice(const SliceOps &op, Comp &c, const Ct
     return true;
 }
 
-__device__ __forceinline__ bool apply_slice(const SliceOps &op, Comp &c, const Ctx &C) {
+__device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16_t *xs, const Ctx &C) {
     if (fast_slice(op, c, C)) return true;
-    return slow_slice(op, c, C);
+    int okv;
+    c = slow_slice(op, c, xs, C, &okv);
+    return okv != 0;
 }
 
-__device__ __forceinline__ int excited_count(const Comp &c) { return __popc(c.pw) + (int)c.nexc; }
+__device__ __forceinline__ int excited_count(const CompR &c) { return __popc(c.pw) + (int)c.nexc; }
 
-// iterate excited sites in increasing site order: returns code 2*site + isR,
-// state (w, xi) advanced.  Returns 0xFFFFFFFF at the end.
-__device__ __forceinline__ uint32_t next_site(const Comp &c, const Ctx &C, uint32_t &w, int &xi) {
-    uint32_t sp = 0xFFFFFFFFu, cp = 0;
-    if (w) {
-        const int b = __ffs(w) - 1;
-        sp = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
-        cp = (C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 1u : 0u;
-    }
-    uint32_t sx = 0xFFFFFFFFu, cx = 0;
-    if (xi < (int)c.nexc) { sx = c.x[xi] >> 1; cx = c.x[xi] & 1u; }
-    if (sp == 0xFFFFFFFFu && sx == 0xFFFFFFFFu) return 0xFFFFFFFFu;
-    if (sp < sx) { w &= w - 1; return (sp << 1) | cp; }
-    ++xi;
-    return (sx << 1) | cx;
-}
-
-// elements of the mask J(x) = C_s n X(x) in canonical order: ask for element
-// number `want` (0-based) after checking that elements 0..np-1 equal pref[].
-// Returns: -2 prefix mismatch, -1 no such element (mask == prefix), else code.
-__device__ long long mask_query(const Comp &c, const Ctx &C, const uint32_t *candbits,
-                                const uint32_t *pref, int np) {
-    uint32_t w = c.pw;
-    int xi = 0, got = 0;
+// Mask J(x) = C_s n X(x) in canonical order (ascending site, then level):
+// checks that its first np elements equal pref[] and returns the next one.
+// Returns -2 on a prefix mismatch, -1 if the mask equals the prefix.
+__device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *xs, const Ctx &C,
+                                                const uint32_t *candbits, const uint32_t *pref, int np) {
+    uint32_t w = c.pw, xi = 0;
+    int got = 0;
     for (;;) {
-        const uint32_t code = next_site(c, C, w, xi);
+        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
         if (code == 0xFFFFFFFFu) return got == np ? -1 : -2;
         const uint32_t site = code >> 1;
         if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
@@ -436,8 +442,8 @@ __device__ long long mask_query(const Comp &c, const Ctx &C, const uint32_t *can
     }
 }
 
-// does the component hold every element of J? (Theorem 3: K_J is nonzero)
-__device__ bool holds_all(const Comp &c, const Ctx &C, const uint32_t *J, int nJ) {
+// does the component hold every element of J at its level? (K_J nonzero)
+__device__ __forceinline__ bool holds_all(const CompR &c, const uint16_t *xs, const Ctx &C, const uint32_t *J, int nJ) {
     for (int j = 0; j < nJ; ++j) {
         const uint32_t site = J[j] >> 1, isR = J[j] & 1u;
         const uint32_t u = site >> 1;
@@ -448,14 +454,14 @@ __device__ bool holds_all(const Comp &c, const Ctx &C, const uint32_t *J, int nJ
             ok = ((c.pw >> b) & 1u) && (C.enc == QRAM_QUBIT || ((c.pwR >> b) & 1u) == isR);
         } else {
             for (uint32_t q = 0; q < c.nexc; ++q)
-                if ((c.x[q] >> 1) == site) { ok = C.enc == QRAM_QUBIT || (c.x[q] & 1u) == isR; break; }
+                if ((xs[q] >> 1) == site) { ok = C.enc == QRAM_QUBIT || (xs[q] & 1u) == isR; break; }
         }
         if (!ok) return false;
     }
     return true;
 }
 
-__device__ void clear_site(Comp &c, const Ctx &C, uint32_t site) {
+__device__ __forceinline__ void clear_site(CompR &c, uint16_t *xs, const Ctx &C, uint32_t site) {
     const uint32_t u = site >> 1;
     const int L = layer_of(u);
     if (L < C.n && u == path_node(C.i, C.n, L)) {
@@ -464,21 +470,20 @@ __device__ void clear_site(Comp &c, const Ctx &C, uint32_t site) {
         return;
     }
     for (uint32_t q = 0; q < c.nexc; ++q)
-        if ((c.x[q] >> 1) == site) {
-            for (uint32_t r = q; r + 1 < c.nexc; ++r) c.x[r] = c.x[r + 1];
+        if ((xs[q] >> 1) == site) {
+            for (uint32_t r = q; r + 1 < c.nexc; ++r) xs[r] = xs[r + 1];
             --c.nexc;
             return;
         }
 }
 
 // FNV-1a over the sorted (site << 2 | level) list; 0 for the ground state
-__device__ uint64_t config_hash(const Comp &c, const Ctx &C) {
+__device__ __noinline__ uint64_t config_hash(const CompR c, const uint16_t *xs, const Ctx C) {
     if (c.pw == 0 && c.nexc == 0) return 0;
     uint64_t h = 1469598103934665603ull;
-    uint32_t w = c.pw;
-    int xi = 0;
+    uint32_t w = c.pw, xi = 0;
     for (;;) {
-        const uint32_t code = next_site(c, C, w, xi);
+        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
         if (code == 0xFFFFFFFFu) break;
         const uint32_t v = ((code >> 1) << 2) | ((code & 1u) ? 2u : 1u);
         for (int b = 0; b < 4; ++b) { h ^= (v >> (8 * b)) & 0xFFu; h *= 1099511628211ull; }
@@ -491,7 +496,8 @@ __device__ __forceinline__ double apow(const Smem &S, int e) {
     return S.powlo[e & 63] * S.powhi[(e >> 6) & 63];
 }
 
-__device__ __forceinline__ void load_comp(const Scratch &scr, size_t base, uint32_t r, Comp &c, uint32_t &lab) {
+__device__ __forceinline__ void load_comp(const Scratch &scr, size_t base, uint32_t r, CompR &c, uint16_t *xs,
+                                          uint32_t &lab) {
     const size_t g = base + r;
     c.pw = scr.pw[g];
     c.pwR = scr.pwR[g];
@@ -501,25 +507,18 @@ __device__ __forceinline__ void load_comp(const Scratch &scr, size_t base, uint3
     c.cb = st & 0xFFu;
     c.sign = (st >> 8) & 1u;
     c.nexc = (st >> 16) & 0xFFu;
-    for (uint32_t q = 0; q < c.nexc; ++q) c.x[q] = scr.exc[g * kXcap + q];
+    for (uint32_t q = 0; q < c.nexc; ++q) xs[q] = scr.exc[g * kXcap + q];
 }
 
-__device__ __forceinline__ void store_comp(const Scratch &scr, size_t base, uint32_t r, const Comp &c, uint32_t lab) {
+__device__ __forceinline__ void store_comp(const Scratch &scr, size_t base, uint32_t r, const CompR &c,
+                                           const uint16_t *xs, uint32_t lab) {
     const size_t g = base + r;
     scr.pw[g] = c.pw;
     scr.pwR[g] = c.pwR;
     scr.ex[g] = c.e;
     scr.lab[g] = lab;
     scr.st[g] = (c.cb & 0xFFu) | (c.sign << 8) | (c.nexc << 16);
-    for (uint32_t q = 0; q < c.nexc; ++q) scr.exc[g * kXcap + q] = c.x[q];
-}
-
-__device__ __forceinline__ void make_ctx(const Params &P, uint32_t col, Ctx &C) {
-    C.enc = P.enc; C.n = P.n; C.k = P.k; C.T = P.T; C.mem = P.mem;
-    C.i = __ldg(P.addr + col);
-    uint32_t pb = 0;
-    for (int L = 0; L < P.n; ++L) pb |= routed_bit(C.i, P.n, L) << (2 * L);
-    C.PB = pb;
+    for (uint32_t q = 0; q < c.nexc; ++q) scr.exc[g * kXcap + q] = xs[q];
 }
 
 __device__ __forceinline__ double col_w2(const Params &P, uint32_t col) {
@@ -753,12 +752,12 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
     if (S.status == QRAM_OK) {
         for (uint32_t r = threadIdx.x; r < ncomp0; r += NT) {
             const uint32_t col = expl[r >> kb], cw = r & ((1u << kb) - 1u);
-            Comp c;
+            CompR c;
             c.pw = 0; c.pwR = 0; c.e = 0; c.nexc = 0;
             const uint32_t j = __ldg(P.bus + col);
             if (qubit) { c.cb = cw; c.sign = __popc(j & cw) & 1u; }   // first wall: (-1)^(j.c)
             else { c.cb = j; c.sign = 0; }
-            store_comp(scr, cbase, r, c, (col << 8) | cw);
+            store_comp(scr, cbase, r, c, nullptr, (col << 8) | cw);
         }
     }
     if (threadIdx.x == 0) S.ncomp = S.status == QRAM_OK ? ncomp0 : 0;
@@ -790,16 +789,17 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
         for (uint32_t r0 = 0; r0 < ncomp; r0 += NT) {
             const uint32_t r = r0 + threadIdx.x;
             bool alive = r < ncomp;
-            Comp c;
+            CompR c;
+            uint16_t xs[kXcap];
             uint32_t lab = 0;
             Ctx C;
             if (alive) {
-                load_comp(scr, cbase, r, c, lab);
-                make_ctx(P, lab >> 8, C);
+                load_comp(scr, cbase, r, c, xs, lab);
+                C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
                 if (s_prev > 0) {                           // pending K_J of slice s_prev
                     if (nJ > 0) {
-                        alive = holds_all(c, C, S.J, nJ);
-                        if (alive) for (int j = 0; j < nJ; ++j) clear_site(c, C, S.J[j] >> 1);
+                        alive = holds_all(c, xs, C, S.J, nJ);
+                        if (alive) for (int j = 0; j < nJ; ++j) clear_site(c, xs, C, S.J[j] >> 1);
                     }
                     if (alive) c.e += excited_count(c);
                 }
@@ -807,14 +807,14 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
             if (alive) {
                 const int slast = final_epoch ? T - 1 : s1;
                 for (int s = s_prev + 1; s <= slast; ++s) {
-                    if (!apply_slice(P.ops[s], c, C)) { capfail = true; break; }
+                    if (!apply_slice(P.ops[s], c, xs, C)) { capfail = true; break; }
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
                 const double ae = apow(S, c.e);
                 const double w = col_w2(P, lab >> 8) * k2 * ae * ae;
                 if (!final_epoch) {
                     wsum += w;
-                    if (mask_query(c, C, S.candbits, S.J, 0) == -1) wempty += w;
+                    if (mask_query(c, xs, C, S.candbits, S.J, 0) == -1) wempty += w;
                 } else {
                     wsum += w;
                     if (c.pw == 0 && c.nexc == 0) {          // ground tree configuration
@@ -836,7 +836,7 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                             const double sc = (qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0) * ae * (c.sign ? -1.0 : 1.0);
                             P.dump.col[di] = col;
                             P.dump.bus[di] = c.cb;
-                            P.dump.hash[di] = config_hash(c, C);
+                            P.dump.hash[di] = config_hash(c, xs, C);
                             P.dump.re[di] = __ldg(P.amp_re + col) * sc;
                             P.dump.im[di] = __ldg(P.amp_im + col) * sc;
                         }
@@ -846,10 +846,10 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
             if (compact) {
                 uint32_t tot;
                 const uint32_t pre = block_scan_flag(alive, &tot, S);
-                if (alive && !final_epoch) store_comp(scr, cbase, wr + pre, c, lab);
+                if (alive && !final_epoch) store_comp(scr, cbase, wr + pre, c, xs, lab);
                 wr += tot;
             } else if (alive && !final_epoch) {
-                store_comp(scr, cbase, r, c, lab);
+                store_comp(scr, cbase, r, c, xs, lab);
             }
         }
         if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
@@ -925,10 +925,10 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                 if (level > 0) {
                     double we = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        Comp c; uint32_t lab; Ctx C;
-                        load_comp(scr, cbase, r, c, lab);
-                        make_ctx(P, lab >> 8, C);
-                        if (mask_query(c, C, S.candbits, pref, level) == -1) {
+                        CompR c; uint16_t xs[kXcap]; uint32_t lab;
+                        load_comp(scr, cbase, r, c, xs, lab);
+                        const Ctx C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
+                        if (mask_query(c, xs, C, S.candbits, pref, level) == -1) {
                             const double ae = apow(S, c.e);
                             we += col_w2(P, lab >> 8) * k2 * ae * ae;
                         }
@@ -945,10 +945,10 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                     const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
                     double f = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        Comp c; uint32_t lab; Ctx C;
-                        load_comp(scr, cbase, r, c, lab);
-                        make_ctx(P, lab >> 8, C);
-                        const long long q = mask_query(c, C, S.candbits, pref, level);
+                        CompR c; uint16_t xs[kXcap]; uint32_t lab;
+                        load_comp(scr, cbase, r, c, xs, lab);
+                        const Ctx C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
+                        const long long q = mask_query(c, xs, C, S.candbits, pref, level);
                         if (q >= 0 && (uint32_t)q <= cmid) {
                             const double ae = apow(S, c.e);
                             f += col_w2(P, lab >> 8) * k2 * ae * ae;
@@ -963,10 +963,10 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                     // group with weight (the oracle's rule); descend on the largest code
                     uint32_t best = 0xFFFFFFFFu;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        Comp c; uint32_t lab; Ctx C;
-                        load_comp(scr, cbase, r, c, lab);
-                        make_ctx(P, lab >> 8, C);
-                        const long long q = mask_query(c, C, S.candbits, pref, level);
+                        CompR c; uint16_t xs[kXcap]; uint32_t lab;
+                        load_comp(scr, cbase, r, c, xs, lab);
+                        const Ctx C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
+                        const long long q = mask_query(c, xs, C, S.candbits, pref, level);
                         if (q >= 0 && (best == 0xFFFFFFFFu || (uint32_t)q > best)) best = (uint32_t)q;
                     }
                     __shared__ uint32_t sbest;
@@ -1032,6 +1032,11 @@ cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t sme
 }
 
 int kernel_threads() { return NT; }
+int kernel_blocks_per_sm() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, traj_kernel, NT, 0) != cudaSuccess) return 0;
+    return b;
+}
 size_t kernel_smem(int) { return sizeof(Smem); }
 
 // ---------------------------------------------------------------------------
