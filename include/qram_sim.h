@@ -174,6 +174,65 @@ int qram_sync(qram_sim_t *sim);
 /* Number of kernel launches issued by this simulator since creation. */
 uint64_t qram_launch_count(const qram_sim_t *sim);
 
+/* ---------------------------------------------------------------------------
+ * Serving loop (continuous batching; no paper counterpart, the paper runs
+ * one query at a time).  A server owns one device.  Requests are queued by
+ * qram_server_submit (non-blocking, inputs copied) and admitted by a native
+ * scheduler thread while their estimated device memory fits the budget and
+ * fewer than max_active requests run; each admitted request gets its own
+ * simulator, stream and share of the SMs, so requests that arrive while
+ * others run are admitted as memory frees up and their kernels overlap on
+ * the device.  Every trajectory is a pure function of (seed, index, gamma),
+ * so a request's results do not depend on what else runs.
+ * ------------------------------------------------------------------------- */
+typedef struct qram_server qram_server_t;
+
+typedef struct {
+    qram_problem_t problem;    /* copied at submit */
+    uint64_t traj0;            /* first trajectory index */
+    uint32_t ntraj;            /* >= 1 */
+    const double *gamma;       /* host, ntraj damping rates in [0, 1) (copied) */
+    int32_t mode;              /* 0 pruned, 1 full */
+} qram_request_t;
+
+typedef struct {
+    uint64_t id;
+    int32_t status;            /* QRAM_OK, a QRAM_E_* code, or QRAM_E_STATE if cancelled */
+    uint32_t ntraj;
+    double mean_fidelity, stderr_fidelity;   /* qram_fidelity over the request */
+    double t_submit, t_admit, t_finish;      /* seconds on the server's steady clock */
+    uint64_t device_bytes;     /* device memory the request held */
+} qram_completion_t;
+
+/* Create a server on `device` with a device-memory budget in bytes and at
+ * most max_active concurrently running requests (>= 1). */
+int qram_server_create(size_t mem_budget, int device, uint32_t max_active, qram_server_t **out);
+
+/* Queue a request; *id receives its identifier.  QRAM_E_ARG for a malformed
+ * request (same checks as qram_sim_create, gamma outside [0,1)), QRAM_E_OOM
+ * if it could never fit the budget, QRAM_E_BUSY if 65536 requests wait. */
+int qram_server_submit(qram_server_t *srv, const qram_request_t *req, uint64_t *id);
+
+/* Copy up to `max` completions (oldest first) into out; *count receives the
+ * number copied.  Non-blocking. */
+int qram_server_poll(qram_server_t *srv, qram_completion_t *out, uint32_t max, uint32_t *count);
+
+/* Per-trajectory results of a completed request (host array of cap
+ * entries); releases them.  QRAM_E_STATE if the id is unknown or pending. */
+int qram_server_results(qram_server_t *srv, uint64_t id, qram_result_t *out, uint32_t cap);
+
+/* Cancel a request: a queued one is dropped, a running one stops taking new
+ * trajectories (the trajectories in flight finish); it completes with status
+ * QRAM_E_STATE.  QRAM_E_STATE if the id is unknown or already complete. */
+int qram_server_cancel(qram_server_t *srv, uint64_t id);
+
+/* Wait (bounded by timeout_s) until no request is queued or running;
+ * QRAM_E_TIMEOUT if the time ran out. */
+int qram_server_drain(qram_server_t *srv, double timeout_s);
+
+/* Stop the scheduler (running requests finish first) and free everything. */
+void qram_server_destroy(qram_server_t *srv);
+
 /* Static message for a QRAM_* code. */
 const char *qram_strerror(int code);
 

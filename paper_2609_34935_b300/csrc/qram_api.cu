@@ -139,41 +139,52 @@ void cand_caps(int n, int k, double gmax, uint32_t *cand_cap, uint32_t *seg_cap)
     *seg_cap = cap(per);
 }
 
-int ensure_scratch(qram_sim *S, double gmax) {
-    uint32_t cc, sc;
-    cand_caps(S->n, S->k, gmax, &cc, &sc);
-    const uint32_t ecap = (uint32_t)S->D << (S->enc == QRAM_QUBIT ? S->k : 0);
-    if (S->scratch && S->scr.cand_cap >= cc && S->scr.seg_cap >= sc && S->scr.ecap >= ecap) return QRAM_OK;
-    if (S->scratch) { cudaFree(S->scratch); S->scratch = nullptr; }
+struct Layout {
+    size_t o_cand, o_seg, o_expl, o_pw, o_pwR, o_ex, o_lab, o_st, o_exc, total;
+    uint32_t cc, sc, ecap;
+};
+
+Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax) {
+    Layout L;
+    cand_caps(n, k, gmax, &L.cc, &L.sc);
+    L.ecap = (uint32_t)D << (enc == QRAM_QUBIT ? k : 0);
     const int NWARP = kernel_threads() / 32;
-    const size_t slots = (size_t)S->slots;
     size_t off = 0;
-    const size_t o_cand = off; off = align_up(off + slots * cc * 4);
-    const size_t o_seg = off; off = align_up(off + slots * NWARP * (size_t)sc * 4);
-    const size_t o_expl = off; off = align_up(off + slots * (size_t)S->D * 4);
-    const size_t o_pw = off; off = align_up(off + slots * (size_t)ecap * 4);
-    const size_t o_pwR = off; off = align_up(off + slots * (size_t)ecap * 4);
-    const size_t o_ex = off; off = align_up(off + slots * (size_t)ecap * 4);
-    const size_t o_lab = off; off = align_up(off + slots * (size_t)ecap * 4);
-    const size_t o_st = off; off = align_up(off + slots * (size_t)ecap * 4);
-    const size_t o_exc = off; off = align_up(off + slots * (size_t)ecap * kXcap * 2);
+    L.o_cand = off; off = align_up(off + slots * L.cc * 4);
+    L.o_seg = off; off = align_up(off + slots * NWARP * (size_t)L.sc * 4);
+    L.o_expl = off; off = align_up(off + slots * (size_t)D * 4);
+    L.o_pw = off; off = align_up(off + slots * (size_t)L.ecap * 4);
+    L.o_pwR = off; off = align_up(off + slots * (size_t)L.ecap * 4);
+    L.o_ex = off; off = align_up(off + slots * (size_t)L.ecap * 4);
+    L.o_lab = off; off = align_up(off + slots * (size_t)L.ecap * 4);
+    L.o_st = off; off = align_up(off + slots * (size_t)L.ecap * 4);
+    L.o_exc = off; off = align_up(off + slots * (size_t)L.ecap * kXcap * 2);
+    L.total = off;
+    return L;
+}
+
+int ensure_scratch(qram_sim *S, double gmax) {
+    const Layout L = scratch_layout(S->enc, S->n, S->k, S->D, (size_t)S->slots, gmax);
+    if (S->scratch && S->scr.cand_cap >= L.cc && S->scr.seg_cap >= L.sc && S->scr.ecap >= L.ecap) return QRAM_OK;
+    // stream-ordered: no device-wide synchronisation, so other work keeps running
+    if (S->scratch) { cudaFreeAsync(S->scratch, S->stream); S->scratch = nullptr; }
     void *p = nullptr;
-    if (!ok(cudaMalloc(&p, off))) { cudaGetLastError(); return QRAM_E_OOM; }
+    if (!ok(cudaMallocAsync(&p, L.total, S->stream))) { cudaGetLastError(); return QRAM_E_OOM; }
     char *b = (char *)p;
     S->scratch = p;
-    S->scratch_bytes = off;
-    S->scr.cand = (uint32_t *)(b + o_cand);
-    S->scr.wseg = (uint32_t *)(b + o_seg);
-    S->scr.expl = (uint32_t *)(b + o_expl);
-    S->scr.pw = (uint32_t *)(b + o_pw);
-    S->scr.pwR = (uint32_t *)(b + o_pwR);
-    S->scr.ex = (int32_t *)(b + o_ex);
-    S->scr.lab = (uint32_t *)(b + o_lab);
-    S->scr.st = (uint32_t *)(b + o_st);
-    S->scr.exc = (uint16_t *)(b + o_exc);
-    S->scr.cand_cap = cc;
-    S->scr.seg_cap = sc;
-    S->scr.ecap = ecap;
+    S->scratch_bytes = L.total;
+    S->scr.cand = (uint32_t *)(b + L.o_cand);
+    S->scr.wseg = (uint32_t *)(b + L.o_seg);
+    S->scr.expl = (uint32_t *)(b + L.o_expl);
+    S->scr.pw = (uint32_t *)(b + L.o_pw);
+    S->scr.pwR = (uint32_t *)(b + L.o_pwR);
+    S->scr.ex = (int32_t *)(b + L.o_ex);
+    S->scr.lab = (uint32_t *)(b + L.o_lab);
+    S->scr.st = (uint32_t *)(b + L.o_st);
+    S->scr.exc = (uint16_t *)(b + L.o_exc);
+    S->scr.cand_cap = L.cc;
+    S->scr.seg_cap = L.sc;
+    S->scr.ecap = L.ecap;
     return QRAM_OK;
 }
 
@@ -240,6 +251,21 @@ int run_mode(qram_sim *S, int mode, uint64_t traj0, uint32_t ntraj, const double
 
 }  // namespace
 
+namespace qram {
+
+size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax) {
+    const size_t prob = (size_t(1) << n) + (size_t)D * 24 + 4096;
+    return prob + scratch_layout(enc, n, k, D, (size_t)slots, gmax).total;
+}
+
+int resident_slots_per_device(int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    return sms * kernel_blocks_per_sm();
+}
+
+}  // namespace qram
+
 extern "C" {
 
 const char *qram_strerror(int code) {
@@ -291,18 +317,21 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     S->blocks_per_sm = kernel_blocks_per_sm();
     if (S->blocks_per_sm < 1) { delete S; return QRAM_E_CUDA; }
     S->slots = S->sms * S->blocks_per_sm;
-    if (!ok(cudaMalloc(&S->d_mem, N)) || !ok(cudaMalloc(&S->d_addr, D * 4)) || !ok(cudaMalloc(&S->d_bus, D * 4)) ||
-        !ok(cudaMalloc(&S->d_re, D * 8)) || !ok(cudaMalloc(&S->d_im, D * 8)) ||
-        !ok(cudaMalloc(&S->d_work, 64)) || !ok(cudaMalloc(&S->d_fid2, 16)) || !ok(cudaMalloc(&S->d_gmax, 8))) {
+    cudaStream_t st = S->stream;
+    if (!ok(cudaMallocAsync((void **)&S->d_mem, N, st)) || !ok(cudaMallocAsync((void **)&S->d_addr, D * 4, st)) ||
+        !ok(cudaMallocAsync((void **)&S->d_bus, D * 4, st)) || !ok(cudaMallocAsync((void **)&S->d_re, D * 8, st)) ||
+        !ok(cudaMallocAsync((void **)&S->d_im, D * 8, st)) || !ok(cudaMallocAsync((void **)&S->d_work, 64, st)) ||
+        !ok(cudaMallocAsync((void **)&S->d_fid2, 16, st)) || !ok(cudaMallocAsync((void **)&S->d_gmax, 8, st))) {
         cudaGetLastError();
         qram_sim_destroy(S);
         return QRAM_E_OOM;
     }
-    if (!ok(cudaMemcpy(S->d_mem, p->memory, N, cudaMemcpyHostToDevice)) ||
-        !ok(cudaMemcpy(S->d_addr, p->addr, D * 4, cudaMemcpyHostToDevice)) ||
-        !ok(cudaMemcpy(S->d_bus, p->bus, D * 4, cudaMemcpyHostToDevice)) ||
-        !ok(cudaMemcpy(S->d_re, p->amp_re, D * 8, cudaMemcpyHostToDevice)) ||
-        !ok(cudaMemcpy(S->d_im, p->amp_im, D * 8, cudaMemcpyHostToDevice)))
+    // pageable sources: each copy returns once the host data is staged
+    if (!ok(cudaMemcpyAsync(S->d_mem, p->memory, N, cudaMemcpyHostToDevice, st)) ||
+        !ok(cudaMemcpyAsync(S->d_addr, p->addr, D * 4, cudaMemcpyHostToDevice, st)) ||
+        !ok(cudaMemcpyAsync(S->d_bus, p->bus, D * 4, cudaMemcpyHostToDevice, st)) ||
+        !ok(cudaMemcpyAsync(S->d_re, p->amp_re, D * 8, cudaMemcpyHostToDevice, st)) ||
+        !ok(cudaMemcpyAsync(S->d_im, p->amp_im, D * 8, cudaMemcpyHostToDevice, st)))
         rc = QRAM_E_CUDA;
     if (rc) { qram_sim_destroy(S); return rc; }
     *out = S;
@@ -313,10 +342,10 @@ void qram_sim_destroy(qram_sim_t *S) {
     if (!S) return;
     {
         DeviceGuard g(S->device);
-        if (S->stream) cudaStreamSynchronize(S->stream); else cudaDeviceSynchronize();
-        cudaFree(S->d_mem); cudaFree(S->d_addr); cudaFree(S->d_bus); cudaFree(S->d_re); cudaFree(S->d_im);
-        cudaFree(S->d_work); cudaFree(S->d_fid2); cudaFree(S->d_gmax);
-        if (S->scratch) cudaFree(S->scratch);
+        cudaStream_t st = S->stream;
+        void *bufs[] = {S->d_mem, S->d_addr, S->d_bus, S->d_re, S->d_im, S->d_work, S->d_fid2, S->d_gmax, S->scratch};
+        for (void *b : bufs) if (b) cudaFreeAsync(b, st);
+        cudaStreamSynchronize(st);
         cudaGetLastError();
     }
     delete S;
@@ -360,8 +389,7 @@ int qram_set_launch_ctas(qram_sim_t *S, uint32_t nctas) {
     const int want = nctas == 0 ? full : (int)std::min<uint32_t>(nctas, (uint32_t)full);
     if (want != S->slots) {
         DeviceGuard g(S->device);
-        if (S->stream) cudaStreamSynchronize(S->stream); else cudaDeviceSynchronize();
-        if (S->scratch) { cudaFree(S->scratch); S->scratch = nullptr; }
+        if (S->scratch) { cudaFreeAsync(S->scratch, S->stream); S->scratch = nullptr; }
         S->slots = want;
     }
     return QRAM_OK;
@@ -459,5 +487,17 @@ int qram_sync(qram_sim_t *S) {
 }
 
 uint64_t qram_launch_count(const qram_sim_t *S) { return S ? S->launches : 0; }
+
+// Stop a running launch of this simulator from taking new trajectories: the
+// work counter is raised past any trajectory count (the CTAs finish the
+// trajectory in hand and exit).  Issued on `ctrl`, a stream other than the
+// simulator's.  Not part of the C ABI (used by the serving loop).
+int qram_internal_cancel(qram_sim_t *S, void *ctrl) {
+    static const uint32_t big = 0x7FFFFFFFu;
+    if (!S) return QRAM_E_ARG;
+    DeviceGuard g(S->device);
+    if (!ok(cudaMemcpyAsync(S->d_work, &big, 4, cudaMemcpyHostToDevice, (cudaStream_t)ctrl))) return QRAM_E_CUDA;
+    return QRAM_OK;
+}
 
 }  // extern "C"

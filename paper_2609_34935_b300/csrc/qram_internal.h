@@ -81,6 +81,10 @@ cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *ou
 cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n, uint32_t cap,
                                  uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
                                  double *o_im, cudaStream_t s);
+// host-side helpers shared by the API and the serving loop
+size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax);
+int resident_slots_per_device(int device);
+
 int kernel_threads();
 int kernel_blocks_per_sm();
 size_t kernel_smem(int n);
