@@ -50,7 +50,8 @@ enum {
     QRAM_E_TIMEOUT = 4,  /* a bounded device wait gave up */
     QRAM_E_BUSY = 5,     /* server queue full / resource busy */
     QRAM_E_CAP = 6,      /* a per-trajectory capacity was exceeded (result marked) */
-    QRAM_E_STATE = 7     /* call not valid in the current state */
+    QRAM_E_STATE = 7,    /* call not valid in the current state */
+    QRAM_E_TOOBIG = 8    /* problem exceeds the static scratch of qram_run_static */
 };
 
 enum { QRAM_QUTRIT = 0, QRAM_QUBIT = 1 };
@@ -232,6 +233,37 @@ int qram_server_drain(qram_server_t *srv, double timeout_s);
 
 /* Stop the scheduler (running requests finish first) and free everything. */
 void qram_server_destroy(qram_server_t *srv);
+
+/* Allocation-free run (no counterpart in the paper; the paper's simulator
+ * is a CPU program).  For callers that must not allocate device memory at
+ * run time: a host with a fixed device-memory plan made at start-up, code
+ * that runs inside another framework's memory pool and may not go around
+ * it, or a process whose device memory is already handed out.  Runs the same
+ * kernel as qram_run_pruned (mode 0) or qram_run_full (mode 1) on one
+ * problem held entirely in caller-owned DEVICE memory:
+ *   memory[2^n], addr[D], bus[D], amp_re[D], amp_im[D]  (as in qram_problem_t)
+ *   gamma[ntraj] in [0, 1), out[ntraj]  (as in qram_run_pruned)
+ * gamma_max (host) bounds the damping rates (sizes the candidate scratch; a
+ * trajectory above it that overflows is reported QRAM_E_CAP).  The inputs
+ * are validated on the device; invalid ones make every trajectory report
+ * QRAM_E_ARG.  Stream-ordered on cuda_stream (a cudaStream_t, may be NULL)
+ * of the current device; returns once enqueued.
+ *
+ * Scratch: one file-scope device array of 32 MiB per GPU that loads the
+ * library, held until the process exits.  The call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  Problems whose
+ * scratch for one CTA exceeds the array are rejected with QRAM_E_TOOBIG;
+ * smaller ones use as many CTAs as fit.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress): make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * last call's contents (the call resets what must start at zero itself), so
+ * calls that overlap on the GPU (different streams or devices' contexts
+ * sharing a device) race: order them on one stream. */
+int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k, int32_t num_branches,
+                    const uint8_t *memory, const uint32_t *addr, const uint32_t *bus,
+                    const double *amp_re, const double *amp_im, uint64_t seed, uint64_t traj0,
+                    uint32_t ntraj, const double *gamma, double gamma_max, qram_result_t *out,
+                    void *cuda_stream);
 
 /* Static message for a QRAM_* code. */
 const char *qram_strerror(int code);

@@ -64,7 +64,7 @@ struct SlotUse {
 // 2l+1, walks down one layer per slice, settles in the router of layer l at
 // 3l+2 and returns along the mirror image s -> T-s; data qubit t enters at
 // 2n+2t+1, is fetched at the leaf layer at 3n+2t+1 and leaves at 4n+2t+1.
-int build_ops(int n, int k, SliceOps *ops) {
+int build_ops_impl(int n, int k, SliceOps *ops) {
     const int T = 6 * n + 2 * k;
     for (int s = 0; s < kMaxT; ++s) { ops[s].load = -1; ops[s].bus = -1; ops[s].fetch = -1; ops[s].pad = 0; ops[s].iswap = 0; ops[s].cswap = 0; }
     auto set8 = [](int8_t &f, int v) { if (f >= 0 && f != v) return false; f = (int8_t)v; return true; };
@@ -253,6 +253,28 @@ int run_mode(qram_sim *S, int mode, uint64_t traj0, uint32_t ntraj, const double
 
 namespace qram {
 
+int build_ops(int n, int k, SliceOps *ops) { return build_ops_impl(n, k, ops); }
+
+size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void *base, Scratch *scr) {
+    const Layout L = scratch_layout(enc, n, k, D, (size_t)slots, gmax);
+    if (base) {
+        char *b = (char *)base;
+        scr->cand = (uint32_t *)(b + L.o_cand);
+        scr->wseg = (uint32_t *)(b + L.o_seg);
+        scr->expl = (uint32_t *)(b + L.o_expl);
+        scr->pw = (uint32_t *)(b + L.o_pw);
+        scr->pwR = (uint32_t *)(b + L.o_pwR);
+        scr->ex = (int32_t *)(b + L.o_ex);
+        scr->lab = (uint32_t *)(b + L.o_lab);
+        scr->st = (uint32_t *)(b + L.o_st);
+        scr->exc = (uint16_t *)(b + L.o_exc);
+        scr->cand_cap = L.cc;
+        scr->seg_cap = L.sc;
+        scr->ecap = L.ecap;
+    }
+    return L.total;
+}
+
 size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax) {
     const size_t prob = (size_t(1) << n) + (size_t)D * 24 + 4096;
     return prob + scratch_layout(enc, n, k, D, (size_t)slots, gmax).total;
@@ -278,6 +300,7 @@ const char *qram_strerror(int code) {
     case QRAM_E_BUSY: return "busy";
     case QRAM_E_CAP: return "per-trajectory capacity exceeded";
     case QRAM_E_STATE: return "invalid state";
+    case QRAM_E_TOOBIG: return "problem exceeds the static scratch of the allocation-free entry point";
     default: return "unknown error";
     }
 }
@@ -309,7 +332,7 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     S->stream = (cudaStream_t)cuda_stream;
     S->enc = p->encoding; S->n = p->n; S->k = p->k; S->D = p->num_branches; S->T = 6 * p->n + 2 * p->k;
     S->seed = p->seed;
-    if (build_ops(S->n, S->k, S->ops) != QRAM_OK) { delete S; return QRAM_E_ARG; }
+    if (build_ops_impl(S->n, S->k, S->ops) != QRAM_OK) { delete S; return QRAM_E_ARG; }
     DeviceGuard g(device);
     int rc = QRAM_OK;
     const size_t D = (size_t)S->D;

@@ -73,6 +73,7 @@ struct Params {
     uint32_t *work;       // work-stealing counter
     DumpOut dump;
     int dump_mode;
+    const uint32_t *input_error;   // if non-null and nonzero at run time: every trajectory is QRAM_E_ARG
     SliceOps ops[kMaxT];
 };
 
@@ -83,6 +84,9 @@ cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n
                                  double *o_im, cudaStream_t s);
 // host-side helpers shared by the API and the serving loop
 size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax);
+int build_ops(int n, int k, SliceOps *ops);
+// lays out the per-slot scratch of `slots` CTAs at `base` (may be null: size only); returns bytes
+size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void *base, Scratch *scr);
 int resident_slots_per_device(int device);
 
 int kernel_threads();

@@ -573,8 +573,18 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
     const size_t slot = blockIdx.x;
     const Scratch &scr = P.scr;
     uint32_t *cand = scr.cand + slot * scr.cand_cap;
-    const bool valid = gamma >= 0.0 && gamma < 1.0;
+    const bool valid = gamma >= 0.0 && gamma < 1.0 && !(P.input_error && *P.input_error);
 
+    if (P.input_error && *P.input_error) {          // inputs failed validation: touch nothing else
+        if (threadIdx.x == 0 && P.out) {
+            qram_result_t R;
+            memset(&R, 0, sizeof(R));
+            R.ref = -1;
+            R.status = QRAM_E_ARG;
+            P.out[t] = R;
+        }
+        return;
+    }
     if (threadIdx.x == 0) { S.status = valid ? QRAM_OK : QRAM_E_ARG; S.refcol = -1; S.nbad = 0; S.nJ = 0; }
     for (int w = threadIdx.x; w < 512; w += NT) S.badbits[w] = 0;
     for (int w = threadIdx.x; w < 1024; w += NT) S.candbits[w] = 0;
