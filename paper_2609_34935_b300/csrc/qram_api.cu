@@ -32,6 +32,7 @@ struct qram_sim {
     uint32_t *d_work = nullptr;
     double *d_fid2 = nullptr;
     double *d_gmax = nullptr;
+    double *d_w2u = nullptr;
     const uint32_t *hist_cand = nullptr, *hist_off = nullptr;
     uint32_t nhist = 0;
     SliceOps ops[kMaxT]{};
@@ -140,8 +141,8 @@ void cand_caps(int n, int k, double gmax, uint32_t *cand_cap, uint32_t *seg_cap)
 }
 
 struct Layout {
-    size_t o_cand, o_seg, o_expl, o_pw, o_pwR, o_ex, o_lab, o_st, o_exc, total;
-    uint32_t cc, sc, ecap;
+    size_t o_cand, o_seg, o_expl, o_pw, o_pwR, o_ex, o_lab, o_st, o_exc, o_selk, o_selw, total;
+    uint32_t cc, sc, ecap, selseg;
 };
 
 Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax) {
@@ -159,6 +160,10 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax) {
     L.o_lab = off; off = align_up(off + slots * (size_t)L.ecap * 4);
     L.o_st = off; off = align_up(off + slots * (size_t)L.ecap * 4);
     L.o_exc = off; off = align_up(off + slots * (size_t)L.ecap * kXcap * 2);
+    // per-warp segments: warp w sees at most ceil(ecap / threads) * 32 components
+    L.selseg = (uint32_t)(((size_t)L.ecap + kernel_threads() - 1) / kernel_threads() * 32);
+    L.o_selk = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 4);
+    L.o_selw = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 8);
     L.total = off;
     return L;
 }
@@ -182,6 +187,9 @@ int ensure_scratch(qram_sim *S, double gmax) {
     S->scr.lab = (uint32_t *)(b + L.o_lab);
     S->scr.st = (uint32_t *)(b + L.o_st);
     S->scr.exc = (uint16_t *)(b + L.o_exc);
+    S->scr.selk = (uint32_t *)(b + L.o_selk);
+    S->scr.selw = (double *)(b + L.o_selw);
+    S->scr.selseg = L.selseg;
     S->scr.cand_cap = L.cc;
     S->scr.seg_cap = L.sc;
     S->scr.ecap = L.ecap;
@@ -211,6 +219,7 @@ Params base_params(qram_sim *S) {
     P.hist_cand = S->hist_cand; P.hist_off = S->hist_off; P.nhist = S->nhist;
     P.scr = S->scr;
     P.work = S->d_work;
+    P.w2u = S->d_w2u;
     std::memcpy(P.ops, S->ops, sizeof(P.ops));
     return P;
 }
@@ -268,6 +277,9 @@ size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void 
         scr->lab = (uint32_t *)(b + L.o_lab);
         scr->st = (uint32_t *)(b + L.o_st);
         scr->exc = (uint16_t *)(b + L.o_exc);
+        scr->selk = (uint32_t *)(b + L.o_selk);
+        scr->selw = (double *)(b + L.o_selw);
+        scr->selseg = L.selseg;
         scr->cand_cap = L.cc;
         scr->seg_cap = L.sc;
         scr->ecap = L.ecap;
@@ -344,7 +356,8 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     if (!ok(cudaMallocAsync((void **)&S->d_mem, N, st)) || !ok(cudaMallocAsync((void **)&S->d_addr, D * 4, st)) ||
         !ok(cudaMallocAsync((void **)&S->d_bus, D * 4, st)) || !ok(cudaMallocAsync((void **)&S->d_re, D * 8, st)) ||
         !ok(cudaMallocAsync((void **)&S->d_im, D * 8, st)) || !ok(cudaMallocAsync((void **)&S->d_work, 64, st)) ||
-        !ok(cudaMallocAsync((void **)&S->d_fid2, 16, st)) || !ok(cudaMallocAsync((void **)&S->d_gmax, 8, st))) {
+        !ok(cudaMallocAsync((void **)&S->d_fid2, 16, st)) || !ok(cudaMallocAsync((void **)&S->d_gmax, 8, st)) ||
+        !ok(cudaMallocAsync((void **)&S->d_w2u, 8, st))) {
         cudaGetLastError();
         qram_sim_destroy(S);
         return QRAM_E_OOM;
@@ -356,6 +369,9 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
         !ok(cudaMemcpyAsync(S->d_re, p->amp_re, D * 8, cudaMemcpyHostToDevice, st)) ||
         !ok(cudaMemcpyAsync(S->d_im, p->amp_im, D * 8, cudaMemcpyHostToDevice, st)))
         rc = QRAM_E_CUDA;
+    if (!rc && !ok(launch_uniform_weight(S->d_re, S->d_im, S->D, S->enc == QRAM_QUBIT ? S->k : 0, S->d_w2u, st)))
+        rc = QRAM_E_CUDA;
+    if (!rc) S->launches++;
     if (rc) { qram_sim_destroy(S); return rc; }
     *out = S;
     return QRAM_OK;
@@ -366,7 +382,7 @@ void qram_sim_destroy(qram_sim_t *S) {
     {
         DeviceGuard g(S->device);
         cudaStream_t st = S->stream;
-        void *bufs[] = {S->d_mem, S->d_addr, S->d_bus, S->d_re, S->d_im, S->d_work, S->d_fid2, S->d_gmax, S->scratch};
+        void *bufs[] = {S->d_mem, S->d_addr, S->d_bus, S->d_re, S->d_im, S->d_work, S->d_fid2, S->d_gmax, S->d_w2u, S->scratch};
         for (void *b : bufs) if (b) cudaFreeAsync(b, st);
         cudaStreamSynchronize(st);
         cudaGetLastError();

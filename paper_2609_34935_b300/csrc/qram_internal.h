@@ -13,6 +13,9 @@ constexpr int kMaxK = 8;
 constexpr int kMaxT = 6 * kMaxN + 2 * kMaxK;   // 100
 constexpr int kXcap = 32;                      // off-path excitations per component
 constexpr int kMaxJ = 64;                      // elements of one joint outcome J
+// Damping exponents are bounded by (2n+k)(T-1) (at most 2n+k excited sites
+// per slice); histograms over them need (2n+k)(T-1)+1 <= 3565 bins.
+constexpr int kHistMax = 3584;
 
 enum Mode : int { kPruned = 0, kFull = 1, kSampleOnly = 2 };
 
@@ -39,7 +42,9 @@ struct Scratch {
     uint32_t *lab;       // [slots][ecap] (column << 8) | first-wall bus word c
     uint32_t *st;        // [slots][ecap] bus word (bits 0-7) | sign (bit 8) | nexc (bits 16-23)
     uint16_t *exc;       // [slots][ecap][kXcap] off-path sites (site << 1 | isR)
-    uint32_t cand_cap, seg_cap, ecap;
+    uint32_t *selk;      // [slots][nwarps][selseg] components with a non-empty mask: first code | size << 16
+    double *selw;        // [slots][nwarps][selseg] their weights
+    uint32_t cand_cap, seg_cap, ecap, selseg;
 };
 
 struct DumpOut {
@@ -74,11 +79,13 @@ struct Params {
     DumpOut dump;
     int dump_mode;
     const uint32_t *input_error;   // if non-null and nonzero at run time: every trajectory is QRAM_E_ARG
+    const double *w2u;             // device scalar: |c|^2 (times 2^-k for qubits) when every column shares it, else 0
     SliceOps ops[kMaxT];
 };
 
 cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s);
+cudaError_t launch_uniform_weight(const double *re, const double *im, int D, int qubit_k, double *out, cudaStream_t s);
 cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n, uint32_t cap,
                                  uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
                                  double *o_im, cudaStream_t s);

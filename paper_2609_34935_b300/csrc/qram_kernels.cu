@@ -106,6 +106,7 @@ struct Smem {
     double redA[NW], redB[NW], redC[NW];
     uint32_t scanw[NW];
     uint32_t wcount[NW];
+    uint32_t segn[NW];             // entries of each warp's compact selection segment
     uint32_t J[kMaxJ];
     int nJ;
     uint32_t nexpl, ncomp, ncand;
@@ -442,6 +443,22 @@ __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *
     }
 }
 
+// first element (code) of the mask J(x) = C_s n X(x) and its size; the
+// code is 0xFFFF... when the mask is empty
+__device__ __forceinline__ uint32_t mask_first(const CompR &c, const uint16_t *xs, const Ctx &C,
+                                               const uint32_t *candbits, uint32_t &cnt) {
+    uint32_t w = c.pw, xi = 0, first = 0xFFFFFFFFu;
+    cnt = 0;
+    for (;;) {
+        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
+        if (code == 0xFFFFFFFFu) return first;
+        const uint32_t site = code >> 1;
+        if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+        if (cnt == 0) first = code;
+        ++cnt;
+    }
+}
+
 // does the component hold every element of J at its level? (K_J nonzero)
 __device__ __forceinline__ bool holds_all(const CompR &c, const uint16_t *xs, const Ctx &C, const uint32_t *J, int nJ) {
     for (int j = 0; j < nJ; ++j) {
@@ -565,7 +582,7 @@ __device__ double data_norm2(const Params &P, const Smem &S, int s) {
 
 // ---------------------------------------------------------------------------
 // one trajectory
-__device__ void run_one(const Params &P, Smem &S, uint32_t t) {
+__device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
     const uint64_t traj = P.traj0 + t;
     const double gamma = P.gamma[t];
     const int n = P.n, T = P.T;
@@ -774,6 +791,13 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
     __syncthreads();
 
     // ---- 4. epochs ----------------------------------------------------------
+    // equal-magnitude inputs: weights are w2u * a^(2e), summed as integer
+    // histograms over e (all, empty mask / ground, signed overlap)
+    const double w2u = P.w2u ? *P.w2u : 0.0;
+    const bool uni = w2u > 0.0;
+    const int H = (2 * n + P.k) * (T - 1) + 1;
+    uint32_t *hall = hist, *hemp = hist + kHistMax;
+    int32_t *hov = (int32_t *)(hist + 2 * kHistMax);
     int s_prev = 0;              // slice whose damping is pending (0: none)
     bool jumped = false;
     uint32_t jumps = 0, first_jump = 0, jump_sites = 0;
@@ -796,12 +820,19 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
         double wsum = 0.0, wempty = 0.0, ovl = 0.0;
         uint32_t wr = 0;        // write cursor (compaction)
         bool capfail = false;
+        // this warp's segment of the compact list of components with a non-empty mask
+        const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+        uint32_t *selk = scr.selk + (slot * NW + warp) * (size_t)scr.selseg;
+        double *selw = scr.selw + (slot * NW + warp) * (size_t)scr.selseg;
+        uint32_t wcur = 0;
         for (uint32_t r0 = 0; r0 < ncomp; r0 += NT) {
             const uint32_t r = r0 + threadIdx.x;
             bool alive = r < ncomp;
             CompR c;
             uint16_t xs[kXcap];
-            uint32_t lab = 0;
+            uint32_t lab = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
+            double w = 0.0;
+            uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | empty/ground << 2 | overlap sign + 1
             Ctx C;
             if (alive) {
                 load_comp(scr, cbase, r, c, xs, lab);
@@ -821,23 +852,36 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
                 const double ae = apow(S, c.e);
-                const double w = col_w2(P, lab >> 8) * k2 * ae * ae;
+                if (uni && c.e >= H) capfail = true;                 // exponent bound violated
                 if (!final_epoch) {
-                    wsum += w;
-                    if (mask_query(c, xs, C, S.candbits, S.J, 0) == -1) wempty += w;
+                    c1 = mask_first(c, xs, C, S.candbits, mcnt);
+                    if (!uni) {
+                        w = col_w2(P, lab >> 8) * k2 * ae * ae;
+                        wsum += w;
+                        if (mcnt == 0) wempty += w;
+                    } else {
+                        if (mcnt > 0) w = w2u * ae * ae;
+                        if (c.e < H) hkey = ((uint32_t)c.e << 3) | ((mcnt == 0 ? 1u : 0u) << 2) | 1u;
+                    }
                 } else {
-                    wsum += w;
-                    if (c.pw == 0 && c.nexc == 0) {          // ground tree configuration
-                        wempty += w;
+                    int ovs = 0;
+                    const bool ground = c.pw == 0 && c.nexc == 0;     // ground tree configuration
+                    if (ground) {
                         const uint32_t col = lab >> 8;
                         if (qubit) {
                             const uint32_t bout = __ldg(P.bus + col) ^ __ldg(P.mem + C.i);
-                            const uint32_t par = (c.sign + __popc(c.cb & bout)) & 1u;
-                            const double term = col_w2(P, col) * k2 * ae;
-                            ovl += par ? -term : term;
+                            ovs = ((c.sign + __popc(c.cb & bout)) & 1u) ? -1 : 1;
                         } else if (c.cb == (__ldg(P.bus + col) ^ __ldg(P.mem + C.i))) {
-                            ovl += col_w2(P, col) * ae;
+                            ovs = 1;
                         }
+                    }
+                    if (!uni) {
+                        w = col_w2(P, lab >> 8) * k2 * ae * ae;
+                        wsum += w;
+                        if (ground) wempty += w;
+                        if (ovs) ovl += ovs * (col_w2(P, lab >> 8) * k2 * ae);
+                    } else if (c.e < H) {
+                        hkey = ((uint32_t)c.e << 3) | ((ground ? 1u : 0u) << 2) | (uint32_t)(ovs + 1);
                     }
                     if (P.dump_mode && threadIdx.x < NT) {
                         const uint32_t di = atomicAdd(P.dump.count, 1u);
@@ -853,6 +897,27 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                     }
                 }
             }
+            if (uni) {
+                // warp-aggregated histogram update (equal keys add once)
+                const uint32_t grp = __match_any_sync(0xFFFFFFFFu, hkey);
+                if (hkey != 0xFFFFFFFFu && (int)lane == __ffs(grp) - 1) {
+                    const uint32_t cnt = __popc(grp), e = hkey >> 3;
+                    atomicAdd(&hall[e], cnt);
+                    if ((hkey >> 2) & 1u) atomicAdd(&hemp[e], cnt);
+                    const int ovs = (int)(hkey & 3u) - 1;
+                    if (ovs) atomicAdd(&hov[e], ovs * (int)cnt);
+                }
+            }
+            {
+                const bool ne = alive && !final_epoch && mcnt > 0;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ne);
+                if (ne) {
+                    const uint32_t pos = wcur + __popc(bal & ((1u << lane) - 1u));
+                    selk[pos] = (c1 & 0xFFFFu) | (mcnt << 16);
+                    selw[pos] = w;
+                }
+                wcur += __popc(bal);
+            }
             if (compact) {
                 uint32_t tot;
                 const uint32_t pre = block_scan_flag(alive, &tot, S);
@@ -862,6 +927,7 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                 store_comp(scr, cbase, r, c, xs, lab);
             }
         }
+        if (lane == 0) S.segn[warp] = wcur;
         if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
         __syncthreads();
         if (threadIdx.x == 0 && compact) S.ncomp = wr;
@@ -890,7 +956,23 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
                 }
             }
         }
+        if (uni) {
+            // fold the histograms (and leave them zero for the next epoch)
+            __syncthreads();
+            for (int b = threadIdx.x; b < H; b += NT) {
+                const uint32_t ca = hall[b];
+                if (!ca) continue;
+                const double ae = apow(S, b), a2 = ae * ae;
+                wsum += (double)ca * a2;
+                const uint32_t ce = hemp[b];
+                if (ce) wempty += (double)ce * a2;
+                const int co = hov[b];
+                if (co) ovl += (double)co * ae;
+                hall[b] = 0; hemp[b] = 0; hov[b] = 0;
+            }
+        }
         block_sum3(wsum, wempty, ovl, S);
+        if (uni) { wsum *= w2u; wempty *= w2u; ovl *= w2u; }
         double wgs = wg, ogs = og, dummy = 0.0;
         block_sum3(wgs, ogs, dummy, S);
         const double Wtot = wsum + wgs, Wemp = wempty + wgs;
@@ -930,7 +1012,52 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
             double O = Wemp;
             const uint32_t cb0 = S.slice_off[s1], ncodes = 2u * (S.slice_off[s1 + 1] - cb0);
             __shared__ uint32_t pref[kMaxJ];
-            for (int level = 0; level < kMaxJ; ++level) {
+            // level 0 on the compact list: first element x with O + F(x) > tgt,
+            // F(x) = weight of components whose first element is <= x
+            int start = 0;
+            bool decided = false;
+            {
+                const uint32_t *sk0 = scr.selk + slot * NW * (size_t)scr.selseg;
+                const double *sw0 = scr.selw + slot * NW * (size_t)scr.selseg;
+                auto Fsum = [&](uint32_t cmax, uint32_t ceq, bool eq_only_single, int *multi) {
+                    double f = 0.0;
+                    int mm = 0;
+                    for (uint32_t q = 0; q < NW; ++q) {
+                        const uint32_t *sk = sk0 + q * (size_t)scr.selseg;
+                        const double *sw = sw0 + q * (size_t)scr.selseg;
+                        for (uint32_t e = threadIdx.x; e < S.segn[q]; e += NT) {
+                            const uint32_t kv = sk[e], code = kv & 0xFFFFu;
+                            if (eq_only_single) {
+                                if (code == ceq) { if ((kv >> 16) == 1u) f += sw[e]; else mm = 1; }
+                            } else if (code <= cmax) f += sw[e];
+                        }
+                    }
+                    if (multi) *multi = mm;
+                    return f;
+                };
+                uint32_t lo = 0, hi = ncodes;
+                double Flo = 0.0;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
+                    const double f = block_sum(Fsum(cmid, 0, false, nullptr), S.redA, S);
+                    if (O + f > tgt) hi = mid;
+                    else { lo = mid + 1; Flo = f; }
+                }
+                if (lo < ncodes) {
+                    const uint32_t code = 2u * (cand[cb0 + (lo >> 1)] & 0xFFFFu) + (lo & 1u);
+                    O += Flo;
+                    int mm = 0;
+                    const double wex = block_sum(Fsum(0, code, true, &mm), S.redA, S);
+                    const int multi = __syncthreads_or(mm);
+                    if (threadIdx.x == 0) pref[0] = code;
+                    __syncthreads();
+                    nsel = 1;
+                    if (!multi || O + wex > tgt) decided = true;       // J = [code]
+                    else start = 1;                                     // longer masks: general descent
+                }
+            }
+            for (int level = start; level < kMaxJ && !decided; ++level) {
                 // weight of components whose mask equals the prefix exactly
                 if (level > 0) {
                     double we = 0.0;
@@ -1022,29 +1149,42 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t) {
     }
 }
 
+constexpr size_t kDynSmem = 3 * kHistMax * sizeof(uint32_t);
+
 __global__ void __launch_bounds__(NT) traj_kernel(const __grid_constant__ Params P) {
     __shared__ Smem S;
+    extern __shared__ uint32_t dyn_hist[];          // 3 x kHistMax exponent histograms, kept zero between uses
+    for (int b = threadIdx.x; b < 3 * kHistMax; b += NT) dyn_hist[b] = 0;
+    __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) S.t = (int)atomicAdd(P.work, 1u);
         __syncthreads();
         const uint32_t t = (uint32_t)S.t;
         __syncthreads();
         if (t >= P.ntraj) break;
-        run_one(P, S, t);
+        run_one(P, S, t, dyn_hist);
         __syncthreads();
     }
 }
 
+// static + dynamic shared memory exceeds 48 KB: opt in (per device)
+static cudaError_t opt_in_smem() {
+    return cudaFuncSetAttribute(traj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+}
+
 cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s) {
     (void)block; (void)smem;
-    traj_kernel<<<grid, NT, 0, s>>>(p);
+    const cudaError_t e = opt_in_smem();
+    if (e != cudaSuccess) return e;
+    traj_kernel<<<grid, NT, kDynSmem, s>>>(p);
     return cudaGetLastError();
 }
 
 int kernel_threads() { return NT; }
 int kernel_blocks_per_sm() {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, traj_kernel, NT, 0) != cudaSuccess) return 0;
+    if (opt_in_smem() != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, traj_kernel, NT, kDynSmem) != cudaSuccess) return 0;
     return b;
 }
 size_t kernel_smem(int) { return sizeof(Smem); }
@@ -1067,6 +1207,26 @@ __global__ void __launch_bounds__(256) fidelity_kernel(const qram_result_t *res,
         out2[0] = m;
         out2[1] = ntraj ? sqrt(var / ntraj) : 0.0;
     }
+}
+
+// |c|^2 * 2^-k if every input column has the same squared magnitude (bitwise),
+// else 0: lets the trajectory kernel sum weights as integer exponent histograms.
+__global__ void uniform_weight_kernel(const double *re, const double *im, int D, int qubit_k, double *out) {
+    __shared__ int diff;
+    if (threadIdx.x == 0) diff = 0;
+    __syncthreads();
+    const double w0 = re[0] * re[0] + im[0] * im[0];
+    for (int b = threadIdx.x; b < D; b += blockDim.x) {
+        const double w = re[b] * re[b] + im[b] * im[b];
+        if (w != w0) diff = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *out = (diff || !(w0 > 0.0)) ? 0.0 : w0 * ldexp(1.0, -qubit_k);
+}
+
+cudaError_t launch_uniform_weight(const double *re, const double *im, int D, int qubit_k, double *out, cudaStream_t s) {
+    uniform_weight_kernel<<<1, 256, 0, s>>>(re, im, D, qubit_k, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s) {

@@ -124,12 +124,15 @@ extern "C" int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k,
     char *b = (char *)base;
     P.work = (uint32_t *)b;
     P.input_error = (const uint32_t *)(b + 4);
+    P.w2u = (const double *)(b + 8);
     carve_scratch(encoding, n, k, num_branches, slots, gamma_max, b + kHeader, &P.scr);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // the array keeps the previous call's contents: reset the counter and the flag
     if (cudaMemsetAsync(b, 0, kHeader, st) != cudaSuccess) return QRAM_E_CUDA;
     validate_kernel<<<1, 1024, 0, st>>>(memory, addr, bus, amp_re, amp_im, n, k, num_branches, (uint32_t *)(b + 4));
     if (cudaGetLastError() != cudaSuccess) return QRAM_E_CUDA;
+    if (launch_uniform_weight(amp_re, amp_im, num_branches, encoding == QRAM_QUBIT ? k : 0, (double *)(b + 8), st) != cudaSuccess)
+        return QRAM_E_CUDA;
     const int grid = (int)std::min<uint32_t>((uint32_t)slots, ntraj);
     if (launch_trajectories(P, grid, kernel_threads(), 0, st) != cudaSuccess) return QRAM_E_CUDA;
     return QRAM_OK;
