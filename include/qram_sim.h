@@ -150,6 +150,22 @@ int qram_set_gamma_bound(qram_sim_t *sim, double gmax);
  * the same GPU.  Takes effect at the next run. */
 int qram_set_launch_ctas(qram_sim_t *sim, uint32_t nctas);
 
+/* CUDA-graph capture of one persistent batched launch (pruned, mode 0, or
+ * full, mode 1) of ntraj trajectories: the graph holds the work-counter reset
+ * and the trajectory kernel.  The first trajectory index is read from
+ * traj0_dev (device, one uint64) when the graph runs, so one graph serves
+ * successive batches; gamma (device, ntraj) and out (device, ntraj results)
+ * are bound at capture.  Needs a damping-rate bound (qram_set_gamma_bound)
+ * so that nothing is read back to the host; the scratch is sized before the
+ * capture.  Capture happens on a private stream; qram_graph_launch runs the
+ * graph on the simulator's stream.  The graph is valid until the
+ * simulator's scratch changes (qram_set_launch_ctas, a larger gamma bound). */
+typedef struct qram_graph qram_graph_t;
+int qram_graph_create(qram_sim_t *sim, int mode, uint32_t ntraj, const double *gamma, qram_result_t *out,
+                      const uint64_t *traj0_dev, qram_graph_t **graph);
+int qram_graph_launch(qram_graph_t *graph);
+void qram_graph_destroy(qram_graph_t *graph);
+
 /* Ensemble mean and standard error of results[0 .. ntraj).fidelity
  * (device array), reduced on the device in a fixed order; blocks until the
  * two host doubles are written. */
@@ -213,6 +229,10 @@ int qram_server_create(size_t mem_budget, int device, uint32_t max_active, qram_
  * request (same checks as qram_sim_create, gamma outside [0,1)), QRAM_E_OOM
  * if it could never fit the budget, QRAM_E_BUSY if 65536 requests wait. */
 int qram_server_submit(qram_server_t *srv, const qram_request_t *req, uint64_t *id);
+
+/* Device bytes the server would reserve for this request (its admission
+ * size); QRAM_E_ARG for a malformed request. */
+int qram_server_estimate(qram_server_t *srv, const qram_request_t *req, size_t *bytes);
 
 /* Copy up to `max` completions (oldest first) into out; *count receives the
  * number copied.  Non-blocking. */

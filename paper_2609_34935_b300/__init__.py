@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["QramSim", "RESULT_DTYPE", "QramError", "load_library", "QUTRIT", "QUBIT"]
+__all__ = ["QramSim", "QramServer", "RESULT_DTYPE", "QramError", "load_library", "QUTRIT", "QUBIT"]
 
 QUTRIT, QUBIT = 0, 1
 OK = 0
@@ -40,6 +40,18 @@ class _Problem(C.Structure):
                 ("num_branches", C.c_int32), ("addr", C.c_void_p), ("bus", C.c_void_p),
                 ("amp_re", C.c_void_p), ("amp_im", C.c_void_p), ("seed", C.c_uint64),
                 ("sampler_version", C.c_uint32)]
+
+
+class _Request(C.Structure):
+    _fields_ = [("problem", _Problem), ("traj0", C.c_uint64), ("ntraj", C.c_uint32),
+                ("gamma", C.c_void_p), ("mode", C.c_int32)]
+
+
+class _Completion(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("ntraj", C.c_uint32),
+                ("mean_fidelity", C.c_double), ("stderr_fidelity", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double),
+                ("device_bytes", C.c_uint64)]
 
 
 _lib = None
@@ -75,6 +87,19 @@ def load_library(build_if_missing: bool = True):
     L.qram_sync.argtypes = [vp]
     L.qram_launch_count.argtypes = [vp]
     L.qram_launch_count.restype = u64
+    L.qram_server_create.argtypes = [C.c_size_t, C.c_int, u32, C.POINTER(vp)]
+    L.qram_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
+    L.qram_server_estimate.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    L.qram_server_poll.argtypes = [vp, vp, u32, C.POINTER(u32)]
+    L.qram_server_results.argtypes = [vp, u64, vp, u32]
+    L.qram_server_cancel.argtypes = [vp, u64]
+    L.qram_server_drain.argtypes = [vp, f64]
+    L.qram_server_destroy.argtypes = [vp]
+    L.qram_server_destroy.restype = None
+    L.qram_graph_create.argtypes = [vp, C.c_int, u32, vp, vp, vp, C.POINTER(vp)]
+    L.qram_graph_launch.argtypes = [vp]
+    L.qram_graph_destroy.argtypes = [vp]
+    L.qram_graph_destroy.restype = None
     L.qram_strerror.argtypes = [C.c_int]
     L.qram_strerror.restype = C.c_char_p
     _lib = L
@@ -219,9 +244,107 @@ class QramSim:
     def set_launch_ctas(self, nctas: int):
         _check(self.lib.qram_set_launch_ctas(self.h, nctas), "qram_set_launch_ctas")
 
+    def graph(self, mode: str, gammas, out, traj0_dev):
+        """Capture one batched launch into a CUDA graph (see qram_graph_create);
+        returns a callable that replays it on the simulator's stream."""
+        h = C.c_void_p()
+        _check(self.lib.qram_graph_create(self.h, 0 if mode == "pruned" else 1, gammas.numel(), _dptr(gammas),
+                                          _dptr(out), _dptr(traj0_dev), C.byref(h)), "qram_graph_create")
+        lib = self.lib
+
+        class _Graph:
+            def __init__(self, handle, keep):
+                self.h, self.keep = handle, keep
+
+            def __call__(self):
+                _check(lib.qram_graph_launch(self.h), "qram_graph_launch")
+
+            def close(self):
+                if self.h:
+                    lib.qram_graph_destroy(self.h)
+                    self.h = None
+
+            def __del__(self):
+                try:
+                    self.close()
+                except Exception:
+                    pass
+        return _Graph(h, (gammas, out, traj0_dev))
+
     def sync(self):
         _check(self.lib.qram_sync(self.h), "qram_sync")
 
     @property
     def launch_count(self) -> int:
         return int(self.lib.qram_launch_count(self.h))
+
+
+class QramServer:
+    """Continuous-batching serving loop (native scheduler thread in the library)."""
+
+    def __init__(self, mem_budget: int, device: int = 0, max_active: int = 4):
+        self.lib = load_library()
+        h = C.c_void_p()
+        _check(self.lib.qram_server_create(mem_budget, device, max_active, C.byref(h)), "qram_server_create")
+        self.h = h
+
+    @staticmethod
+    def _request(problem, seed, traj0, gammas, mode):
+        keep = []
+        mem = np.ascontiguousarray(problem.memory, dtype=np.uint8)
+        addr = np.ascontiguousarray(problem.addr, dtype=np.uint32)
+        bus = np.ascontiguousarray(problem.bus, dtype=np.uint32)
+        amp = np.asarray(problem.amp, dtype=np.complex128)
+        re = np.ascontiguousarray(amp.real)
+        im = np.ascontiguousarray(amp.imag)
+        g = np.ascontiguousarray(gammas, dtype=np.float64)
+        keep += [mem, addr, bus, re, im, g]
+        p = _Problem(int(problem.encoding), int(problem.n), int(problem.k), mem.ctypes.data, len(addr),
+                     addr.ctypes.data, bus.ctypes.data, re.ctypes.data, im.ctypes.data,
+                     int(seed) & (2 ** 64 - 1), 1)
+        return _Request(p, int(traj0), len(g), g.ctypes.data, int(mode)), keep
+
+    def submit(self, problem, seed: int, traj0: int, gammas, mode: int = 0) -> int:
+        req, keep = self._request(problem, seed, traj0, gammas, mode)
+        rid = C.c_uint64()
+        _check(self.lib.qram_server_submit(self.h, C.byref(req), C.byref(rid)), "qram_server_submit")
+        del keep
+        return int(rid.value)
+
+    def estimate(self, problem, ntraj: int, gamma: float = 1e-2) -> int:
+        req, keep = self._request(problem, 0, 0, np.full(ntraj, gamma), 0)
+        b = C.c_size_t()
+        _check(self.lib.qram_server_estimate(self.h, C.byref(req), C.byref(b)), "qram_server_estimate")
+        return int(b.value)
+
+    def poll(self, max_items: int = 4096):
+        buf = (_Completion * max_items)()
+        cnt = C.c_uint32()
+        _check(self.lib.qram_server_poll(self.h, buf, max_items, C.byref(cnt)), "qram_server_poll")
+        return [{f: getattr(buf[i], f) for f, _ in _Completion._fields_} for i in range(cnt.value)]
+
+    def results(self, rid: int, ntraj: int):
+        out = np.zeros(ntraj, dtype=RESULT_DTYPE)
+        _check(self.lib.qram_server_results(self.h, rid, out.ctypes.data, ntraj), "qram_server_results")
+        return out
+
+    def cancel(self, rid: int):
+        _check(self.lib.qram_server_cancel(self.h, rid), "qram_server_cancel")
+
+    def drain(self, timeout_s: float) -> bool:
+        rc = self.lib.qram_server_drain(self.h, timeout_s)
+        if rc == 4:
+            return False
+        _check(rc, "qram_server_drain")
+        return True
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qram_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -36,6 +36,7 @@ struct qram_sim {
     const uint32_t *hist_cand = nullptr, *hist_off = nullptr;
     uint32_t nhist = 0;
     SliceOps ops[kMaxT]{};
+    uint32_t occ2[kMaxT]{};
     uint64_t launches = 0;
     int sms = 0, blocks_per_sm = 0;
     double gamma_bound = 0.0;
@@ -141,7 +142,7 @@ void cand_caps(int n, int k, double gmax, uint32_t *cand_cap, uint32_t *seg_cap)
 }
 
 struct Layout {
-    size_t o_cand, o_seg, o_expl, o_pw, o_pwR, o_ex, o_lab, o_st, o_exc, o_selk, o_selw, total;
+    size_t o_cand, o_seg, o_expl, o_cs, o_exc, o_selk, o_selw, total;
     uint32_t cc, sc, ecap, selseg;
 };
 
@@ -154,11 +155,7 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax) {
     L.o_cand = off; off = align_up(off + slots * L.cc * 4);
     L.o_seg = off; off = align_up(off + slots * NWARP * (size_t)L.sc * 4);
     L.o_expl = off; off = align_up(off + slots * (size_t)D * 4);
-    L.o_pw = off; off = align_up(off + slots * (size_t)L.ecap * 4);
-    L.o_pwR = off; off = align_up(off + slots * (size_t)L.ecap * 4);
-    L.o_ex = off; off = align_up(off + slots * (size_t)L.ecap * 4);
-    L.o_lab = off; off = align_up(off + slots * (size_t)L.ecap * 4);
-    L.o_st = off; off = align_up(off + slots * (size_t)L.ecap * 4);
+    L.o_cs = off; off = align_up(off + slots * (size_t)L.ecap * 16);
     L.o_exc = off; off = align_up(off + slots * (size_t)L.ecap * kXcap * 2);
     // per-warp segments: warp w sees at most ceil(ecap / threads) * 32 components
     L.selseg = (uint32_t)(((size_t)L.ecap + kernel_threads() - 1) / kernel_threads() * 32);
@@ -181,11 +178,7 @@ int ensure_scratch(qram_sim *S, double gmax) {
     S->scr.cand = (uint32_t *)(b + L.o_cand);
     S->scr.wseg = (uint32_t *)(b + L.o_seg);
     S->scr.expl = (uint32_t *)(b + L.o_expl);
-    S->scr.pw = (uint32_t *)(b + L.o_pw);
-    S->scr.pwR = (uint32_t *)(b + L.o_pwR);
-    S->scr.ex = (int32_t *)(b + L.o_ex);
-    S->scr.lab = (uint32_t *)(b + L.o_lab);
-    S->scr.st = (uint32_t *)(b + L.o_st);
+    S->scr.cs = (uint4 *)(b + L.o_cs);
     S->scr.exc = (uint16_t *)(b + L.o_exc);
     S->scr.selk = (uint32_t *)(b + L.o_selk);
     S->scr.selw = (double *)(b + L.o_selw);
@@ -221,6 +214,7 @@ Params base_params(qram_sim *S) {
     P.work = S->d_work;
     P.w2u = S->d_w2u;
     std::memcpy(P.ops, S->ops, sizeof(P.ops));
+    std::memcpy(P.occ2, S->occ2, sizeof(P.occ2));
     return P;
 }
 
@@ -264,6 +258,28 @@ namespace qram {
 
 int build_ops(int n, int k, SliceOps *ops) { return build_ops_impl(n, k, ops); }
 
+// Noiseless orbit with every item excited (all address bits 1, all data bits
+// 1): its path word after each slice marks every position an item can hold.
+void build_occupancy(int n, int k, const SliceOps *ops, uint32_t *occ2) {
+    const int T = 6 * n + 2 * k;
+    uint32_t pw = 0, bus = (1u << k) - 1u;
+    for (int s = 0; s < kMaxT; ++s) occ2[s] = 0;
+    for (int s = 1; s < T; ++s) {
+        const SliceOps &o = ops[s];
+        if (o.load >= 0) pw ^= 2u;
+        if (o.bus >= 0) {
+            const uint32_t d0 = (pw >> 1) & 1u, b = (bus >> o.bus) & 1u;
+            pw = (pw & ~2u) | (b << 1);
+            bus = (bus & ~(1u << o.bus)) | (d0 << o.bus);
+        }
+        uint32_t t = (pw ^ (pw >> 1)) & o.iswap2;
+        pw ^= t | (t << 1);
+        t = (pw ^ (pw >> 2)) & (o.cswap2 << 1);
+        pw ^= t | (t << 2);
+        occ2[s] = pw;
+    }
+}
+
 size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void *base, Scratch *scr) {
     const Layout L = scratch_layout(enc, n, k, D, (size_t)slots, gmax);
     if (base) {
@@ -271,11 +287,7 @@ size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void 
         scr->cand = (uint32_t *)(b + L.o_cand);
         scr->wseg = (uint32_t *)(b + L.o_seg);
         scr->expl = (uint32_t *)(b + L.o_expl);
-        scr->pw = (uint32_t *)(b + L.o_pw);
-        scr->pwR = (uint32_t *)(b + L.o_pwR);
-        scr->ex = (int32_t *)(b + L.o_ex);
-        scr->lab = (uint32_t *)(b + L.o_lab);
-        scr->st = (uint32_t *)(b + L.o_st);
+        scr->cs = (uint4 *)(b + L.o_cs);
         scr->exc = (uint16_t *)(b + L.o_exc);
         scr->selk = (uint32_t *)(b + L.o_selk);
         scr->selw = (double *)(b + L.o_selw);
@@ -345,6 +357,7 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     S->enc = p->encoding; S->n = p->n; S->k = p->k; S->D = p->num_branches; S->T = 6 * p->n + 2 * p->k;
     S->seed = p->seed;
     if (build_ops_impl(S->n, S->k, S->ops) != QRAM_OK) { delete S; return QRAM_E_ARG; }
+    build_occupancy(S->n, S->k, S->ops, S->occ2);
     DeviceGuard g(device);
     int rc = QRAM_OK;
     const size_t D = (size_t)S->D;
@@ -420,6 +433,61 @@ int qram_set_fault_history(qram_sim_t *S, uint32_t nhist, const uint32_t *cand, 
     S->hist_cand = nhist ? cand : nullptr;
     S->hist_off = nhist ? off : nullptr;
     return QRAM_OK;
+}
+
+struct qram_graph {
+    qram_sim *sim = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int qram_graph_create(qram_sim_t *S, int mode, uint32_t ntraj, const double *gamma, qram_result_t *out,
+                      const uint64_t *traj0_dev, qram_graph_t **gout) {
+    if (!S || !gamma || !out || !traj0_dev || !gout || ntraj == 0 || (mode != 0 && mode != 1)) return QRAM_E_ARG;
+    if (!(S->gamma_bound > 0.0)) return QRAM_E_STATE;              // no host read-back inside a capture
+    *gout = nullptr;
+    DeviceGuard g(S->device);
+    int rc = ensure_scratch(S, S->gamma_bound);
+    if (rc) return rc;
+    if (S->stream && !ok(cudaStreamSynchronize(S->stream))) return QRAM_E_CUDA;
+    cudaStream_t cap = nullptr;
+    if (!ok(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return QRAM_E_CUDA;
+    qram_graph *G = new (std::nothrow) qram_graph();
+    if (!G) { cudaStreamDestroy(cap); return QRAM_E_OOM; }
+    G->sim = S;
+    Params P = base_params(S);
+    P.ntraj = ntraj; P.gamma = gamma; P.mode = mode == 0 ? kPruned : kFull; P.out = out; P.traj0_dev = traj0_dev;
+    const int grid = (int)std::min<uint32_t>((uint32_t)S->slots, ntraj);
+    rc = QRAM_OK;
+    if (!ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) rc = QRAM_E_CUDA;
+    else {
+        if (!ok(cudaMemsetAsync(S->d_work, 0, sizeof(uint32_t), cap)) ||
+            !ok(launch_trajectories(P, grid, kernel_threads(), 0, cap)))
+            rc = QRAM_E_CUDA;
+        cudaGraph_t graph = nullptr;
+        if (!ok(cudaStreamEndCapture(cap, &graph))) rc = QRAM_E_CUDA;
+        G->graph = graph;
+        if (!rc && !ok(cudaGraphInstantiate(&G->exec, G->graph, 0))) rc = QRAM_E_CUDA;
+    }
+    cudaStreamDestroy(cap);
+    if (rc) { cudaGetLastError(); qram_graph_destroy(G); return rc; }
+    *gout = G;
+    return QRAM_OK;
+}
+
+int qram_graph_launch(qram_graph_t *G) {
+    if (!G || !G->exec) return QRAM_E_ARG;
+    DeviceGuard g(G->sim->device);
+    if (!ok(cudaGraphLaunch(G->exec, G->sim->stream))) return QRAM_E_CUDA;
+    G->sim->launches++;
+    return QRAM_OK;
+}
+
+void qram_graph_destroy(qram_graph_t *G) {
+    if (!G) return;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    delete G;
 }
 
 int qram_set_launch_ctas(qram_sim_t *S, uint32_t nctas) {

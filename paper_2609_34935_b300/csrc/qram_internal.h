@@ -36,11 +36,12 @@ struct Scratch {
     uint32_t *cand;      // [slots][cand_cap]  packed (slice << 16) | site
     uint32_t *wseg;      // [slots][nwarps][seg_cap] per-warp candidate segments
     uint32_t *expl;      // [slots][D] explicit input columns
-    uint32_t *pw;        // [slots][ecap] on-path excitation bits (2 per layer)
-    uint32_t *pwR;       // [slots][ecap] on-path level-R bits (qutrit)
-    int32_t *ex;         // [slots][ecap] damping exponent (number of K0 factors a)
-    uint32_t *lab;       // [slots][ecap] (column << 8) | first-wall bus word c
-    uint32_t *st;        // [slots][ecap] bus word (bits 0-7) | sign (bit 8) | nexc (bits 16-23)
+    // [slots][ecap] packed components, one 16-byte load/store each:
+    //   x = path word (bit 2L router, 2L+1 data slot of the path node at layer L)
+    //   y = level-R bits of the path word (qutrit)
+    //   z = K0 exponent (bits 0-15) | bus word (16-23) | sign (24) | off-path count (25-30)
+    //   w = input column (bits 0-13) | address (bits 14-27)
+    uint4 *cs;
     uint16_t *exc;       // [slots][ecap][kXcap] off-path sites (site << 1 | isR)
     uint32_t *selk;      // [slots][nwarps][selseg] components with a non-empty mask: first code | size << 16
     double *selw;        // [slots][nwarps][selseg] their weights
@@ -80,7 +81,9 @@ struct Params {
     int dump_mode;
     const uint32_t *input_error;   // if non-null and nonzero at run time: every trajectory is QRAM_E_ARG
     const double *w2u;             // device scalar: |c|^2 (times 2^-k for qubits) when every column shares it, else 0
+    const uint64_t *traj0_dev;     // if non-null, the first trajectory index is read here (graph replays)
     SliceOps ops[kMaxT];
+    uint32_t occ2[kMaxT];  // per slice: path-word positions any noiseless orbit can hold excited
 };
 
 cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s);
@@ -92,6 +95,9 @@ cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n
 // host-side helpers shared by the API and the serving loop
 size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax);
 int build_ops(int n, int k, SliceOps *ops);
+// occ2[s] = (layer, slot) positions, as path-word bits, that an item can
+// occupy after the gates of slice s in a noiseless orbit
+void build_occupancy(int n, int k, const SliceOps *ops, uint32_t *occ2);
 // lays out the per-slot scratch of `slots` CTAs at `base` (may be null: size only); returns bytes
 size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void *base, Scratch *scr);
 int resident_slots_per_device(int device);

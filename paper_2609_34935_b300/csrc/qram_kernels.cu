@@ -107,6 +107,8 @@ struct Smem {
     uint32_t scanw[NW];
     uint32_t wcount[NW];
     uint32_t segn[NW];             // entries of each warp's compact selection segment
+    uint32_t syncmask[8];          // slices with a candidate a noiseless orbit can excite / with any candidate
+    uint32_t cl2;                  // path-word positions (2L + slot) holding a candidate in the current slice
     uint32_t J[kMaxJ];
     int nJ;
     uint32_t nexpl, ncomp, ncand;
@@ -444,10 +446,11 @@ __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *
 }
 
 // first element (code) of the mask J(x) = C_s n X(x) and its size; the
-// code is 0xFFFF... when the mask is empty
+// code is 0xFFFF... when the mask is empty.  cl2 = path-word positions that
+// hold any candidate this slice: on-path sites elsewhere cannot be in J.
 __device__ __forceinline__ uint32_t mask_first(const CompR &c, const uint16_t *xs, const Ctx &C,
-                                               const uint32_t *candbits, uint32_t &cnt) {
-    uint32_t w = c.pw, xi = 0, first = 0xFFFFFFFFu;
+                                               const uint32_t *candbits, uint32_t cl2, uint32_t &cnt) {
+    uint32_t w = c.nexc ? c.pw : (c.pw & cl2), xi = 0, first = 0xFFFFFFFFu;
     cnt = 0;
     for (;;) {
         const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
@@ -513,28 +516,34 @@ __device__ __forceinline__ double apow(const Smem &S, int e) {
     return S.powlo[e & 63] * S.powhi[(e >> 6) & 63];
 }
 
-__device__ __forceinline__ void load_comp(const Scratch &scr, size_t base, uint32_t r, CompR &c, uint16_t *xs,
-                                          uint32_t &lab) {
-    const size_t g = base + r;
-    c.pw = scr.pw[g];
-    c.pwR = scr.pwR[g];
-    c.e = scr.ex[g];
-    lab = scr.lab[g];
-    const uint32_t st = scr.st[g];
-    c.cb = st & 0xFFu;
-    c.sign = (st >> 8) & 1u;
-    c.nexc = (st >> 16) & 0xFFu;
-    for (uint32_t q = 0; q < c.nexc; ++q) xs[q] = scr.exc[g * kXcap + q];
+// packed component (see Scratch::cs)
+__device__ __forceinline__ void unpack(const uint4 v, CompR &c, uint32_t &col, uint32_t &addr) {
+    c.pw = v.x;
+    c.pwR = v.y;
+    c.e = (int32_t)(v.z & 0xFFFFu);
+    c.cb = (v.z >> 16) & 0xFFu;
+    c.sign = (v.z >> 24) & 1u;
+    c.nexc = (v.z >> 25) & 0x3Fu;
+    col = v.w & 0x3FFFu;
+    addr = (v.w >> 14) & 0x3FFFu;
 }
 
-__device__ __forceinline__ void store_comp(const Scratch &scr, size_t base, uint32_t r, const CompR &c,
-                                           const uint16_t *xs, uint32_t lab) {
-    const size_t g = base + r;
-    scr.pw[g] = c.pw;
-    scr.pwR[g] = c.pwR;
-    scr.ex[g] = c.e;
-    scr.lab[g] = lab;
-    scr.st[g] = (c.cb & 0xFFu) | (c.sign << 8) | (c.nexc << 16);
+__device__ __forceinline__ uint4 pack(const CompR &c, uint32_t col, uint32_t addr) {
+    uint4 v;
+    v.x = c.pw;
+    v.y = c.pwR;
+    v.z = ((uint32_t)c.e & 0xFFFFu) | ((c.cb & 0xFFu) << 16) | ((c.sign & 1u) << 24) | ((c.nexc & 0x3Fu) << 25);
+    v.w = col | (addr << 14);
+    return v;
+}
+
+__device__ __forceinline__ void load_exc(const Scratch &scr, size_t g, uint32_t nexc, uint16_t *xs) {
+    for (uint32_t q = 0; q < nexc; ++q) xs[q] = scr.exc[g * kXcap + q];
+}
+
+__device__ __forceinline__ void store_comp(const Scratch &scr, size_t g, const CompR &c, const uint16_t *xs,
+                                           uint32_t col, uint32_t addr) {
+    scr.cs[g] = pack(c, col, addr);
     for (uint32_t q = 0; q < c.nexc; ++q) scr.exc[g * kXcap + q] = xs[q];
 }
 
@@ -583,7 +592,7 @@ __device__ double data_norm2(const Params &P, const Smem &S, int s) {
 // ---------------------------------------------------------------------------
 // one trajectory
 __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
-    const uint64_t traj = P.traj0 + t;
+    const uint64_t traj = (P.traj0_dev ? *P.traj0_dev : P.traj0) + t;
     const double gamma = P.gamma[t];
     const int n = P.n, T = P.T;
     const uint32_t nodes = (uint32_t)P.nodes;
@@ -680,6 +689,15 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
     if (threadIdx.x == 0) S.ncand = ncand;
 
     // per-slice offsets (candidates are sorted by (slice, site))
+    if (threadIdx.x < 8) S.syncmask[threadIdx.x] = 0;   // [0..3] relevant, [4..7] any candidate
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < ncand; c += NT) {
+        const uint32_t s = cand[c] >> 16, q = cand[c] & 0xFFFFu;
+        const int L = layer_of(q >> 1);
+        atomicOr(&S.syncmask[4 + (s >> 5)], 1u << (s & 31u));
+        if ((P.occ2[s] >> (2 * L + (int)(q & 1u))) & 1u)   // a noiseless orbit can hold it excited
+            atomicOr(&S.syncmask[s >> 5], 1u << (s & 31u));
+    }
     for (int s = threadIdx.x; s <= T; s += NT) {
         uint32_t lo = 0, hi = ncand;
         const uint32_t key = (uint32_t)s << 16;
@@ -784,7 +802,7 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
             const uint32_t j = __ldg(P.bus + col);
             if (qubit) { c.cb = cw; c.sign = __popc(j & cw) & 1u; }   // first wall: (-1)^(j.c)
             else { c.cb = j; c.sign = 0; }
-            store_comp(scr, cbase, r, c, nullptr, (col << 8) | cw);
+            store_comp(scr, cbase + r, c, nullptr, col, __ldg(P.addr + col));
         }
     }
     if (threadIdx.x == 0) S.ncomp = S.status == QRAM_OK ? ncomp0 : 0;
@@ -803,14 +821,22 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
     uint32_t jumps = 0, first_jump = 0, jump_sites = 0;
     const double k2 = qubit ? ldexp(1.0, -P.k) : 1.0;   // |first-wall factor|^2
     for (;;) {
-        // next slice with candidates
+        // next slice whose candidates can matter: before the first fired jump
+        // every component is on a noiseless orbit, so a candidate on a position
+        // no orbit can excite leaves J empty and needs no draw
         int s1 = s_prev + 1;
-        while (s1 < T && S.slice_off[s1 + 1] == S.slice_off[s1]) ++s1;
+        {
+            const uint32_t *m = jumped ? S.syncmask + 4 : S.syncmask;
+            while (s1 < T && !((m[s1 >> 5] >> (s1 & 31)) & 1u)) ++s1;
+        }
         const bool final_epoch = s1 >= T;
+        if (threadIdx.x == 0) S.cl2 = 0;
+        __syncthreads();
         if (!final_epoch) {
             for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {
                 const uint32_t site = cand[c] & 0xFFFFu;
                 atomicOr(&S.candbits[site >> 5], 1u << (site & 31u));
+                atomicOr(&S.cl2, 1u << (2 * layer_of(site >> 1) + (int)(site & 1u)));
             }
         }
         __syncthreads();
@@ -825,18 +851,25 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
         uint32_t *selk = scr.selk + (slot * NW + warp) * (size_t)scr.selseg;
         double *selw = scr.selw + (slot * NW + warp) * (size_t)scr.selseg;
         uint32_t wcur = 0;
+        // one chunk of look-ahead: the next chunk's packed state is in flight
+        // while this chunk evolves
+        uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
+        if (threadIdx.x < ncomp) nxt = scr.cs[cbase + threadIdx.x];
         for (uint32_t r0 = 0; r0 < ncomp; r0 += NT) {
             const uint32_t r = r0 + threadIdx.x;
             bool alive = r < ncomp;
+            const uint4 cur = nxt;
+            if (r + NT < ncomp) nxt = scr.cs[cbase + r + NT];
             CompR c;
             uint16_t xs[kXcap];
-            uint32_t lab = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
+            uint32_t lab = 0, addr = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
             double w = 0.0;
             uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | empty/ground << 2 | overlap sign + 1
             Ctx C;
             if (alive) {
-                load_comp(scr, cbase, r, c, xs, lab);
-                C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
+                unpack(cur, c, lab, addr);
+                if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
+                C = make_ctx(P.enc, n, P.mem, addr);
                 if (s_prev > 0) {                           // pending K_J of slice s_prev
                     if (nJ > 0) {
                         alive = holds_all(c, xs, C, S.J, nJ);
@@ -854,9 +887,9 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
                 const double ae = apow(S, c.e);
                 if (uni && c.e >= H) capfail = true;                 // exponent bound violated
                 if (!final_epoch) {
-                    c1 = mask_first(c, xs, C, S.candbits, mcnt);
+                    c1 = mask_first(c, xs, C, S.candbits, S.cl2, mcnt);
                     if (!uni) {
-                        w = col_w2(P, lab >> 8) * k2 * ae * ae;
+                        w = col_w2(P, lab) * k2 * ae * ae;
                         wsum += w;
                         if (mcnt == 0) wempty += w;
                     } else {
@@ -867,7 +900,7 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
                     int ovs = 0;
                     const bool ground = c.pw == 0 && c.nexc == 0;     // ground tree configuration
                     if (ground) {
-                        const uint32_t col = lab >> 8;
+                        const uint32_t col = lab;
                         if (qubit) {
                             const uint32_t bout = __ldg(P.bus + col) ^ __ldg(P.mem + C.i);
                             ovs = ((c.sign + __popc(c.cb & bout)) & 1u) ? -1 : 1;
@@ -876,17 +909,17 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
                         }
                     }
                     if (!uni) {
-                        w = col_w2(P, lab >> 8) * k2 * ae * ae;
+                        w = col_w2(P, lab) * k2 * ae * ae;
                         wsum += w;
                         if (ground) wempty += w;
-                        if (ovs) ovl += ovs * (col_w2(P, lab >> 8) * k2 * ae);
+                        if (ovs) ovl += ovs * (col_w2(P, lab) * k2 * ae);
                     } else if (c.e < H) {
                         hkey = ((uint32_t)c.e << 3) | ((ground ? 1u : 0u) << 2) | (uint32_t)(ovs + 1);
                     }
                     if (P.dump_mode && threadIdx.x < NT) {
                         const uint32_t di = atomicAdd(P.dump.count, 1u);
                         if (di < P.dump.cap) {
-                            const uint32_t col = lab >> 8;
+                            const uint32_t col = lab;
                             const double sc = (qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0) * ae * (c.sign ? -1.0 : 1.0);
                             P.dump.col[di] = col;
                             P.dump.bus[di] = c.cb;
@@ -921,10 +954,10 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
             if (compact) {
                 uint32_t tot;
                 const uint32_t pre = block_scan_flag(alive, &tot, S);
-                if (alive && !final_epoch) store_comp(scr, cbase, wr + pre, c, xs, lab);
+                if (alive && !final_epoch) store_comp(scr, cbase + wr + pre, c, xs, lab, addr);
                 wr += tot;
             } else if (alive && !final_epoch) {
-                store_comp(scr, cbase, r, c, xs, lab);
+                store_comp(scr, cbase + r, c, xs, lab, addr);
             }
         }
         if (lane == 0) S.segn[warp] = wcur;
@@ -1062,12 +1095,13 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
                 if (level > 0) {
                     double we = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; uint16_t xs[kXcap]; uint32_t lab;
-                        load_comp(scr, cbase, r, c, xs, lab);
-                        const Ctx C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
+                        CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
+                        unpack(scr.cs[cbase + r], c, lab, addr);
+                        if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
+                        const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         if (mask_query(c, xs, C, S.candbits, pref, level) == -1) {
                             const double ae = apow(S, c.e);
-                            we += col_w2(P, lab >> 8) * k2 * ae * ae;
+                            we += (uni ? w2u : col_w2(P, lab) * k2) * ae * ae;
                         }
                     }
                     we = block_sum(we, S.redA, S);
@@ -1082,13 +1116,14 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
                     const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
                     double f = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; uint16_t xs[kXcap]; uint32_t lab;
-                        load_comp(scr, cbase, r, c, xs, lab);
-                        const Ctx C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
+                        CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
+                        unpack(scr.cs[cbase + r], c, lab, addr);
+                        if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
+                        const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         const long long q = mask_query(c, xs, C, S.candbits, pref, level);
                         if (q >= 0 && (uint32_t)q <= cmid) {
                             const double ae = apow(S, c.e);
-                            f += col_w2(P, lab >> 8) * k2 * ae * ae;
+                            f += (uni ? w2u : col_w2(P, lab) * k2) * ae * ae;
                         }
                     }
                     f = block_sum(f, S.redA, S);
@@ -1100,9 +1135,10 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
                     // group with weight (the oracle's rule); descend on the largest code
                     uint32_t best = 0xFFFFFFFFu;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; uint16_t xs[kXcap]; uint32_t lab;
-                        load_comp(scr, cbase, r, c, xs, lab);
-                        const Ctx C = make_ctx(P.enc, n, P.mem, __ldg(P.addr + (lab >> 8)));
+                        CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
+                        unpack(scr.cs[cbase + r], c, lab, addr);
+                        if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
+                        const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         const long long q = mask_query(c, xs, C, S.candbits, pref, level);
                         if (q >= 0 && (best == 0xFFFFFFFFu || (uint32_t)q > best)) best = (uint32_t)q;
                     }
@@ -1151,7 +1187,7 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
 
 constexpr size_t kDynSmem = 3 * kHistMax * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(NT) traj_kernel(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(NT, 4) traj_kernel(const __grid_constant__ Params P) {
     __shared__ Smem S;
     extern __shared__ uint32_t dyn_hist[];          // 3 x kHistMax exponent histograms, kept zero between uses
     for (int b = threadIdx.x; b < 3 * kHistMax; b += NT) dyn_hist[b] = 0;

@@ -265,6 +265,16 @@ int qram_server_submit(qram_server_t *S, const qram_request_t *q, uint64_t *id) 
     return QRAM_OK;
 }
 
+int qram_server_estimate(qram_server_t *S, const qram_request_t *q, size_t *bytes) {
+    if (!S || !q || !bytes || !valid_request(q)) return QRAM_E_ARG;
+    double gmax = 0.0;
+    for (uint32_t t = 0; t < q->ntraj; ++t) gmax = q->gamma[t] > gmax ? q->gamma[t] : gmax;
+    const qram_problem_t &p = q->problem;
+    *bytes = estimate_sim_bytes(p.encoding, p.n, p.k, p.num_branches, slots_for(S), gmax) +
+             (size_t)q->ntraj * (8 + sizeof(qram_result_t)) + 4096;
+    return QRAM_OK;
+}
+
 int qram_server_poll(qram_server_t *S, qram_completion_t *out, uint32_t max, uint32_t *count) {
     if (!S || !count || (max && !out)) return QRAM_E_ARG;
     std::lock_guard<std::mutex> lk(S->mu);

@@ -236,3 +236,25 @@ def test_fidelity_reduction():
     f = sim.results(raw)["fidelity"]
     assert abs(m - f.mean()) < 1e-13 and abs(s - f.std(ddof=1) / math.sqrt(len(f))) < 1e-12
     sim.close()
+
+
+def test_cuda_graph_replay_matches_direct_launch():
+    """One persistent batched launch captured in a CUDA graph and replayed for
+    two batches (first trajectory index read from device memory) gives the
+    same results as direct launches."""
+    p = W.data_loading(W.QUBIT, 6, 2, seed=31)
+    sim = _sim(p, 31)
+    sim.set_gamma_bound(1e-2)
+    g = torch.full((700,), 4e-3, dtype=torch.float64, device="cuda:0")
+    out = torch.empty((700, 48), dtype=torch.uint8, device="cuda:0")
+    t0 = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    graph = sim.graph("pruned", g, out, t0)
+    for first in (0, 500):
+        t0.fill_(first)
+        graph()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().copy()
+        ref = sim.run_pruned(first, g).cpu().numpy()
+        assert np.array_equal(got, ref)
+    graph.close()
+    sim.close()
