@@ -166,10 +166,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--full-per-batch", type=int, default=5, help="full-mode trajectories per gamma batch")
+    ap.add_argument("--full-per-batch", type=int, default=20, help="full-mode trajectories per gamma batch")
+    ap.add_argument("--serving", action="store_true", help="run the serving-stream benchmark instead")
+    ap.add_argument("--requests", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
     rank, world, local = _env_rank()
@@ -186,13 +190,18 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sim = QramSim(p, seed=SEED, device=local, stream=stream)
     sim.set_gamma_bound(G_HI)
+    with torch.cuda.stream(stream):
+        variant = sim.autotune("pruned", 3e-3, 2000)                     # threads per CTA for this problem
     gam = torch.tensor(gam_h, dtype=torch.float64, device=dev)
     out = torch.empty((NTRAJ, 48), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # > 126 MB L2
     base = rank * 1_000_000_000                                           # disjoint trajectory ranges
+    traj0 = torch.zeros(1, dtype=torch.int64, device=dev)
+    graph = sim.graph("pruned", gam, out, traj0)                          # one persistent launch per step
 
     def step(j):
-        sim.run_pruned(base + j * NTRAJ, gam, out)
+        traj0.fill_(base + j * NTRAJ)
+        graph()
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -281,16 +290,20 @@ def main():
     nodes = (1 << N) - 1
     T = 6 * N + 2 * K
     philox_calls = NTRAJ * (T - 1) * nodes
-    ops_per_call = 84            # 10 rounds x (2 wide multiplies + 4 xor + 2 key adds) + 2 64-bit compares
+    comp_slices = float(np.sum(res["explicit_comps"].astype(np.float64))) * (T - 1)   # upper bound (deaths)
+    ops = philox_calls * 84 + comp_slices * 12
     sm_mhz = cl.get("sm_mhz") or 2032.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_int = nsm * 64 * sm_mhz * 1e6 / 1e12          # Tops/s: 64 INT32 lanes/SM/clock
-    achieved = philox_calls * ops_per_call / (t_dev / (world * args.steps)) / 1e12 / world
-    traffic = None
+    launch_s = t_dev / args.steps
+    achieved = ops / launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "Tops/s (INT32)",
-            "frac": achieved / peak_int, "traffic": traffic,
-            "note": "algorithmic INT32 ops of the Philox candidate draw per launch / launch time; "
-                    "peak = SMs x 64 INT32 lanes x median SM clock under load"}
+            "frac": achieved / peak_int, "traffic": None,
+            "note": "algorithmic INT32 ops per launch (84 per Philox4x32-10 candidate draw of a (slice, node); "
+                    "12 per explicit component-slice of path-word gates, counted as explicit components x (T-1)) "
+                    "/ launch time from CUDA events; peak derived: SMs x 64 INT32 lanes/clock x median SM clock "
+                    "under load (not a measured peak)",
+            "philox_calls": philox_calls, "component_slices_upper": comp_slices, "variant_threads": variant}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -323,9 +336,72 @@ def main():
             "clocks": cl,
         }
         print(json.dumps(line), flush=True)
+    graph.close()
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_serving(args):
+    """Serving stream: Poisson arrivals of requests, each drawing encoding
+    (qutrit/qubit 50/50), n uniform in 4..14, data qubits 1..min(n, 4), gamma
+    log-uniform in [1e-5, 1e-2], trajectories log-uniform in [lo, hi],
+    seeded data; admitted by device-memory budget.  The arrival rate is set
+    to a fraction (0.7 and 0.95) of the capacity measured on the same request
+    mix submitted at once.  Reports p50/p99 latency and trajectories/s."""
+    import torch
+    from paper_2609_34935_b300 import QramServer
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(5001)
+    lo, hi = 1e2, 1e4
+    reqs = []
+    for i in range(args.requests):
+        enc = int(rng.integers(0, 2))
+        n = int(rng.integers(4, 15))
+        k = int(rng.integers(1, min(n, 4) + 1))
+        g = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-2))))
+        nt = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        reqs.append((W.data_loading(enc, n, k, seed=5001 * 1_000_000 + i), 5001 * 1_000_000 + i, 0,
+                     np.full(nt, g), 0))
+    free = torch.cuda.mem_get_info(local)[0]
+    budget = int(free * 0.6)
+
+    def run(rate):
+        srv = QramServer(budget, device=local, max_active=8)
+        t0 = time.perf_counter()
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs))) if rate else np.zeros(len(reqs))
+        ids = []
+        for (p, seed, traj0, g, mode), ta in zip(reqs, arrivals):
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.0005)
+            ids.append(srv.submit(p, seed, traj0, g, mode))
+        assert srv.drain(3600.0)
+        wall = time.perf_counter() - t0
+        comps = srv.poll(len(ids) + 16)
+        srv.close()
+        lat = np.array([c["t_finish"] - c["t_submit"] for c in comps])
+        ok = all(c["status"] == 0 for c in comps)
+        ntot = sum(c["ntraj"] for c in comps)
+        return wall, lat, ok, ntot
+
+    wall0, _, ok0, ntot = run(0.0)                     # capacity: everything submitted at once
+    cap_rps = len(reqs) / wall0
+    lines = []
+    for frac in (0.7, 0.95):
+        wall, lat, ok, ntot = run(frac * cap_rps)
+        lines.append({"load": frac, "rate_req_per_s": frac * cap_rps, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                      "p99_ms": 1e3 * float(np.percentile(lat, 99)), "trajectories_per_s": ntot / wall,
+                      "status_ok": bool(ok)})
+    print(json.dumps({"metric": "serving stream: p50/p99 query latency and trajectories/s", "unit": "ms",
+                      "requests": len(reqs), "capacity_req_per_s": cap_rps, "capacity_traj_per_s": ntot / wall0,
+                      "runs": lines, "data": "synthetic",
+                      "config": {"workload": f"Poisson arrivals of {len(reqs)} requests; encoding 50/50, n in 4..14, "
+                                             f"k in 1..min(n,4), gamma log-uniform [1e-5,1e-2], trajectories "
+                                             f"log-uniform [{lo:g},{hi:g}], data-loading input, pruned mode",
+                                 "budget_bytes": budget, "max_active": 8}}), flush=True)
 
 
 if __name__ == "__main__":

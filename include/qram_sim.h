@@ -166,6 +166,20 @@ int qram_graph_create(qram_sim_t *sim, int mode, uint32_t ntraj, const double *g
 int qram_graph_launch(qram_graph_t *graph);
 void qram_graph_destroy(qram_graph_t *graph);
 
+/* Launch variant: threads per CTA of the trajectory kernel (128, 256 or
+ * 512; default 256).  Results do not depend on it except through the order
+ * of floating-point block reductions (rounding).  qram_get_variant returns
+ * the current one. */
+int qram_set_variant(qram_sim_t *sim, int threads);
+int qram_get_variant(const qram_sim_t *sim);
+
+/* Autotuner: times one launch of each variant on ntraj trajectories (from
+ * traj0) at damping rate gamma in the given mode (0 pruned, 1 full) and
+ * keeps the fastest; *best_threads and *best_ms (may be NULL) receive the
+ * choice and its time.  Blocks until done; allocates its probe buffers. */
+int qram_autotune(qram_sim_t *sim, int mode, double gamma, uint32_t ntraj, uint64_t traj0, int *best_threads,
+                  float *best_ms);
+
 /* Ensemble mean and standard error of results[0 .. ntraj).fidelity
  * (device array), reduced on the device in a fixed order; blocks until the
  * two host doubles are written. */

@@ -100,6 +100,9 @@ def load_library(build_if_missing: bool = True):
     L.qram_graph_launch.argtypes = [vp]
     L.qram_graph_destroy.argtypes = [vp]
     L.qram_graph_destroy.restype = None
+    L.qram_set_variant.argtypes = [vp, C.c_int]
+    L.qram_get_variant.argtypes = [vp]
+    L.qram_autotune.argtypes = [vp, C.c_int, f64, u32, u64, C.POINTER(C.c_int), C.POINTER(C.c_float)]
     L.qram_strerror.argtypes = [C.c_int]
     L.qram_strerror.restype = C.c_char_p
     _lib = L
@@ -270,6 +273,41 @@ class QramSim:
                 except Exception:
                     pass
         return _Graph(h, (gammas, out, traj0_dev))
+
+    def set_variant(self, threads: int):
+        _check(self.lib.qram_set_variant(self.h, threads), "qram_set_variant")
+
+    @property
+    def variant(self) -> int:
+        return int(self.lib.qram_get_variant(self.h))
+
+    def autotune(self, mode: str = "pruned", gamma: float = 3e-3, ntraj: int = 2000, cache: str | None = None):
+        """Pick the fastest launch variant for this problem (threads per CTA).
+        With `cache` (a JSON path) the choice is looked up / stored under the
+        key (encoding, n, k, decade of gamma)."""
+        import json
+        import math
+        key = f"{self.encoding}:{self.n}:{self.k}:{mode}:1e{int(math.floor(math.log10(max(gamma, 1e-12))))}"
+        table = {}
+        if cache and os.path.exists(cache):
+            try:
+                table = json.load(open(cache))
+            except Exception:
+                table = {}
+        if key in table:
+            self.set_variant(int(table[key]["threads"]))
+            return int(table[key]["threads"])
+        best = C.c_int()
+        ms = C.c_float()
+        _check(self.lib.qram_autotune(self.h, 0 if mode == "pruned" else 1, gamma, ntraj, 1 << 40, C.byref(best),
+                                      C.byref(ms)), "qram_autotune")
+        if cache:
+            table[key] = {"threads": int(best.value), "ms": float(ms.value), "ntraj": ntraj}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return int(best.value)
 
     def sync(self):
         _check(self.lib.qram_sync(self.h), "qram_sync")

@@ -39,6 +39,9 @@ struct qram_sim {
     uint32_t occ2[kMaxT]{};
     uint64_t launches = 0;
     int sms = 0, blocks_per_sm = 0;
+    int threads = 256;          // launch variant (threads per CTA)
+    size_t dyn = 0;             // dynamic shared memory per CTA
+    int scr_threads = 0;        // variant the scratch was laid out for
     double gamma_bound = 0.0;
 };
 
@@ -126,8 +129,8 @@ int build_ops_impl(int n, int k, SliceOps *ops) {
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 // per-slot candidate capacities for a damping-rate bound gmax: mean + 12 sigma
-void cand_caps(int n, int k, double gmax, uint32_t *cand_cap, uint32_t *seg_cap) {
-    const int NWARP = kernel_threads() / 32;
+void cand_caps(int n, int k, double gmax, int threads, uint32_t *cand_cap, uint32_t *seg_cap) {
+    const int NWARP = threads / 32;
     const double items = (double)(6 * n + 2 * k - 1) * (double)((1u << n) - 1);
     const double per = std::ceil(items / NWARP);
     auto cap = [&](double m) {
@@ -146,11 +149,11 @@ struct Layout {
     uint32_t cc, sc, ecap, selseg;
 };
 
-Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax) {
+Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax, int threads) {
     Layout L;
-    cand_caps(n, k, gmax, &L.cc, &L.sc);
+    cand_caps(n, k, gmax, threads, &L.cc, &L.sc);
     L.ecap = (uint32_t)D << (enc == QRAM_QUBIT ? k : 0);
-    const int NWARP = kernel_threads() / 32;
+    const int NWARP = threads / 32;
     size_t off = 0;
     L.o_cand = off; off = align_up(off + slots * L.cc * 4);
     L.o_seg = off; off = align_up(off + slots * NWARP * (size_t)L.sc * 4);
@@ -158,7 +161,7 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax) {
     L.o_cs = off; off = align_up(off + slots * (size_t)L.ecap * 16);
     L.o_exc = off; off = align_up(off + slots * (size_t)L.ecap * kXcap * 2);
     // per-warp segments: warp w sees at most ceil(ecap / threads) * 32 components
-    L.selseg = (uint32_t)(((size_t)L.ecap + kernel_threads() - 1) / kernel_threads() * 32);
+    L.selseg = (uint32_t)(((size_t)L.ecap + threads - 1) / threads * 32);
     L.o_selk = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 4);
     L.o_selw = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 8);
     L.total = off;
@@ -166,8 +169,10 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax) {
 }
 
 int ensure_scratch(qram_sim *S, double gmax) {
-    const Layout L = scratch_layout(S->enc, S->n, S->k, S->D, (size_t)S->slots, gmax);
-    if (S->scratch && S->scr.cand_cap >= L.cc && S->scr.seg_cap >= L.sc && S->scr.ecap >= L.ecap) return QRAM_OK;
+    const Layout L = scratch_layout(S->enc, S->n, S->k, S->D, (size_t)S->slots, gmax, S->threads);
+    if (S->scratch && S->scr_threads == S->threads && S->scr.cand_cap >= L.cc && S->scr.seg_cap >= L.sc &&
+        S->scr.ecap >= L.ecap)
+        return QRAM_OK;
     // stream-ordered: no device-wide synchronisation, so other work keeps running
     if (S->scratch) { cudaFreeAsync(S->scratch, S->stream); S->scratch = nullptr; }
     void *p = nullptr;
@@ -186,6 +191,7 @@ int ensure_scratch(qram_sim *S, double gmax) {
     S->scr.cand_cap = L.cc;
     S->scr.seg_cap = L.sc;
     S->scr.ecap = L.ecap;
+    S->scr_threads = S->threads;
     return QRAM_OK;
 }
 
@@ -206,7 +212,7 @@ Params base_params(qram_sim *S) {
     Params P;
     std::memset(&P, 0, sizeof(P));
     P.enc = S->enc; P.n = S->n; P.k = S->k; P.T = S->T; P.D = S->D;
-    P.nodes = (1 << S->n) - 1; P.M = 2 * P.nodes; P.nthreads = kernel_threads();
+    P.nodes = (1 << S->n) - 1; P.M = 2 * P.nodes; P.nthreads = S->threads; P.hist_pad = hist_pad(S->n, S->k);
     P.mem = S->d_mem; P.addr = S->d_addr; P.bus = S->d_bus; P.amp_re = S->d_re; P.amp_im = S->d_im;
     P.seed = S->seed;
     P.hist_cand = S->hist_cand; P.hist_off = S->hist_off; P.nhist = S->nhist;
@@ -234,7 +240,7 @@ int bound_gamma(qram_sim *S, const double *gamma, uint32_t ntraj, double *gmax) 
 int launch(qram_sim *S, Params &P, uint32_t ntraj) {
     if (!ok(cudaMemsetAsync(S->d_work, 0, sizeof(uint32_t), S->stream))) return QRAM_E_CUDA;
     const int grid = (int)std::min<uint32_t>((uint32_t)S->slots, std::max<uint32_t>(ntraj, 1u));
-    if (!ok(launch_trajectories(P, grid, kernel_threads(), 0, S->stream))) return QRAM_E_CUDA;
+    if (!ok(launch_trajectories(P, grid, S->threads, S->dyn, S->stream))) return QRAM_E_CUDA;
     S->launches++;
     return QRAM_OK;
 }
@@ -280,8 +286,8 @@ void build_occupancy(int n, int k, const SliceOps *ops, uint32_t *occ2) {
     }
 }
 
-size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void *base, Scratch *scr) {
-    const Layout L = scratch_layout(enc, n, k, D, (size_t)slots, gmax);
+size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, int threads, void *base, Scratch *scr) {
+    const Layout L = scratch_layout(enc, n, k, D, (size_t)slots, gmax, threads);
     if (base) {
         char *b = (char *)base;
         scr->cand = (uint32_t *)(b + L.o_cand);
@@ -299,15 +305,15 @@ size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void 
     return L.total;
 }
 
-size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax) {
+size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax, int threads) {
     const size_t prob = (size_t(1) << n) + (size_t)D * 24 + 4096;
-    return prob + scratch_layout(enc, n, k, D, (size_t)slots, gmax).total;
+    return prob + scratch_layout(enc, n, k, D, (size_t)slots, gmax, threads).total;
 }
 
-int resident_slots_per_device(int device) {
+int resident_slots_per_device(int device, int threads, size_t dyn) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    return sms * kernel_blocks_per_sm();
+    return sms * kernel_blocks_per_sm(threads, dyn);
 }
 
 }  // namespace qram
@@ -362,7 +368,8 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     int rc = QRAM_OK;
     const size_t D = (size_t)S->D;
     if (!ok(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, device))) { delete S; return QRAM_E_CUDA; }
-    S->blocks_per_sm = kernel_blocks_per_sm();
+    S->dyn = dyn_smem_bytes(S->n, S->k);
+    S->blocks_per_sm = kernel_blocks_per_sm(S->threads, S->dyn);
     if (S->blocks_per_sm < 1) { delete S; return QRAM_E_CUDA; }
     S->slots = S->sms * S->blocks_per_sm;
     cudaStream_t st = S->stream;
@@ -462,7 +469,7 @@ int qram_graph_create(qram_sim_t *S, int mode, uint32_t ntraj, const double *gam
     if (!ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) rc = QRAM_E_CUDA;
     else {
         if (!ok(cudaMemsetAsync(S->d_work, 0, sizeof(uint32_t), cap)) ||
-            !ok(launch_trajectories(P, grid, kernel_threads(), 0, cap)))
+            !ok(launch_trajectories(P, grid, S->threads, S->dyn, cap)))
             rc = QRAM_E_CUDA;
         cudaGraph_t graph = nullptr;
         if (!ok(cudaStreamEndCapture(cap, &graph))) rc = QRAM_E_CUDA;
@@ -499,6 +506,64 @@ int qram_set_launch_ctas(qram_sim_t *S, uint32_t nctas) {
         if (S->scratch) { cudaFreeAsync(S->scratch, S->stream); S->scratch = nullptr; }
         S->slots = want;
     }
+    return QRAM_OK;
+}
+
+int qram_set_variant(qram_sim_t *S, int threads) {
+    if (!S || !valid_threads(threads)) return QRAM_E_ARG;
+    if (threads == S->threads) return QRAM_OK;
+    DeviceGuard g(S->device);
+    const int b = kernel_blocks_per_sm(threads, S->dyn);
+    if (b < 1) return QRAM_E_ARG;
+    const bool capped = S->slots < S->sms * S->blocks_per_sm;
+    S->threads = threads;
+    S->blocks_per_sm = b;
+    S->slots = capped ? std::min(S->slots, S->sms * b) : S->sms * b;
+    if (S->scratch) { cudaFreeAsync(S->scratch, S->stream); S->scratch = nullptr; }
+    return QRAM_OK;
+}
+
+int qram_get_variant(const qram_sim_t *S) { return S ? S->threads : 0; }
+
+int qram_autotune(qram_sim_t *S, int mode, double gamma, uint32_t ntraj, uint64_t traj0, int *best_threads,
+                  float *best_ms) {
+    if (!S || !best_threads || ntraj == 0 || (mode != 0 && mode != 1) || !(gamma >= 0.0 && gamma < 1.0)) return QRAM_E_ARG;
+    DeviceGuard g(S->device);
+    double *dg = nullptr;
+    qram_result_t *dr = nullptr;
+    cudaStream_t st = S->stream;
+    if (!ok(cudaMallocAsync((void **)&dg, ntraj * 8ull, st)) || !ok(cudaMallocAsync((void **)&dr, ntraj * sizeof(qram_result_t), st))) {
+        cudaGetLastError();
+        if (dg) cudaFreeAsync(dg, st);
+        return QRAM_E_OOM;
+    }
+    std::vector<double> hg(ntraj, gamma);
+    int rc = ok(cudaMemcpyAsync(dg, hg.data(), ntraj * 8ull, cudaMemcpyHostToDevice, st)) ? QRAM_OK : QRAM_E_CUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1)))) rc = QRAM_E_CUDA;
+    const int variants[3] = {128, 256, 512};
+    const int keep = S->threads;
+    int best = keep;
+    float bms = 3.4e38f;
+    for (int v = 0; v < 3 && !rc; ++v) {
+        if (qram_set_variant(S, variants[v]) != QRAM_OK) continue;
+        // one untimed launch (scratch, caches), then one timed launch
+        if ((rc = run_mode(S, mode, traj0, ntraj, dg, dr))) break;
+        if (!ok(cudaEventRecord(e0, st))) { rc = QRAM_E_CUDA; break; }
+        if ((rc = run_mode(S, mode, traj0, ntraj, dg, dr))) break;
+        if (!ok(cudaEventRecord(e1, st)) || !ok(cudaEventSynchronize(e1))) { rc = QRAM_E_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < bms) { bms = ms; best = variants[v]; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(dg, st);
+    cudaFreeAsync(dr, st);
+    if (rc) { qram_set_variant(S, keep); return rc; }
+    qram_set_variant(S, best);
+    *best_threads = best;
+    if (best_ms) *best_ms = bms;
     return QRAM_OK;
 }
 

@@ -82,6 +82,7 @@ struct Params {
     const uint32_t *input_error;   // if non-null and nonzero at run time: every trajectory is QRAM_E_ARG
     const double *w2u;             // device scalar: |c|^2 (times 2^-k for qubits) when every column shares it, else 0
     const uint64_t *traj0_dev;     // if non-null, the first trajectory index is read here (graph replays)
+    int hist_pad;                  // bins per exponent histogram (dynamic shared memory: 3 of them)
     SliceOps ops[kMaxT];
     uint32_t occ2[kMaxT];  // per slice: path-word positions any noiseless orbit can hold excited
 };
@@ -93,17 +94,19 @@ cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n
                                  uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
                                  double *o_im, cudaStream_t s);
 // host-side helpers shared by the API and the serving loop
-size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax);
+size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax, int threads);
 int build_ops(int n, int k, SliceOps *ops);
 // occ2[s] = (layer, slot) positions, as path-word bits, that an item can
 // occupy after the gates of slice s in a noiseless orbit
 void build_occupancy(int n, int k, const SliceOps *ops, uint32_t *occ2);
 // lays out the per-slot scratch of `slots` CTAs at `base` (may be null: size only); returns bytes
-size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, void *base, Scratch *scr);
-int resident_slots_per_device(int device);
+size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, int threads, void *base, Scratch *scr);
+int resident_slots_per_device(int device, int threads, size_t dyn);
 
-int kernel_threads();
-int kernel_blocks_per_sm();
-size_t kernel_smem(int n);
+int kernel_threads();                                   // default variant
+bool valid_threads(int threads);                        // 128, 256 or 512
+int kernel_blocks_per_sm(int threads, size_t dyn);      // resident CTAs per SM of a variant
+int hist_pad(int n, int k);
+size_t dyn_smem_bytes(int n, int k);
 
 }  // namespace qram

@@ -31,8 +31,6 @@
 
 namespace qram {
 
-constexpr int NT = 256;            // threads per CTA
-constexpr int NW = NT / 32;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 from its published definition (Salmon et al., SC'11).
@@ -98,7 +96,9 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
+template <int NT>
 struct Smem {
+    static constexpr int NW = NT / 32;
     uint32_t badbits[512];         // 2^14 addresses
     uint32_t candbits[1024];       // M <= 32766 sites, candidates of the current slice
     uint32_t slice_off[kMaxT + 2];
@@ -119,7 +119,9 @@ struct Smem {
     double sA, sB, sC;
 };
 
-__device__ double block_sum(double x, double *red, Smem &S) {
+template <int NT>
+__device__ double block_sum(double x, double *red, Smem<NT> &S) {
+    constexpr int NW = NT / 32;
     x = warp_sum(x);
     const int w = threadIdx.x >> 5;
     __syncthreads();
@@ -131,7 +133,9 @@ __device__ double block_sum(double x, double *red, Smem &S) {
 }
 
 // three sums at once
-__device__ void block_sum3(double &a, double &b, double &c, Smem &S) {
+template <int NT>
+__device__ void block_sum3(double &a, double &b, double &c, Smem<NT> &S) {
+    constexpr int NW = NT / 32;
     a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
     const int w = threadIdx.x >> 5;
     __syncthreads();
@@ -143,7 +147,9 @@ __device__ void block_sum3(double &a, double &b, double &c, Smem &S) {
 }
 
 // exclusive scan of a 0/1 flag over the block; returns prefix, total in *tot
-__device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem &S) {
+template <int NT>
+__device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem<NT> &S) {
+    constexpr int NW = NT / 32;
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, f);
     const uint32_t pre = __popc(b & ((1u << lane) - 1u));
@@ -512,7 +518,8 @@ __device__ __noinline__ uint64_t config_hash(const CompR c, const uint16_t *xs, 
 }
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double apow(const Smem &S, int e) {
+template <int NT>
+__device__ __forceinline__ double apow(const Smem<NT> &S, int e) {
     return S.powlo[e & 63] * S.powhi[(e >> 6) & 63];
 }
 
@@ -578,7 +585,8 @@ __device__ int good_exposure(const Params &P, uint32_t col, int s) {
 
 // qubit data-register norm^2 of a good branch after damping layers 1..s:
 // prod_t (1 + a^(2 m_t)) / 2 (Lemma 1)
-__device__ double data_norm2(const Params &P, const Smem &S, int s) {
+template <int NT>
+__device__ double data_norm2(const Params &P, const Smem<NT> &S, int s) {
     if (P.enc != QRAM_QUBIT) return 1.0;
     double r = 1.0;
     for (int t = 0; t < P.k; ++t) {
@@ -591,7 +599,9 @@ __device__ double data_norm2(const Params &P, const Smem &S, int s) {
 
 // ---------------------------------------------------------------------------
 // one trajectory
-__device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
+template <int NT>
+__device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist) {
+    constexpr int NW = NT / 32;
     const uint64_t traj = (P.traj0_dev ? *P.traj0_dev : P.traj0) + t;
     const double gamma = P.gamma[t];
     const int n = P.n, T = P.T;
@@ -814,8 +824,8 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
     const double w2u = P.w2u ? *P.w2u : 0.0;
     const bool uni = w2u > 0.0;
     const int H = (2 * n + P.k) * (T - 1) + 1;
-    uint32_t *hall = hist, *hemp = hist + kHistMax;
-    int32_t *hov = (int32_t *)(hist + 2 * kHistMax);
+    uint32_t *hall = hist, *hemp = hist + P.hist_pad;
+    int32_t *hov = (int32_t *)(hist + 2 * P.hist_pad);
     int s_prev = 0;              // slice whose damping is pending (0: none)
     bool jumped = false;
     uint32_t jumps = 0, first_jump = 0, jump_sites = 0;
@@ -1185,12 +1195,11 @@ __device__ void run_one(const Params &P, Smem &S, uint32_t t, uint32_t *hist) {
     }
 }
 
-constexpr size_t kDynSmem = 3 * kHistMax * sizeof(uint32_t);
-
-__global__ void __launch_bounds__(NT, 4) traj_kernel(const __grid_constant__ Params P) {
-    __shared__ Smem S;
-    extern __shared__ uint32_t dyn_hist[];          // 3 x kHistMax exponent histograms, kept zero between uses
-    for (int b = threadIdx.x; b < 3 * kHistMax; b += NT) dyn_hist[b] = 0;
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) traj_kernel(const __grid_constant__ Params P) {
+    __shared__ Smem<NT> S;
+    extern __shared__ uint32_t dyn_hist[];          // 3 exponent histograms of hist_pad bins, kept zero between uses
+    for (int b = threadIdx.x; b < 3 * P.hist_pad; b += NT) dyn_hist[b] = 0;
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) S.t = (int)atomicAdd(P.work, 1u);
@@ -1198,32 +1207,52 @@ __global__ void __launch_bounds__(NT, 4) traj_kernel(const __grid_constant__ Par
         const uint32_t t = (uint32_t)S.t;
         __syncthreads();
         if (t >= P.ntraj) break;
-        run_one(P, S, t, dyn_hist);
+        run_one<NT>(P, S, t, dyn_hist);
         __syncthreads();
     }
 }
 
-// static + dynamic shared memory exceeds 48 KB: opt in (per device)
-static cudaError_t opt_in_smem() {
-    return cudaFuncSetAttribute(traj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
-}
-
-cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s) {
-    (void)block; (void)smem;
-    const cudaError_t e = opt_in_smem();
+// launch variants (threads per CTA, minimum resident CTAs for the register cap)
+template <int NT, int MINB>
+static cudaError_t launch_variant(const Params &p, int grid, size_t dyn, cudaStream_t s, bool occupancy_only, int *blocks) {
+    // static + dynamic shared memory can exceed 48 KB: opt in
+    cudaError_t e = cudaFuncSetAttribute(traj_kernel<NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(3 * kHistMax * sizeof(uint32_t)));
     if (e != cudaSuccess) return e;
-    traj_kernel<<<grid, NT, kDynSmem, s>>>(p);
+    if (occupancy_only) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traj_kernel<NT, MINB>, NT, dyn);
+    traj_kernel<NT, MINB><<<grid, NT, dyn, s>>>(p);
     return cudaGetLastError();
 }
 
-int kernel_threads() { return NT; }
-int kernel_blocks_per_sm() {
+static cudaError_t dispatch(int threads, const Params &p, int grid, size_t dyn, cudaStream_t s, bool occ, int *blocks) {
+    switch (threads) {
+    case 128: return launch_variant<128, 8>(p, grid, dyn, s, occ, blocks);
+    case 256: return launch_variant<256, 4>(p, grid, dyn, s, occ, blocks);
+    case 512: return launch_variant<512, 2>(p, grid, dyn, s, occ, blocks);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_trajectories(const Params &p, int grid, int threads, size_t dyn, cudaStream_t s) {
+    return dispatch(threads, p, grid, dyn, s, false, nullptr);
+}
+
+int hist_pad(int n, int k) {
+    const int H = (2 * n + k) * (6 * n + 2 * k - 1) + 1;
+    return (H + 31) & ~31;
+}
+
+size_t dyn_smem_bytes(int n, int k) { return 3 * (size_t)hist_pad(n, k) * sizeof(uint32_t); }
+
+bool valid_threads(int threads) { return threads == 128 || threads == 256 || threads == 512; }
+
+int kernel_threads() { return 256; }
+
+int kernel_blocks_per_sm(int threads, size_t dyn) {
     int b = 0;
-    if (opt_in_smem() != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, traj_kernel, NT, kDynSmem) != cudaSuccess) return 0;
+    if (dispatch(threads, Params{}, 0, dyn, nullptr, true, &b) != cudaSuccess) { cudaGetLastError(); return 0; }
     return b;
 }
-size_t kernel_smem(int) { return sizeof(Smem); }
 
 // ---------------------------------------------------------------------------
 // ensemble mean / standard error in a fixed order (one CTA)

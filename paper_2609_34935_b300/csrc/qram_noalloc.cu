@@ -34,24 +34,21 @@ namespace {
 
 std::mutex g_mu;
 void *g_base[kMaxDevices] = {};
-int g_slots[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the
 // static array (the host-side symbol is only a stand-in, not an address).
-int static_setup(int device, void **base, int *resident_slots) {
+int static_setup(int device, size_t dyn, void **base, int *resident_slots) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (device < 0 || device >= kMaxDevices) return QRAM_E_ARG;
     if (!g_base[device]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_qram_static_scratch);
         if (e != cudaSuccess || !p) { cudaGetLastError(); return QRAM_E_CUDA; }
-        const int slots = resident_slots_per_device(device);
-        if (slots < 1) return QRAM_E_CUDA;
         g_base[device] = p;
-        g_slots[device] = slots;
     }
     *base = g_base[device];
-    *resident_slots = g_slots[device];
+    *resident_slots = resident_slots_per_device(device, kernel_threads(), dyn);
+    if (*resident_slots < 1) return QRAM_E_CUDA;
     return QRAM_OK;
 }
 
@@ -104,20 +101,22 @@ extern "C" int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k,
     if (cudaGetDevice(&device) != cudaSuccess) return QRAM_E_CUDA;
     void *base = nullptr;
     int resident = 0;
-    int rc = static_setup(device, &base, &resident);
+    const size_t dyn = dyn_smem_bytes(n, k);
+    int rc = static_setup(device, dyn, &base, &resident);
     if (rc) return rc;
     // as many CTA slots as fit in the static array (at most one per resident CTA)
     const size_t avail = kStaticBytes - kHeader;
-    const size_t one = carve_scratch(encoding, n, k, num_branches, 1, gamma_max, nullptr, nullptr);
+    const int threads = kernel_threads();
+    const size_t one = carve_scratch(encoding, n, k, num_branches, 1, gamma_max, threads, nullptr, nullptr);
     if (one > avail) return QRAM_E_TOOBIG;
     int slots = (int)std::min<size_t>((size_t)resident, avail / one);
-    while (slots > 1 && carve_scratch(encoding, n, k, num_branches, slots, gamma_max, nullptr, nullptr) > avail) --slots;
+    while (slots > 1 && carve_scratch(encoding, n, k, num_branches, slots, gamma_max, threads, nullptr, nullptr) > avail) --slots;
     Params P;
     std::memset(&P, 0, sizeof(P));
     if (build_ops(n, k, P.ops) != QRAM_OK) return QRAM_E_ARG;
     build_occupancy(n, k, P.ops, P.occ2);
     P.enc = encoding; P.n = n; P.k = k; P.T = 6 * n + 2 * k; P.D = num_branches;
-    P.nodes = (1 << n) - 1; P.M = 2 * P.nodes; P.nthreads = kernel_threads();
+    P.nodes = (1 << n) - 1; P.M = 2 * P.nodes; P.nthreads = threads; P.hist_pad = hist_pad(n, k);
     P.mem = memory; P.addr = addr; P.bus = bus; P.amp_re = amp_re; P.amp_im = amp_im;
     P.seed = seed; P.traj0 = traj0; P.ntraj = ntraj; P.gamma = gamma;
     P.mode = mode == 0 ? kPruned : kFull;
@@ -126,7 +125,7 @@ extern "C" int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k,
     P.work = (uint32_t *)b;
     P.input_error = (const uint32_t *)(b + 4);
     P.w2u = (const double *)(b + 8);
-    carve_scratch(encoding, n, k, num_branches, slots, gamma_max, b + kHeader, &P.scr);
+    carve_scratch(encoding, n, k, num_branches, slots, gamma_max, threads, b + kHeader, &P.scr);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // the array keeps the previous call's contents: reset the counter and the flag
     if (cudaMemsetAsync(b, 0, kHeader, st) != cudaSuccess) return QRAM_E_CUDA;
@@ -135,6 +134,6 @@ extern "C" int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k,
     if (launch_uniform_weight(amp_re, amp_im, num_branches, encoding == QRAM_QUBIT ? k : 0, (double *)(b + 8), st) != cudaSuccess)
         return QRAM_E_CUDA;
     const int grid = (int)std::min<uint32_t>((uint32_t)slots, ntraj);
-    if (launch_trajectories(P, grid, kernel_threads(), 0, st) != cudaSuccess) return QRAM_E_CUDA;
+    if (launch_trajectories(P, grid, threads, dyn, st) != cudaSuccess) return QRAM_E_CUDA;
     return QRAM_OK;
 }

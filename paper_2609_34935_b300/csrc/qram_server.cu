@@ -216,7 +216,7 @@ int qram_server_create(size_t mem_budget, int device, uint32_t max_active, qram_
     S->max_active = max_active;
     S->t0 = Clock::now();
     if (cudaSetDevice(device) != cudaSuccess) { delete S; return QRAM_E_CUDA; }
-    S->total_slots = resident_slots_per_device(device);
+    S->total_slots = resident_slots_per_device(device, kernel_threads(), 3 * kHistMax * sizeof(uint32_t));
     if (S->total_slots < 1 || cudaStreamCreateWithFlags(&S->ctrl, cudaStreamNonBlocking) != cudaSuccess) {
         delete S;
         return QRAM_E_CUDA;
@@ -253,7 +253,7 @@ int qram_server_submit(qram_server_t *S, const qram_request_t *q, uint64_t *id) 
     for (double g : r->gamma) gmax = g > gmax ? g : gmax;
     std::lock_guard<std::mutex> lk(S->mu);
     r->slots = slots_for(S);
-    r->bytes = estimate_sim_bytes(r->enc, r->n, r->k, r->D, r->slots, gmax) +
+    r->bytes = estimate_sim_bytes(r->enc, r->n, r->k, r->D, r->slots, gmax, kernel_threads()) +
                (size_t)r->ntraj * (8 + sizeof(qram_result_t)) + 4096;
     if (r->bytes > S->budget) { delete r; return QRAM_E_OOM; }
     if (S->queue.size() >= 65536) { delete r; return QRAM_E_BUSY; }
@@ -270,7 +270,7 @@ int qram_server_estimate(qram_server_t *S, const qram_request_t *q, size_t *byte
     double gmax = 0.0;
     for (uint32_t t = 0; t < q->ntraj; ++t) gmax = q->gamma[t] > gmax ? q->gamma[t] : gmax;
     const qram_problem_t &p = q->problem;
-    *bytes = estimate_sim_bytes(p.encoding, p.n, p.k, p.num_branches, slots_for(S), gmax) +
+    *bytes = estimate_sim_bytes(p.encoding, p.n, p.k, p.num_branches, slots_for(S), gmax, kernel_threads()) +
              (size_t)q->ntraj * (8 + sizeof(qram_result_t)) + 4096;
     return QRAM_OK;
 }

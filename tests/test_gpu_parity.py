@@ -258,3 +258,31 @@ def test_cuda_graph_replay_matches_direct_launch():
         assert np.array_equal(got, ref)
     graph.close()
     sim.close()
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_launch_variants_match_oracle(threads):
+    """Every launch variant of the autotuner (threads per CTA) gives the
+    oracle's results."""
+    p = W.data_loading(W.QUBIT, 5, 3, seed=91)
+    g = np.full(300, 2e-2)
+    ref = core.run(p, 91, 0, g)
+    sim = _sim(p, 91)
+    sim.set_variant(threads)
+    assert sim.variant == threads
+    _cmp_results(sim.results(sim.run_pruned(0, torch.tensor(g, device="cuda:0"))), ref)
+    sim.close()
+
+
+def test_autotune_picks_a_variant_and_caches(tmp_path):
+    import json
+    p = W.data_loading(W.QUTRIT, 8, 1, seed=5)
+    sim = _sim(p, 5)
+    cache = str(tmp_path / "tune.json")
+    best = sim.autotune("pruned", 3e-3, 1500, cache=cache)
+    assert best in (128, 256, 512) and sim.variant == best
+    table = json.load(open(cache))
+    assert list(table.values())[0]["threads"] == best
+    sim.set_variant(256)
+    assert sim.autotune("pruned", 3e-3, 1500, cache=cache) == best      # served from the cache
+    sim.close()
