@@ -167,11 +167,15 @@ __device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem<NT> &S) {
 // (rare: only after a jump moved an item off its address path) in a small
 // per-thread array xs[] that only the slow path and the mask queries touch.
 struct CompR {
-    uint32_t pw, pwR;    // path word: bit 2L router, 2L+1 data slot of the path node at layer L
+    uint32_t pw, pwR;    // path A (the branch's address path): bit 2L router, 2L+1 data slot of its
+                         // node at layer L; pwR: level-R bits (qutrit)
+    uint32_t pwB;        // qubit, after a misaligned router at layer ldiv sent items off path A:
+                         // path B (layers > ldiv), whose nodes follow B's own routers
+    int32_t ldiv;        // divergence layer of path B, -1 = single path
     int32_t e;           // number of K0 factors a collected
     uint32_t cb;         // bus word (register outside the tree)
     uint32_t sign;       // phase (-1)^sign
-    uint32_t nexc;       // off-path excitations in xs[]
+    uint32_t nexc;       // off-path excitations in xs[] (never together with path B)
 };
 
 struct Ctx {
@@ -187,6 +191,28 @@ __device__ __forceinline__ Ctx make_ctx(int enc, int n, const uint8_t *mem, uint
     C.PB = spread2(__brev(i) >> (32 - n));      // routed bit of layer L = bit n-1-L of i
     return C;
 }
+
+// bit 2L of x -> bit L
+__device__ __forceinline__ uint32_t compact2(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
+}
+
+// The address whose path is B: i above the divergence, the other child at
+// layer ldiv, then B's router values (an idle router routes left).
+__device__ __forceinline__ uint32_t b_addr(const CompR &c, const Ctx &C) {
+    if (c.ldiv < 0) return 0;
+    const int sh = C.n - 1 - c.ldiv;
+    const uint32_t low = (1u << sh) - 1u;
+    const uint32_t rev = __brev(compact2(c.pwB)) >> (32 - C.n);
+    return ((C.i ^ (1u << sh)) & ~low) | (rev & low);
+}
+
+__device__ __forceinline__ bool is_ground(const CompR &c) { return c.pw == 0 && c.pwB == 0 && c.nexc == 0; }
 
 // ---- generic slow path: sorted list of (site << 2 | level) ----------------
 struct Ents {
@@ -219,36 +245,47 @@ __device__ bool ent_set(Ents &E, uint32_t site, int lvl) {
     return true;
 }
 
-// the excited sites of a component in increasing site order, as codes
-// 2*site + isR; xi/w carry the iteration state
-__device__ __forceinline__ uint32_t next_site(uint32_t pw, uint32_t pwR, uint32_t nexc, const uint16_t *xs,
-                                              const Ctx &C, uint32_t &w, uint32_t &xi) {
-    uint32_t sp = 0xFFFFFFFFu, cp = 0;
-    if (w) {
-        const int b = __ffs(w) - 1;
-        sp = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
-        cp = (C.enc == QRAM_QUTRIT && ((pwR >> b) & 1u)) ? 1u : 0u;
+// The excited sites of a component in increasing site order, as codes
+// 2*site + isR, merging path A (wA), path B (wB, address iB) and the
+// off-path list (xi); returns 0xFFFFFFFF at the end.
+__device__ __forceinline__ uint32_t next_site(const CompR &c, const uint16_t *xs, const Ctx &C, uint32_t iB,
+                                              uint32_t &wA, uint32_t &wB, uint32_t &xi) {
+    uint32_t best = 0xFFFFFFFFu, code = 0xFFFFFFFFu;
+    int src = -1;
+    if (wA) {
+        const int b = __ffs(wA) - 1;
+        best = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
+        code = (best << 1) | ((C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 1u : 0u);
+        src = 0;
     }
-    uint32_t sx = 0xFFFFFFFFu, cx = 0;
-    if (xi < nexc) { sx = xs[xi] >> 1; cx = xs[xi] & 1u; }
-    if (sp == 0xFFFFFFFFu && sx == 0xFFFFFFFFu) return 0xFFFFFFFFu;
-    if (sp < sx) { w &= w - 1; return (sp << 1) | cp; }
-    ++xi;
-    return (sx << 1) | cx;
+    if (wB) {
+        const int b = __ffs(wB) - 1;
+        const uint32_t s = 2u * path_node(iB, C.n, b >> 1) + (uint32_t)(b & 1);
+        if (s < best) { best = s; code = s << 1; src = 1; }
+    }
+    if (xi < c.nexc) {
+        const uint32_t s = xs[xi] >> 1;
+        if (s < best) { best = s; code = xs[xi]; src = 2; }
+    }
+    if (src == 0) wA &= wA - 1;
+    else if (src == 1) wB &= wB - 1;
+    else if (src == 2) ++xi;
+    return code;
 }
 
 __device__ void to_ents(const CompR &c, const uint16_t *xs, const Ctx &C, Ents &E) {
     E.n = 0;
-    uint32_t w = c.pw, xi = 0;
+    const uint32_t iB = b_addr(c, C);
+    uint32_t wA = c.pw, wB = c.pwB, xi = 0;
     for (;;) {
-        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
+        const uint32_t code = next_site(c, xs, C, iB, wA, wB, xi);
         if (code == 0xFFFFFFFFu) break;
         E.v[E.n++] = ((code >> 1) << 2) | ((code & 1u) ? 2u : 1u);
     }
 }
 
 __device__ bool from_ents(CompR &c, uint16_t *xs, const Ctx &C, const Ents &E) {
-    c.pw = 0; c.pwR = 0; c.nexc = 0;
+    c.pw = 0; c.pwR = 0; c.pwB = 0; c.ldiv = -1; c.nexc = 0;
     for (int j = 0; j < E.n; ++j) {
         const uint32_t site = E.v[j] >> 2, lvl = E.v[j] & 3u;
         const uint32_t u = site >> 1;
@@ -354,17 +391,38 @@ __device__ __noinline__ CompR slow_slice(const SliceOps op, CompR c, uint16_t *x
     return c;
 }
 
-// ---- fast path on the path word ------------------------------------------
-// Handles every slice in which nothing leaves or enters the address path:
-// no off-path excitation, and every active controlled swap whose on-path data
-// slot is occupied is aligned with the path.  Returns false otherwise.
+// ---- fast path on the path words -----------------------------------------
+// Handles every slice in which nothing lands outside the component's paths:
+// no off-path excitation; qutrit: every active controlled swap whose on-path
+// data slot is occupied is aligned with the address path; qubit: the same,
+// except that one misaligned router (layer ldiv) may send items to path B,
+// which is kept as a second path word as long as B's routers do not change
+// under items already on B.  Returns false otherwise (generic slow path).
 __device__ __forceinline__ bool fast_slice(const SliceOps &op, CompR &c, const Ctx &C) {
     if (c.nexc) return false;
     const int n = C.n;
     const uint32_t CM2 = op.cswap2;
     const bool qubit = C.enc == QRAM_QUBIT;
-    const uint32_t mis = qubit ? ((c.pw ^ C.PB) & CM2) : (CM2 & c.pw & (c.pwR ^ C.PB));
-    if (mis & (c.pw >> 1)) return false;               // a data item would leave the path
+    int ldiv = c.ldiv;
+    uint32_t mis;
+    if (qubit) {
+        mis = (c.pw ^ C.PB) & CM2;
+        const uint32_t mv = mis & (c.pw >> 1);           // data items a router would send off path A
+        if (ldiv < 0) {
+            if (mv) {
+                if (mv & (mv - 1)) return false;         // two divergences at once
+                ldiv = (__ffs(mv) - 1) >> 1;
+            }
+        } else {
+            if (mv & ~(3u << (2 * ldiv))) return false;  // would need a third path
+            // a router of B changed by this slice moves B's path below it
+            const uint32_t chg = (c.pwB ^ (c.pwB >> 1)) & op.iswap2;
+            if (chg && (c.pwB >> (2 * ((__ffs(chg) - 1) >> 1) + 2))) return false;
+        }
+    } else {
+        mis = CM2 & c.pw & (c.pwR ^ C.PB);
+        if (mis & (c.pw >> 1)) return false;             // a data item would leave the path
+    }
     if (op.load >= 0) {
         const uint32_t b = routed_bit(C.i, n, op.load);
         if (qubit) c.pw ^= b << 1;
@@ -389,16 +447,39 @@ __device__ __forceinline__ bool fast_slice(const SliceOps &op, CompR &c, const C
     if (op.iswap2) {
         uint32_t t = (c.pw ^ (c.pw >> 1)) & op.iswap2;
         c.pw ^= t | (t << 1);
-        t = (c.pwR ^ (c.pwR >> 1)) & op.iswap2;
-        c.pwR ^= t | (t << 1);
+        if (qubit) {
+            t = (c.pwB ^ (c.pwB >> 1)) & op.iswap2;
+            c.pwB ^= t | (t << 1);
+        } else {
+            t = (c.pwR ^ (c.pwR >> 1)) & op.iswap2;
+            c.pwR ^= t | (t << 1);
+        }
     }
     if (CM2) {
-        // aligned controlled swaps move d(P_L) <-> d(P_{L+1}); a qutrit router at W swaps nothing
-        const uint32_t SM = (qubit ? (CM2 & ~mis) : (CM2 & c.pw & ~mis)) << 1;
-        uint32_t t = (c.pw ^ (c.pw >> 2)) & SM;
-        c.pw ^= t | (t << 2);
-        t = (c.pwR ^ (c.pwR >> 2)) & SM;
-        c.pwR ^= t | (t << 2);
+        if (qubit) {
+            // aligned swaps on A; on B every router is B's own direction; at the
+            // divergence layer a router pointing away from A swaps with B's top
+            const bool cross = ldiv >= 0 && ((mis >> (2 * ldiv)) & 1u);
+            const uint32_t SMA = (CM2 & ~mis) << 1;
+            const uint32_t SMB = ldiv >= 0 ? (CM2 & (0xFFFFFFFFu << (2 * ldiv + 2))) << 1 : 0u;
+            uint32_t t = (c.pw ^ (c.pw >> 2)) & SMA;
+            c.pw ^= t | (t << 2);
+            t = (c.pwB ^ (c.pwB >> 2)) & SMB;
+            c.pwB ^= t | (t << 2);
+            if (cross) {
+                const int bA = 2 * ldiv + 1, bB = 2 * ldiv + 3;
+                const uint32_t x = ((c.pw >> bA) ^ (c.pwB >> bB)) & 1u;
+                c.pw ^= x << bA;
+                c.pwB ^= x << bB;
+            }
+        } else {
+            // a qutrit router at W swaps nothing
+            const uint32_t SM = (CM2 & c.pw & ~mis) << 1;
+            uint32_t t = (c.pw ^ (c.pw >> 2)) & SM;
+            c.pw ^= t | (t << 2);
+            t = (c.pwR ^ (c.pwR >> 2)) & SM;
+            c.pwR ^= t | (t << 2);
+        }
     }
     if (op.fetch >= 0) {
         const int L = n - 1;
@@ -406,6 +487,12 @@ __device__ __forceinline__ bool fast_slice(const SliceOps &op, CompR &c, const C
         if (qubit) {
             if (de) {
                 const uint32_t cell = ((C.i >> 1) << 1) | re;
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) c.sign ^= 1u;
+            }
+            if ((c.pwB >> (2 * L + 1)) & 1u) {                // the leaf of path B
+                c.ldiv = ldiv;
+                const uint32_t iB = b_addr(c, C);
+                const uint32_t cell = ((iB >> 1) << 1) | ((c.pwB >> (2 * L)) & 1u);
                 if ((__ldg(C.mem + cell) >> op.fetch) & 1u) c.sign ^= 1u;
             }
         } else if (re) {
@@ -418,6 +505,7 @@ __device__ __forceinline__ bool fast_slice(const SliceOps &op, CompR &c, const C
             }
         }
     }
+    c.ldiv = (ldiv >= 0 && c.pwB == 0) ? -1 : ldiv;
     return true;
 }
 
@@ -428,17 +516,20 @@ __device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16
     return okv != 0;
 }
 
-__device__ __forceinline__ int excited_count(const CompR &c) { return __popc(c.pw) + (int)c.nexc; }
+__device__ __forceinline__ int excited_count(const CompR &c) {
+    return __popc(c.pw) + __popc(c.pwB) + (int)c.nexc;
+}
 
 // Mask J(x) = C_s n X(x) in canonical order (ascending site, then level):
 // checks that its first np elements equal pref[] and returns the next one.
 // Returns -2 on a prefix mismatch, -1 if the mask equals the prefix.
 __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *xs, const Ctx &C,
                                                 const uint32_t *candbits, const uint32_t *pref, int np) {
-    uint32_t w = c.pw, xi = 0;
+    const uint32_t iB = b_addr(c, C);
+    uint32_t wA = c.pw, wB = c.pwB, xi = 0;
     int got = 0;
     for (;;) {
-        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
+        const uint32_t code = next_site(c, xs, C, iB, wA, wB, xi);
         if (code == 0xFFFFFFFFu) return got == np ? -1 : -2;
         const uint32_t site = code >> 1;
         if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
@@ -453,13 +544,14 @@ __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *
 
 // first element (code) of the mask J(x) = C_s n X(x) and its size; the
 // code is 0xFFFF... when the mask is empty.  cl2 = path-word positions that
-// hold any candidate this slice: on-path sites elsewhere cannot be in J.
+// hold any candidate this slice: path sites elsewhere cannot be in J.
 __device__ __forceinline__ uint32_t mask_first(const CompR &c, const uint16_t *xs, const Ctx &C,
                                                const uint32_t *candbits, uint32_t cl2, uint32_t &cnt) {
-    uint32_t w = c.nexc ? c.pw : (c.pw & cl2), xi = 0, first = 0xFFFFFFFFu;
+    uint32_t wA = c.nexc ? c.pw : (c.pw & cl2), wB = c.pwB & cl2, xi = 0, first = 0xFFFFFFFFu;
+    const uint32_t iB = wB ? b_addr(c, C) : 0u;
     cnt = 0;
     for (;;) {
-        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
+        const uint32_t code = next_site(c, xs, C, iB, wA, wB, xi);
         if (code == 0xFFFFFFFFu) return first;
         const uint32_t site = code >> 1;
         if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
@@ -468,78 +560,104 @@ __device__ __forceinline__ uint32_t mask_first(const CompR &c, const uint16_t *x
     }
 }
 
+// where a site sits in the component: 0 = path A bit b, 1 = path B bit b,
+// 2 = off-path list, -1 = not excited
+__device__ __forceinline__ int locate(const CompR &c, const uint16_t *xs, const Ctx &C, uint32_t iB, uint32_t site,
+                                      int &b) {
+    const uint32_t u = site >> 1;
+    const int L = layer_of(u);
+    b = 2 * L + (int)(site & 1u);
+    if (L < C.n && u == path_node(C.i, C.n, L)) return ((c.pw >> b) & 1u) ? 0 : -1;
+    if (c.ldiv >= 0 && L > c.ldiv && L < C.n && u == path_node(iB, C.n, L)) return ((c.pwB >> b) & 1u) ? 1 : -1;
+    for (uint32_t q = 0; q < c.nexc; ++q)
+        if ((xs[q] >> 1) == site) { b = (int)q; return 2; }
+    return -1;
+}
+
 // does the component hold every element of J at its level? (K_J nonzero)
 __device__ __forceinline__ bool holds_all(const CompR &c, const uint16_t *xs, const Ctx &C, const uint32_t *J, int nJ) {
+    const uint32_t iB = b_addr(c, C);
     for (int j = 0; j < nJ; ++j) {
         const uint32_t site = J[j] >> 1, isR = J[j] & 1u;
-        const uint32_t u = site >> 1;
-        const int L = layer_of(u);
-        bool ok = false;
-        if (L < C.n && u == path_node(C.i, C.n, L)) {
-            const int b = 2 * L + (int)(site & 1u);
-            ok = ((c.pw >> b) & 1u) && (C.enc == QRAM_QUBIT || ((c.pwR >> b) & 1u) == isR);
-        } else {
-            for (uint32_t q = 0; q < c.nexc; ++q)
-                if ((xs[q] >> 1) == site) { ok = C.enc == QRAM_QUBIT || (xs[q] & 1u) == isR; break; }
+        int b;
+        const int w = locate(c, xs, C, iB, site, b);
+        if (w < 0) return false;
+        if (C.enc == QRAM_QUTRIT) {
+            const uint32_t lv = w == 0 ? ((c.pwR >> b) & 1u) : (xs[b] & 1u);
+            if (lv != isR) return false;
         }
-        if (!ok) return false;
     }
     return true;
 }
 
-__device__ __forceinline__ void clear_site(CompR &c, uint16_t *xs, const Ctx &C, uint32_t site) {
-    const uint32_t u = site >> 1;
-    const int L = layer_of(u);
-    if (L < C.n && u == path_node(C.i, C.n, L)) {
-        const uint32_t bit = 1u << (2 * L + (int)(site & 1u));
-        c.pw &= ~bit; c.pwR &= ~bit;
-        return;
-    }
-    for (uint32_t q = 0; q < c.nexc; ++q)
-        if ((xs[q] >> 1) == site) {
-            for (uint32_t r = q; r + 1 < c.nexc; ++r) xs[r] = xs[r + 1];
-            --c.nexc;
-            return;
+// K_J clears the sites of J.  Clearing a router of path B that has items
+// below it would move B's path: the component then goes to the generic
+// representation.  Returns false if a capacity was exceeded.
+__device__ __noinline__ bool clear_site(CompR &c, uint16_t *xs, const Ctx &C, uint32_t site) {
+    const uint32_t iB = b_addr(c, C);
+    int b;
+    const int w = locate(c, xs, C, iB, site, b);
+    if (w == 0) { c.pw &= ~(1u << b); c.pwR &= ~(1u << b); return true; }
+    if (w == 1) {
+        if ((b & 1) == 0 && (c.pwB >> (b + 2))) {        // B's router with items below
+            Ents E;
+            to_ents(c, xs, C, E);
+            for (int j = 0; j < E.n; ++j)
+                if ((E.v[j] >> 2) == site) { for (int q = j; q + 1 < E.n; ++q) E.v[q] = E.v[q + 1]; --E.n; break; }
+            return from_ents(c, xs, C, E);
         }
+        c.pwB &= ~(1u << b);
+        if (c.pwB == 0) c.ldiv = -1;
+        return true;
+    }
+    if (w == 2) {
+        for (uint32_t r = (uint32_t)b; r + 1 < c.nexc; ++r) xs[r] = xs[r + 1];
+        --c.nexc;
+    }
+    return true;
 }
 
 // FNV-1a over the sorted (site << 2 | level) list; 0 for the ground state
 __device__ __noinline__ uint64_t config_hash(const CompR c, const uint16_t *xs, const Ctx C) {
-    if (c.pw == 0 && c.nexc == 0) return 0;
+    if (is_ground(c)) return 0;
     uint64_t h = 1469598103934665603ull;
-    uint32_t w = c.pw, xi = 0;
+    const uint32_t iB = b_addr(c, C);
+    uint32_t wA = c.pw, wB = c.pwB, xi = 0;
     for (;;) {
-        const uint32_t code = next_site(c.pw, c.pwR, c.nexc, xs, C, w, xi);
+        const uint32_t code = next_site(c, xs, C, iB, wA, wB, xi);
         if (code == 0xFFFFFFFFu) break;
         const uint32_t v = ((code >> 1) << 2) | ((code & 1u) ? 2u : 1u);
-        for (int b = 0; b < 4; ++b) { h ^= (v >> (8 * b)) & 0xFFu; h *= 1099511628211ull; }
+        for (int bb = 0; bb < 4; ++bb) { h ^= (v >> (8 * bb)) & 0xFFu; h *= 1099511628211ull; }
     }
     return h ? h : 1;
 }
 
-// ---------------------------------------------------------------------------
+// a^e from the two tables a^j and a^(64 j), j < 64
 template <int NT>
 __device__ __forceinline__ double apow(const Smem<NT> &S, int e) {
     return S.powlo[e & 63] * S.powhi[(e >> 6) & 63];
 }
 
 // packed component (see Scratch::cs)
-__device__ __forceinline__ void unpack(const uint4 v, CompR &c, uint32_t &col, uint32_t &addr) {
+__device__ __forceinline__ void unpack(const uint4 v, bool qubit, CompR &c, uint32_t &col, uint32_t &addr) {
     c.pw = v.x;
-    c.pwR = v.y;
-    c.e = (int32_t)(v.z & 0xFFFFu);
-    c.cb = (v.z >> 16) & 0xFFu;
-    c.sign = (v.z >> 24) & 1u;
-    c.nexc = (v.z >> 25) & 0x3Fu;
+    c.pwR = qubit ? 0u : v.y;
+    c.pwB = qubit ? v.y : 0u;
+    c.e = (int32_t)(v.z & 0xFFFu);
+    c.cb = (v.z >> 12) & 0xFFu;
+    c.sign = (v.z >> 20) & 1u;
+    c.nexc = (v.z >> 21) & 0x3Fu;
+    c.ldiv = (int32_t)((v.z >> 27) & 0xFu) - 1;
     col = v.w & 0x3FFFu;
     addr = (v.w >> 14) & 0x3FFFu;
 }
 
-__device__ __forceinline__ uint4 pack(const CompR &c, uint32_t col, uint32_t addr) {
+__device__ __forceinline__ uint4 pack(const CompR &c, bool qubit, uint32_t col, uint32_t addr) {
     uint4 v;
     v.x = c.pw;
-    v.y = c.pwR;
-    v.z = ((uint32_t)c.e & 0xFFFFu) | ((c.cb & 0xFFu) << 16) | ((c.sign & 1u) << 24) | ((c.nexc & 0x3Fu) << 25);
+    v.y = qubit ? c.pwB : c.pwR;
+    v.z = ((uint32_t)c.e & 0xFFFu) | ((c.cb & 0xFFu) << 12) | ((c.sign & 1u) << 20) | ((c.nexc & 0x3Fu) << 21) |
+          ((uint32_t)(c.ldiv + 1) << 27);
     v.w = col | (addr << 14);
     return v;
 }
@@ -549,8 +667,8 @@ __device__ __forceinline__ void load_exc(const Scratch &scr, size_t g, uint32_t 
 }
 
 __device__ __forceinline__ void store_comp(const Scratch &scr, size_t g, const CompR &c, const uint16_t *xs,
-                                           uint32_t col, uint32_t addr) {
-    scr.cs[g] = pack(c, col, addr);
+                                           bool qubit, uint32_t col, uint32_t addr) {
+    scr.cs[g] = pack(c, qubit, col, addr);
     for (uint32_t q = 0; q < c.nexc; ++q) scr.exc[g * kXcap + q] = xs[q];
 }
 
@@ -808,11 +926,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         for (uint32_t r = threadIdx.x; r < ncomp0; r += NT) {
             const uint32_t col = expl[r >> kb], cw = r & ((1u << kb) - 1u);
             CompR c;
-            c.pw = 0; c.pwR = 0; c.e = 0; c.nexc = 0;
+            c.pw = 0; c.pwR = 0; c.pwB = 0; c.ldiv = -1; c.e = 0; c.nexc = 0;
             const uint32_t j = __ldg(P.bus + col);
             if (qubit) { c.cb = cw; c.sign = __popc(j & cw) & 1u; }   // first wall: (-1)^(j.c)
             else { c.cb = j; c.sign = 0; }
-            store_comp(scr, cbase + r, c, nullptr, col, __ldg(P.addr + col));
+            store_comp(scr, cbase + r, c, nullptr, qubit, col, __ldg(P.addr + col));
         }
     }
     if (threadIdx.x == 0) S.ncomp = S.status == QRAM_OK ? ncomp0 : 0;
@@ -877,13 +995,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | empty/ground << 2 | overlap sign + 1
             Ctx C;
             if (alive) {
-                unpack(cur, c, lab, addr);
+                unpack(cur, qubit, c, lab, addr);
                 if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                 C = make_ctx(P.enc, n, P.mem, addr);
                 if (s_prev > 0) {                           // pending K_J of slice s_prev
                     if (nJ > 0) {
                         alive = holds_all(c, xs, C, S.J, nJ);
-                        if (alive) for (int j = 0; j < nJ; ++j) clear_site(c, xs, C, S.J[j] >> 1);
+                        if (alive)
+                            for (int j = 0; j < nJ; ++j)
+                                if (!clear_site(c, xs, C, S.J[j] >> 1)) capfail = true;
                     }
                     if (alive) c.e += excited_count(c);
                 }
@@ -895,7 +1015,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
                 const double ae = apow(S, c.e);
-                if (uni && c.e >= H) capfail = true;                 // exponent bound violated
+                if (c.e >= 4096 || (uni && c.e >= H)) capfail = true;   // exponent bound (packed in 12 bits)
                 if (!final_epoch) {
                     c1 = mask_first(c, xs, C, S.candbits, S.cl2, mcnt);
                     if (!uni) {
@@ -908,7 +1028,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     }
                 } else {
                     int ovs = 0;
-                    const bool ground = c.pw == 0 && c.nexc == 0;     // ground tree configuration
+                    const bool ground = is_ground(c);                 // ground tree configuration
                     if (ground) {
                         const uint32_t col = lab;
                         if (qubit) {
@@ -964,10 +1084,10 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             if (compact) {
                 uint32_t tot;
                 const uint32_t pre = block_scan_flag(alive, &tot, S);
-                if (alive && !final_epoch) store_comp(scr, cbase + wr + pre, c, xs, lab, addr);
+                if (alive && !final_epoch) store_comp(scr, cbase + wr + pre, c, xs, qubit, lab, addr);
                 wr += tot;
             } else if (alive && !final_epoch) {
-                store_comp(scr, cbase + r, c, xs, lab, addr);
+                store_comp(scr, cbase + r, c, xs, qubit, lab, addr);
             }
         }
         if (lane == 0) S.segn[warp] = wcur;
@@ -1106,7 +1226,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     double we = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
                         CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
-                        unpack(scr.cs[cbase + r], c, lab, addr);
+                        unpack(scr.cs[cbase + r], qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         if (mask_query(c, xs, C, S.candbits, pref, level) == -1) {
@@ -1127,7 +1247,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     double f = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
                         CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
-                        unpack(scr.cs[cbase + r], c, lab, addr);
+                        unpack(scr.cs[cbase + r], qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         const long long q = mask_query(c, xs, C, S.candbits, pref, level);
@@ -1146,7 +1266,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     uint32_t best = 0xFFFFFFFFu;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
                         CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
-                        unpack(scr.cs[cbase + r], c, lab, addr);
+                        unpack(scr.cs[cbase + r], qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         const long long q = mask_query(c, xs, C, S.candbits, pref, level);
