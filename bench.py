@@ -43,6 +43,26 @@ def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def trajectory_base(rank: int) -> int:
+    """First trajectory index of a rank: ranks simulate disjoint ranges (weak
+    scaling; trajectories are independent given (seed, index))."""
+    return rank * 1_000_000_000
+
+
+def world_throughput(t_local: float, steps: int, ntraj: int, dist=None) -> tuple:
+    """Whole-job trajectories/s: every rank ran `steps` x `ntraj`; the job
+    takes as long as the slowest rank (max over ranks, the only exchange)."""
+    import torch
+    world = 1
+    t = t_local
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        tt = torch.tensor([t_local], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt[0])
+    return world * steps * ntraj / t, t
+
+
 def _problem():
     return W.data_loading(W.QUBIT, N, K, seed=SEED)
 
@@ -195,7 +215,7 @@ def main():
     gam = torch.tensor(gam_h, dtype=torch.float64, device=dev)
     out = torch.empty((NTRAJ, 48), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # > 126 MB L2
-    base = rank * 1_000_000_000                                           # disjoint trajectory ranges
+    base = trajectory_base(rank)                                          # disjoint trajectory ranges
     traj0 = torch.zeros(1, dtype=torch.int64, device=dev)
     graph = sim.graph("pruned", gam, out, traj0)                          # one persistent launch per step
 
@@ -231,12 +251,7 @@ def main():
     ms = [a.elapsed_time(b) for a, b in ev]
     cl = clocks.stop()
     res = sim.results(out)
-    t_dev = sum(ms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_dev], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt[0])
-    value = world * args.steps * NTRAJ / t_dev
+    value, t_dev = world_throughput(sum(ms) / 1e3, args.steps, NTRAJ, dist)
 
     # ---- pruned vs full on the same stratified subset --------------------
     sub = np.concatenate([np.arange(b, b + args.full_per_batch) for b in range(0, NTRAJ, BATCH)])
@@ -261,6 +276,21 @@ def main():
     t_psub = timed(lambda: sim.run_pruned(base + 7_000_000, gsub, osub), reps=3)
     pr_res = sim.results(osub)
     agree = float(np.max(np.abs(full_res["fidelity"] - pr_res["fidelity"])))
+
+    # ---- pruned vs full per gamma decade (the shape of the paper's Tab. V) ---
+    per_decade = {}
+    nd = 4000
+    gd = torch.empty(nd, dtype=torch.float64, device=dev)
+    od = torch.empty((nd, 48), dtype=torch.uint8, device=dev)
+    for dg in (1e-5, 1e-4, 1e-3, 1e-2):
+        gd.fill_(dg)
+        tp = timed(lambda: sim.run_pruned(base + 8_000_000, gd, od))
+        rp = sim.results(od)
+        tf = timed(lambda: sim.run_full(base + 8_000_000, gd, od))
+        rf = sim.results(od)
+        per_decade[f"{dg:g}"] = {"pruned_traj_per_s": nd / tp, "full_traj_per_s": nd / tf, "speedup": tf / tp,
+                                 "evolved_fraction": float(np.mean(rp["explicit_comps"]) / np.mean(rf["explicit_comps"])),
+                                 "max_abs_fidelity_diff": float(np.max(np.abs(rp["fidelity"] - rf["fidelity"])))}
 
     # ---- per-query latency: one gamma batch (1000 trajectories) alone -----
     lat = []
@@ -324,6 +354,7 @@ def main():
                      "pruned_same_subset": len(sub) / t_psub, "speedup_pruned_over_full": t_full / t_psub,
                      "subset": f"{args.full_per_batch} trajectories per gamma batch ({len(sub)} total)",
                      "max_abs_fidelity_diff_pruned_vs_full": agree},
+            "per_gamma_decade": per_decade,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "query": "one gamma batch of 1000 trajectories launched alone", "n": int(len(lat))},
             "mean_fidelity": float(res["fidelity"].mean()), "status_ok": bool(np.all(res["status"] == 0)),

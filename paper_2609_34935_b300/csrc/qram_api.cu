@@ -4,11 +4,13 @@
 // time-sliced bucket-brigade schedule (Sec. II.A, Eqs. (2)-(4); App. C gate
 // list), sizes the per-CTA scratch and launches the kernels of
 // qram_kernels.cu.  No CPU computation of the method happens here.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -37,6 +39,7 @@ struct qram_sim {
     uint32_t nhist = 0;
     SliceOps ops[kMaxT]{};
     uint32_t occ2[kMaxT]{};
+    Orbit orbit{};
     uint64_t launches = 0;
     int sms = 0, blocks_per_sm = 0;
     int threads = 256;          // launch variant (threads per CTA)
@@ -161,7 +164,10 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax, i
     L.o_cs = off; off = align_up(off + slots * (size_t)L.ecap * 16);
     L.o_exc = off; off = align_up(off + slots * (size_t)L.ecap * kXcap * 2);
     // per-warp segments: warp w sees at most ceil(ecap / threads) * 32 components
-    L.selseg = (uint32_t)(((size_t)L.ecap + threads - 1) / threads * 32);
+    // (also when each thread of a warp materialises all configurations of one branch)
+    const size_t per_comp = ((size_t)L.ecap + threads - 1) / threads * 32;
+    const size_t per_branch = ((size_t)D + threads - 1) / threads * 32 * ((size_t)L.ecap / (size_t)std::max(D, 1));
+    L.selseg = (uint32_t)std::max(per_comp, per_branch);
     L.o_selk = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 4);
     L.o_selw = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 8);
     L.total = off;
@@ -221,6 +227,7 @@ Params base_params(qram_sim *S) {
     P.w2u = S->d_w2u;
     std::memcpy(P.ops, S->ops, sizeof(P.ops));
     std::memcpy(P.occ2, S->occ2, sizeof(P.occ2));
+    P.orbit = S->orbit;
     return P;
 }
 
@@ -284,6 +291,73 @@ void build_occupancy(int n, int k, const SliceOps *ops, uint32_t *occ2) {
         pw ^= t | (t << 2);
         occ2[s] = pw;
     }
+}
+
+void build_orbit(int n, int k, const SliceOps *ops, Orbit *orb) {
+    std::memset(orb, 0, sizeof(*orb));
+    const int T = 6 * n + 2 * k;
+    int8_t pos[2 * kMaxN] = {0}, bus[kMaxK] = {0};
+    for (int t = 0; t < k; ++t) bus[t] = (int8_t)(1 + n + t);
+    auto is_addr = [&](int it) { return it >= 1 && it <= n; };
+    uint32_t fetched = 0;
+    bool good = true;
+    int in_tree[kMaxN + kMaxK] = {0}, first[kMaxN + kMaxK], last[kMaxN + kMaxK], fetch_at[kMaxK];
+    for (int x = 0; x < kMaxN + kMaxK; ++x) { first[x] = -1; last[x] = -1; }
+    for (int t = 0; t < kMaxK; ++t) fetch_at[t] = -1;
+    for (int s = 1; s < T; ++s) {
+        const SliceOps &o = ops[s];
+        if (o.load >= 0) {
+            const int8_t a = (int8_t)(1 + o.load);
+            if (pos[1] == 0) pos[1] = a;
+            else if (pos[1] == a) pos[1] = 0;
+            else good = false;
+        }
+        if (o.bus >= 0) {
+            if (is_addr(pos[1])) good = false;
+            std::swap(pos[1], bus[o.bus]);
+            if (bus[o.bus] != 0 && bus[o.bus] != 1 + n + o.bus) good = false;
+        }
+        for (int L = 0; L < n; ++L)
+            if ((o.iswap >> L) & 1u) std::swap(pos[2 * L], pos[2 * L + 1]);
+        for (int L = 0; L + 1 < n; ++L) {
+            if (!((o.cswap >> L) & 1u)) continue;
+            // an item may only cross a router that already holds its address bit
+            if ((pos[2 * L + 1] || pos[2 * L + 3]) && !is_addr(pos[2 * L])) good = false;
+            std::swap(pos[2 * L + 1], pos[2 * L + 3]);
+        }
+        if (o.fetch >= 0) {
+            if (pos[2 * (n - 1) + 1] != 1 + n + o.fetch || !is_addr(pos[2 * (n - 1)])) good = false;
+            fetched |= 1u << o.fetch;
+            fetch_at[o.fetch] = s;
+        }
+        uint32_t occ = 0, bm = 0;
+        for (int b = 0; b < 2 * n; ++b) {
+            orb->item[s][b] = pos[b];
+            if (pos[b]) {
+                occ |= 1u << b;
+                const int x = pos[b] - 1;
+                ++in_tree[x];
+                if (first[x] < 0) first[x] = s;
+                last[x] = s;
+            }
+        }
+        for (int t = 0; t < k; ++t) if (bus[t] == 1 + n + t) bm |= 1u << t;
+        orb->occ[s] = occ;
+        orb->bus[s] = (uint8_t)bm;
+        orb->fetched[s] = (uint8_t)fetched;
+    }
+    // the kernels take the exposures in closed form: address bit l in the tree
+    // during slices [2l+1, T-2l-2], data qubit t during [2n+2t+1, 4n+2t],
+    // fetched at 3n+2t+1 (Sec. II.A); the orbit must end with an empty tree
+    for (int l = 0; l < n; ++l)
+        if (first[l] != 2 * l + 1 || last[l] != T - 2 * l - 2 || in_tree[l] != last[l] - first[l] + 1) good = false;
+    for (int t = 0; t < k; ++t) {
+        const int x = n + t;
+        if (first[x] != 2 * n + 2 * t + 1 || last[x] != 4 * n + 2 * t || in_tree[x] != 2 * n) good = false;
+        if (fetch_at[t] != 3 * n + 2 * t + 1) good = false;
+    }
+    if (orb->occ[T - 1] != 0 || orb->bus[T - 1] != (uint8_t)((1u << k) - 1u)) good = false;
+    orb->ok = good ? 1 : 0;
 }
 
 size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, int threads, void *base, Scratch *scr) {
@@ -364,6 +438,7 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     S->seed = p->seed;
     if (build_ops_impl(S->n, S->k, S->ops) != QRAM_OK) { delete S; return QRAM_E_ARG; }
     build_occupancy(S->n, S->k, S->ops, S->occ2);
+    build_orbit(S->n, S->k, S->ops, &S->orbit);
     DeviceGuard g(device);
     int rc = QRAM_OK;
     const size_t D = (size_t)S->D;

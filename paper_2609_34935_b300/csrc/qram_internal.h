@@ -48,6 +48,19 @@ struct Scratch {
     uint32_t cand_cap, seg_cap, ecap, selseg;
 };
 
+// Noiseless orbit of the items through the path-word positions.  Items:
+// 0 = none, 1 + l = the address bit routed at layer l, 1 + n + t = data
+// qubit t.  On a noiseless orbit every gate moves items between positions
+// independently of their values (a router holds its address bit before any
+// item crosses it), so one table serves every (address, data) pair.
+struct Orbit {
+    int8_t item[kMaxT][2 * kMaxN];   // item at path-word position b after the gates of slice s
+    uint32_t occ[kMaxT];             // positions holding an item
+    uint8_t bus[kMaxT];              // bus slots holding their data qubit
+    uint8_t fetched[kMaxT];          // data qubits already fetched
+    int ok;                          // 0: the schedule breaks the assumption (no lazy branches)
+};
+
 struct DumpOut {
     uint32_t *col;       // [cap] explicit components at the end
     uint32_t *bus;
@@ -85,6 +98,7 @@ struct Params {
     int hist_pad;                  // bins per exponent histogram (dynamic shared memory: 3 of them)
     SliceOps ops[kMaxT];
     uint32_t occ2[kMaxT];  // per slice: path-word positions any noiseless orbit can hold excited
+    Orbit orbit;
 };
 
 cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s);
@@ -99,6 +113,8 @@ int build_ops(int n, int k, SliceOps *ops);
 // occ2[s] = (layer, slot) positions, as path-word bits, that an item can
 // occupy after the gates of slice s in a noiseless orbit
 void build_occupancy(int n, int k, const SliceOps *ops, uint32_t *occ2);
+// the item table of the noiseless orbit (see Orbit)
+void build_orbit(int n, int k, const SliceOps *ops, Orbit *orb);
 // lays out the per-slot scratch of `slots` CTAs at `base` (may be null: size only); returns bytes
 size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, int threads, void *base, Scratch *scr);
 int resident_slots_per_device(int device, int threads, size_t dyn);

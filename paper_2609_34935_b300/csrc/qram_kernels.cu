@@ -60,6 +60,20 @@ __device__ __forceinline__ uint32_t path_node(uint32_t i, int n, int L) {
     return ((1u << L) - 1u) + (i >> (n - L));
 }
 __device__ __forceinline__ uint32_t routed_bit(uint32_t i, int n, int l) { return (i >> (n - 1 - l)) & 1u; }
+// lowest common ancestor of two nodes (heap order: children of v are 2v+1, 2v+2)
+__device__ __forceinline__ uint32_t tree_lca(uint32_t u, uint32_t v) {
+    uint32_t x = u + 1u, y = v + 1u;                 // 1-based: the path is the binary prefix
+    const int dx = 31 - __clz(x), dy = 31 - __clz(y);
+    if (dx > dy) x >>= dx - dy; else y >>= dy - dx;
+    while (x != y) { x >>= 1; y >>= 1; }
+    return x - 1u;
+}
+// u is an ancestor of r, r itself, or inside subtree(r)
+__device__ __forceinline__ bool tree_related(uint32_t u, uint32_t r) {
+    const uint32_t x = u + 1u, y = r + 1u;
+    const int dx = 31 - __clz(x), dy = 31 - __clz(y);
+    return dx <= dy ? (y >> (dy - dx)) == x : (x >> (dx - dy)) == y;
+}
 // spread bit L of x to bit 2L
 __device__ __forceinline__ uint32_t spread2(uint32_t x) {
     x &= 0xFFFFu;
@@ -107,7 +121,7 @@ struct Smem {
     uint32_t scanw[NW];
     uint32_t wcount[NW];
     uint32_t segn[NW];             // entries of each warp's compact selection segment
-    uint32_t syncmask[8];          // slices with a candidate a noiseless orbit can excite / with any candidate
+    uint32_t syncmask[8];          // slices whose candidates can matter: [0..3] before a jump, [4..7] after
     uint32_t cl2;                  // path-word positions (2L + slot) holding a candidate in the current slice
     uint32_t J[kMaxJ];
     int nJ;
@@ -117,19 +131,27 @@ struct Smem {
     int t;
     int status;
     double sA, sB, sC;
+    double dn, al, qt[kMaxK];      // per-epoch data factors (qubit): norm^2, final overlap, 1/(1 + a^(2 m_t))
+    uint32_t region;               // after a jump: root of the subtree that can hold excitations
 };
 
+// Block sums of doubles.  FP64 issue is scarce on this part (about two
+// lanes per clock per SM), so each warp reduces its own values and a single
+// warp reduces the per-warp partials; every thread then reads the result.
 template <int NT>
 __device__ double block_sum(double x, double *red, Smem<NT> &S) {
     constexpr int NW = NT / 32;
     x = warp_sum(x);
-    const int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = x;
+    if (lane == 0) red[w] = x;
     __syncthreads();
-    double r = 0.0;
-    for (int i = 0; i < NW; ++i) r += red[i];
-    return r;
+    if (w == 0) {
+        const double v = warp_sum(lane < NW ? red[lane] : 0.0);
+        if (lane == 0) S.sA = v;
+    }
+    __syncthreads();
+    return S.sA;
 }
 
 // three sums at once
@@ -137,13 +159,38 @@ template <int NT>
 __device__ void block_sum3(double &a, double &b, double &c, Smem<NT> &S) {
     constexpr int NW = NT / 32;
     a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
-    const int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) { S.redA[w] = a; S.redB[w] = b; S.redC[w] = c; }
+    if (lane == 0) { S.redA[w] = a; S.redB[w] = b; S.redC[w] = c; }
     __syncthreads();
-    double ra = 0.0, rb = 0.0, rc = 0.0;
-    for (int i = 0; i < NW; ++i) { ra += S.redA[i]; rb += S.redB[i]; rc += S.redC[i]; }
-    a = ra; b = rb; c = rc;
+    if (w == 0) {
+        const double ra = warp_sum(lane < NW ? S.redA[lane] : 0.0);
+        const double rb = warp_sum(lane < NW ? S.redB[lane] : 0.0);
+        const double rc = warp_sum(lane < NW ? S.redC[lane] : 0.0);
+        if (lane == 0) { S.sA = ra; S.sB = rb; S.sC = rc; }
+    }
+    __syncthreads();
+    a = S.sA; b = S.sB; c = S.sC;
+}
+
+// exclusive scan of a count over the block; returns prefix, total in *tot
+template <int NT>
+__device__ uint32_t block_scan_count(uint32_t v, uint32_t *tot, Smem<NT> &S) {
+    constexpr int NW = NT / 32;
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) S.scanw[w] = x;
+    __syncthreads();
+    uint32_t base = 0, all = 0;
+    for (uint32_t i = 0; i < NW; ++i) { if (i < w) base += S.scanw[i]; all += S.scanw[i]; }
+    *tot = all;
+    return base + x - v;
 }
 
 // exclusive scan of a 0/1 flag over the block; returns prefix, total in *tot
@@ -592,29 +639,32 @@ __device__ __forceinline__ bool holds_all(const CompR &c, const uint16_t *xs, co
 
 // K_J clears the sites of J.  Clearing a router of path B that has items
 // below it would move B's path: the component then goes to the generic
-// representation.  Returns false if a capacity was exceeded.
-__device__ __noinline__ bool clear_site(CompR &c, uint16_t *xs, const Ctx &C, uint32_t site) {
+// representation.  Takes and returns the register state by value (callers
+// keep it in registers); *okp = 0 if a capacity was exceeded.
+__device__ __noinline__ CompR clear_site(CompR c, uint16_t *xs, const Ctx C, uint32_t site, int *okp) {
+    *okp = 1;
     const uint32_t iB = b_addr(c, C);
     int b;
     const int w = locate(c, xs, C, iB, site, b);
-    if (w == 0) { c.pw &= ~(1u << b); c.pwR &= ~(1u << b); return true; }
+    if (w == 0) { c.pw &= ~(1u << b); c.pwR &= ~(1u << b); return c; }
     if (w == 1) {
         if ((b & 1) == 0 && (c.pwB >> (b + 2))) {        // B's router with items below
             Ents E;
             to_ents(c, xs, C, E);
             for (int j = 0; j < E.n; ++j)
                 if ((E.v[j] >> 2) == site) { for (int q = j; q + 1 < E.n; ++q) E.v[q] = E.v[q + 1]; --E.n; break; }
-            return from_ents(c, xs, C, E);
+            if (!from_ents(c, xs, C, E)) *okp = 0;
+            return c;
         }
         c.pwB &= ~(1u << b);
         if (c.pwB == 0) c.ldiv = -1;
-        return true;
+        return c;
     }
     if (w == 2) {
         for (uint32_t r = (uint32_t)b; r + 1 < c.nexc; ++r) xs[r] = xs[r + 1];
         --c.nexc;
     }
-    return true;
+    return c;
 }
 
 // FNV-1a over the sorted (site << 2 | level) list; 0 for the ground state
@@ -701,18 +751,80 @@ __device__ int good_exposure(const Params &P, uint32_t col, int s) {
     return E;
 }
 
-// qubit data-register norm^2 of a good branch after damping layers 1..s:
-// prod_t (1 + a^(2 m_t)) / 2 (Lemma 1)
-template <int NT>
-__device__ double data_norm2(const Params &P, const Smem<NT> &S, int s) {
-    if (P.enc != QRAM_QUBIT) return 1.0;
-    double r = 1.0;
-    for (int t = 0; t < P.k; ++t) {
-        const int m = ov(2 * P.n + 2 * t + 1, 4 * P.n + 2 * t, s);
-        const double am = apow(S, m);
-        r *= 0.5 * (1.0 + am * am);
+// ---- lazy branches --------------------------------------------------------
+// Before the first fired jump every configuration is still on its noiseless
+// orbit: K0 only scales it (Eq. (12)).  Its path word at any slice follows
+// from the orbit table, its weight from the closed-form exposure; explicit
+// state is only needed once a jump fires, and only for the configurations
+// whose mask at that slice is non-empty (the others are annihilated).
+
+// value of an item on the orbit of address i: address bits are excited at
+// level L/R (qutrit) or when 1 (qubit); data qubit t carries the wall
+// configuration cw (qubit) or the bus bit j, flipped by the fetch (qutrit)
+__device__ __forceinline__ uint32_t orbit_value(const Params &P, int it, int s, uint32_t i, uint32_t cw, uint32_t j,
+                                                uint32_t d, uint32_t &isR) {
+    const int n = P.n;
+    if (it <= n) {
+        const uint32_t r = routed_bit(i, n, it - 1);
+        isR = r;
+        return P.enc == QRAM_QUTRIT ? 1u : r;
     }
-    return r;
+    const int t = it - 1 - n;
+    if (P.enc == QRAM_QUBIT) { isR = 0; return (cw >> t) & 1u; }
+    const uint32_t v = ((((P.orbit.fetched[s] >> t) & 1u) ? (j ^ d) : j) >> t) & 1u;
+    isR = v;
+    return v;
+}
+
+// candidates of slice s on the orbit of address i at the positions `pos`:
+// *all = every configuration has a non-empty mask; the return value (qubit)
+// = data qubits whose excitation at a candidate site makes it non-empty
+__device__ __forceinline__ uint32_t orbit_hits(const Params &P, const uint32_t *candbits, uint32_t pos, int s,
+                                               uint32_t i, uint32_t j, uint32_t d, bool &all) {
+    const int n = P.n;
+    uint32_t tm = 0;
+    all = false;
+    for (uint32_t w = pos; w; w &= w - 1u) {
+        const int b = __ffs(w) - 1;
+        const uint32_t site = 2u * path_node(i, n, b >> 1) + (uint32_t)(b & 1);
+        if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+        const int it = P.orbit.item[s][b];
+        if (P.enc == QRAM_QUBIT && it > n) { tm |= 1u << (it - 1 - n); continue; }
+        uint32_t isR;
+        if (orbit_value(P, it, s, i, 0u, j, d, isR)) all = true;
+    }
+    return tm;
+}
+
+// the explicit state of configuration cw of the branch with address i after
+// the gates of slice s (exponent left to the caller)
+__device__ __forceinline__ CompR orbit_state(const Params &P, int s, uint32_t i, uint32_t cw, uint32_t j, uint32_t d) {
+    CompR c;
+    c.pw = 0; c.pwR = 0; c.pwB = 0; c.ldiv = -1; c.e = 0; c.nexc = 0;
+    for (uint32_t w = P.orbit.occ[s]; w; w &= w - 1u) {
+        const int b = __ffs(w) - 1;
+        uint32_t isR;
+        const uint32_t v = orbit_value(P, P.orbit.item[s][b], s, i, cw, j, d, isR);
+        c.pw |= v << b;
+        if (P.enc == QRAM_QUTRIT) c.pwR |= (v & isR) << b;
+    }
+    const uint32_t bm = P.orbit.bus[s], fm = P.orbit.fetched[s];
+    if (P.enc == QRAM_QUBIT) {
+        c.cb = cw & bm;
+        c.sign = (__popc(j & cw) + __popc(cw & d & fm)) & 1u;          // first wall, fetch phases
+    } else {
+        c.cb = ((j & ~fm) | ((j ^ d) & fm)) & bm;
+        c.sign = 0;
+    }
+    return c;
+}
+
+// qubit data exposure of wall configuration cw after damping slices 1..s
+__device__ __forceinline__ int data_exposure(const Params &P, uint32_t cw, int s) {
+    int E = 0;
+    for (int t = 0; t < P.k; ++t)
+        if ((cw >> t) & 1u) E += ov(2 * P.n + 2 * t + 1, 4 * P.n + 2 * t, s);
+    return E;
 }
 
 // ---------------------------------------------------------------------------
@@ -817,12 +929,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     if (threadIdx.x == 0) S.ncand = ncand;
 
     // per-slice offsets (candidates are sorted by (slice, site))
-    if (threadIdx.x < 8) S.syncmask[threadIdx.x] = 0;   // [0..3] relevant, [4..7] any candidate
+    if (threadIdx.x < 8) S.syncmask[threadIdx.x] = 0;   // [4..7] are set at each fired jump
     __syncthreads();
     for (uint32_t c = threadIdx.x; c < ncand; c += NT) {
         const uint32_t s = cand[c] >> 16, q = cand[c] & 0xFFFFu;
         const int L = layer_of(q >> 1);
-        atomicOr(&S.syncmask[4 + (s >> 5)], 1u << (s & 31u));
         if ((P.occ2[s] >> (2 * L + (int)(q & 1u))) & 1u)   // a noiseless orbit can hold it excited
             atomicOr(&S.syncmask[s >> 5], 1u << (s & 31u));
     }
@@ -899,7 +1010,13 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         S.powhi[threadIdx.x] = p;
     }
     uint32_t *expl = scr.expl + slot * (size_t)P.D;
-    {
+    // pruned mode keeps every branch implicit until a jump fires (the state
+    // dump reads the explicit set at the end, so it keeps the eager form)
+    const bool lazy = P.mode == kPruned && P.orbit.ok && !P.dump_mode;
+    if (lazy) {
+        // only the size of the explicit set is reported: B plus the reference
+        if (threadIdx.x == 0) S.nexpl = S.nbad + (S.refcol >= 0 ? 1u : 0u);
+    } else {
         uint32_t base = 0;
         for (uint32_t b0 = 0; b0 < (uint32_t)P.D; b0 += NT) {
             const uint32_t b = b0 + threadIdx.x;
@@ -922,7 +1039,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     if (ncomp0 > scr.ecap) { if (threadIdx.x == 0) S.status = QRAM_E_CAP; }
     __syncthreads();
     const size_t cbase = slot * (size_t)scr.ecap;
-    if (S.status == QRAM_OK) {
+    if (S.status == QRAM_OK && !lazy) {
         for (uint32_t r = threadIdx.x; r < ncomp0; r += NT) {
             const uint32_t col = expl[r >> kb], cw = r & ((1u << kb) - 1u);
             CompR c;
@@ -933,7 +1050,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             store_comp(scr, cbase + r, c, nullptr, qubit, col, __ldg(P.addr + col));
         }
     }
-    if (threadIdx.x == 0) S.ncomp = S.status == QRAM_OK ? ncomp0 : 0;
+    if (threadIdx.x == 0) S.ncomp = (S.status == QRAM_OK && !lazy) ? ncomp0 : 0;
     __syncthreads();
 
     // ---- 4. epochs ----------------------------------------------------------
@@ -951,14 +1068,33 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     for (;;) {
         // next slice whose candidates can matter: before the first fired jump
         // every component is on a noiseless orbit, so a candidate on a position
-        // no orbit can excite leaves J empty and needs no draw
+        // no orbit can excite leaves J empty and needs no draw; after it, only
+        // candidates in the subtree a jump damaged (and on the path to it)
         int s1 = s_prev + 1;
         {
             const uint32_t *m = jumped ? S.syncmask + 4 : S.syncmask;
             while (s1 < T && !((m[s1 >> 5] >> (s1 & 31)) & 1u)) ++s1;
         }
         const bool final_epoch = s1 >= T;
-        if (threadIdx.x == 0) S.cl2 = 0;
+        if (threadIdx.x == 0) {
+            S.cl2 = 0;
+            // data factors after damping slices 1..sw (Lemma 1): each data
+            // qubit t contributes (1 + a^(2 m_t)) / 2 to a branch's norm^2
+            const int sw = final_epoch ? T - 1 : s1 - 1;
+            double dn = 1.0, al = 1.0;
+            if (qubit) {
+                const double an = apow(S, 2 * n);
+                for (int q = 0; q < P.k; ++q) {
+                    const double am = apow(S, ov(2 * n + 2 * q + 1, 4 * n + 2 * q, sw));
+                    const double h = 1.0 + am * am;
+                    dn *= 0.5 * h;
+                    S.qt[q] = 1.0 / h;
+                    al *= 0.5 * (1.0 + an);
+                }
+            }
+            S.dn = dn;
+            S.al = al;
+        }
         __syncthreads();
         if (!final_epoch) {
             for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {
@@ -971,9 +1107,52 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         const uint32_t ncomp = S.ncomp;
         const int nJ = S.nJ;
         const bool compact = s_prev > 0 && nJ > 0;
+        const bool lazy_pre = lazy && !jumped;       // every branch still on its noiseless orbit
         double wsum = 0.0, wempty = 0.0, ovl = 0.0;
+        bool capfail_lazy = false;
+        if (lazy_pre) {
+            // closed-form weights of every branch (Eq. (12), Lemma 1): the
+            // configurations of a branch share its address exposure E and
+            // differ only in their data qubits, whose factors are per-epoch
+            // scalars.  Equal-magnitude inputs are counted in the integer
+            // histograms over E (FP64 issue is scarce); a branch with a data
+            // qubit excited at a candidate keeps only the configurations
+            // where those qubits are 0 in the empty-mask weight.
+            const int sw = final_epoch ? T - 1 : s1 - 1;
+            const uint32_t pos = final_epoch ? 0u : (S.cl2 & P.orbit.occ[s1]);
+            for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
+                const uint32_t i = __ldg(P.addr + b);
+                const int E = good_exposure(P, b, sw);
+                bool all = false;
+                uint32_t tm = 0;
+                if (pos) tm = orbit_hits(P, S.candbits, pos, s1, i, __ldg(P.bus + b), __ldg(P.mem + i), all);
+                double qp = 1.0;
+                for (uint32_t x = tm; x; x &= x - 1u) qp *= S.qt[__ffs(x) - 1];
+                if (uni) {
+                    if (E >= H) { capfail_lazy = true; continue; }
+                    atomicAdd(&hall[E], 1u);
+                    if (final_epoch) {                      // the orbit ends in the ground tree, Walsh coefficient +1
+                        atomicAdd(&hemp[E], 1u);
+                        atomicAdd(&hov[E], 1);
+                    } else if (!all && !tm) {
+                        atomicAdd(&hemp[E], 1u);
+                    } else if (!all) {
+                        const double ae = apow(S, E);
+                        wempty += ae * ae * qp;
+                    }
+                } else {
+                    const double w2 = col_w2(P, b);
+                    const double ae = apow(S, E);
+                    const double w = w2 * ae * ae;
+                    wsum += w;
+                    if (final_epoch) { wempty += w; ovl += w2 * ae; }
+                    else if (!all) wempty += w * qp;
+                }
+            }
+        }
+        const uint32_t ncomp_pass = lazy_pre ? 0u : ncomp;
         uint32_t wr = 0;        // write cursor (compaction)
-        bool capfail = false;
+        bool capfail = capfail_lazy;
         // this warp's segment of the compact list of components with a non-empty mask
         const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
         uint32_t *selk = scr.selk + (slot * NW + warp) * (size_t)scr.selseg;
@@ -982,12 +1161,12 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         // one chunk of look-ahead: the next chunk's packed state is in flight
         // while this chunk evolves
         uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
-        if (threadIdx.x < ncomp) nxt = scr.cs[cbase + threadIdx.x];
-        for (uint32_t r0 = 0; r0 < ncomp; r0 += NT) {
+        if (threadIdx.x < ncomp_pass) nxt = scr.cs[cbase + threadIdx.x];
+        for (uint32_t r0 = 0; r0 < ncomp_pass; r0 += NT) {
             const uint32_t r = r0 + threadIdx.x;
-            bool alive = r < ncomp;
+            bool alive = r < ncomp_pass;
             const uint4 cur = nxt;
-            if (r + NT < ncomp) nxt = scr.cs[cbase + r + NT];
+            if (r + NT < ncomp_pass) nxt = scr.cs[cbase + r + NT];
             CompR c;
             uint16_t xs[kXcap];
             uint32_t lab = 0, addr = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
@@ -1002,8 +1181,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     if (nJ > 0) {
                         alive = holds_all(c, xs, C, S.J, nJ);
                         if (alive)
-                            for (int j = 0; j < nJ; ++j)
-                                if (!clear_site(c, xs, C, S.J[j] >> 1)) capfail = true;
+                            for (int j = 0; j < nJ; ++j) {
+                                int okc;
+                                c = clear_site(c, xs, C, S.J[j] >> 1, &okc);
+                                if (!okc) capfail = true;
+                            }
                     }
                     if (alive) c.e += excited_count(c);
                 }
@@ -1014,19 +1196,20 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     if (!apply_slice(P.ops[s], c, xs, C)) { capfail = true; break; }
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
-                const double ae = apow(S, c.e);
                 if (c.e >= 4096 || (uni && c.e >= H)) capfail = true;   // exponent bound (packed in 12 bits)
                 if (!final_epoch) {
                     c1 = mask_first(c, xs, C, S.candbits, S.cl2, mcnt);
                     if (!uni) {
+                        const double ae = apow(S, c.e);
                         w = col_w2(P, lab) * k2 * ae * ae;
                         wsum += w;
                         if (mcnt == 0) wempty += w;
                     } else {
-                        if (mcnt > 0) w = w2u * ae * ae;
+                        if (mcnt > 0) { const double ae = apow(S, c.e); w = w2u * ae * ae; }
                         if (c.e < H) hkey = ((uint32_t)c.e << 3) | ((mcnt == 0 ? 1u : 0u) << 2) | 1u;
                     }
                 } else {
+                    const double ae = apow(S, c.e);
                     int ovs = 0;
                     const bool ground = is_ground(c);                 // ground tree configuration
                     if (ground) {
@@ -1094,31 +1277,6 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
         __syncthreads();
         if (threadIdx.x == 0 && compact) S.ncomp = wr;
-        // good branches: closed-form weights before the first jump (Eq. (18))
-        double wg = 0.0, og = 0.0;
-        if (P.mode == kPruned && !jumped) {
-            const int sw = final_epoch ? T - 1 : s1 - 1;
-            const double dn = data_norm2(P, S, sw);
-            for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
-                const uint32_t i = __ldg(P.addr + b);
-                if ((S.badbits[i >> 5] >> (i & 31u)) & 1u) continue;
-                if ((int)b == S.refcol) continue;
-                const int E = good_exposure(P, b, sw);
-                const double ae = apow(S, E);
-                const double w2 = col_w2(P, b);
-                wg += w2 * ae * ae * dn;
-                if (final_epoch) {
-                    if (qubit) {
-                        const double an = apow(S, 2 * n);
-                        double al = 1.0;
-                        for (int q = 0; q < P.k; ++q) al *= 0.5 * (1.0 + an);
-                        og += w2 * ae * al;
-                    } else {
-                        og += w2 * ae;
-                    }
-                }
-            }
-        }
         if (uni) {
             // fold the histograms (and leave them zero for the next epoch)
             __syncthreads();
@@ -1135,9 +1293,32 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             }
         }
         block_sum3(wsum, wempty, ovl, S);
-        if (uni) { wsum *= w2u; wempty *= w2u; ovl *= w2u; }
-        double wgs = wg, ogs = og, dummy = 0.0;
-        block_sum3(wgs, ogs, dummy, S);
+        if (lazy_pre) {
+            // histogram counts are per branch: |c|^2 without the wall factor
+            const double sc = uni ? w2u / k2 : 1.0;
+            wsum *= sc * S.dn; wempty *= sc * S.dn; ovl *= sc * S.al;
+        } else if (uni) {
+            wsum *= w2u; wempty *= w2u; ovl *= w2u;
+        }
+        // good branches of the eager form: closed-form weights before the
+        // first jump (Eq. (18))
+        double wgs = 0.0, ogs = 0.0;
+        if (P.mode == kPruned && !jumped && !lazy) {
+            const int sw = final_epoch ? T - 1 : s1 - 1;
+            for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
+                const uint32_t i = __ldg(P.addr + b);
+                if ((S.badbits[i >> 5] >> (i & 31u)) & 1u) continue;
+                if ((int)b == S.refcol) continue;
+                const double ae = apow(S, good_exposure(P, b, sw));
+                const double w2 = col_w2(P, b);
+                wgs += w2 * ae * ae;
+                if (final_epoch) ogs += w2 * ae;
+            }
+            double dummy = 0.0;
+            block_sum3(wgs, ogs, dummy, S);
+            wgs *= S.dn;
+            ogs *= S.al;
+        }
         const double Wtot = wsum + wgs, Wemp = wempty + wgs;
         if (final_epoch) {
             const double ov_all = ovl + ogs;
@@ -1170,6 +1351,58 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         const double u = uniform53(P.seed, (uint32_t)s1, 2u, traj);
         double tgt = u * Wtot;
         int nsel = 0;
+        if (!(Wemp > tgt) && S.status == QRAM_OK && lazy_pre) {
+            // a jump may fire: give the configurations with a non-empty mask
+            // explicit state (after the gates of s1, K0 through s1 - 1) and
+            // the compact list of (first element, size, weight) the descent reads
+            const uint32_t pos = S.cl2 & P.orbit.occ[s1];
+            const uint32_t ncw = qubit ? (1u << P.k) : 1u;
+            uint32_t base = 0;
+            bool capfail = false;
+            for (uint32_t b0 = 0; b0 < (uint32_t)P.D; b0 += NT) {
+                const uint32_t b = b0 + threadIdx.x;
+                uint32_t cnt = 0, tm = 0, i = 0, j = 0, d = 0;
+                bool all = false;
+                if (b < (uint32_t)P.D) {
+                    i = __ldg(P.addr + b); j = __ldg(P.bus + b); d = __ldg(P.mem + i);
+                    tm = orbit_hits(P, S.candbits, pos, s1, i, j, d, all);
+                    cnt = all ? ncw : (tm ? ncw - (ncw >> __popc(tm)) : 0u);
+                }
+                uint32_t tot;
+                const uint32_t pre = block_scan_count(cnt, &tot, S);
+                if (base + tot > scr.ecap) { capfail = true; break; }
+                uint32_t r = base + pre;
+                const int E0 = cnt ? good_exposure(P, b, s1 - 1) : 0;
+                const double w2 = cnt ? (uni ? w2u : col_w2(P, b) * k2) : 0.0;
+                const Ctx C = make_ctx(P.enc, n, P.mem, i);
+                for (uint32_t cw = 0; cw < ncw; ++cw) {
+                    const bool take = cnt && (all || (cw & tm));
+                    uint32_t c1 = 0, mcnt = 0;
+                    double w = 0.0;
+                    if (take) {
+                        CompR c = orbit_state(P, s1, i, cw, j, d);
+                        c.e = E0 + (qubit ? data_exposure(P, cw, s1 - 1) : 0);
+                        store_comp(scr, cbase + r, c, nullptr, qubit, b, i);
+                        ++r;
+                        c1 = mask_first(c, nullptr, C, S.candbits, S.cl2, mcnt);
+                        const double ae = apow(S, c.e);
+                        w = w2 * ae * ae;
+                    }
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
+                    if (take) {
+                        const uint32_t q = wcur + __popc(bal & ((1u << lane) - 1u));
+                        if (q < scr.selseg) { selk[q] = (c1 & 0xFFFFu) | (mcnt << 16); selw[q] = w; }
+                        else capfail = true;
+                    }
+                    wcur += __popc(bal);
+                }
+                base += tot;
+            }
+            if (lane == 0) S.segn[warp] = min(wcur, scr.selseg);
+            if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
+            if (threadIdx.x == 0) S.ncomp = base;
+            __syncthreads();
+        }
         if (!(Wemp > tgt) && S.status == QRAM_OK) {
             // descent over the canonical order; O = weight before the subtree
             double O = Wemp;
@@ -1297,13 +1530,34 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 for (int j = 0; j < nsel; ++j) S.J[j] = pref[j];
             }
         }
-        if (threadIdx.x == 0) S.nJ = nsel;
+        if (threadIdx.x == 0) {
+            S.nJ = nsel;
+            if (lazy_pre && nsel == 0) S.ncomp = 0;       // no jump: the branches stay implicit
+        }
         __syncthreads();
         if (nsel > 0) {
             if (!jumped) first_jump = (uint32_t)s1;
-            jumped = true;
             ++jumps;
             jump_sites += (uint32_t)nsel;
+            // Relevance after a jump.  Every survivor held all of J on its
+            // address path; an item can only leave that path below a damaged
+            // router and only into that router's subtree, and it can only
+            // leave a subtree through its root.  So all later excitations lie
+            // on the path to r = LCA(J, earlier roots) or inside subtree(r):
+            // candidates elsewhere leave J empty and need no draw.
+            if (threadIdx.x == 0) {
+                uint32_t r = jumped ? S.region : (S.J[0] >> 2);
+                for (int q = 0; q < nsel; ++q) r = tree_lca(r, S.J[q] >> 2);
+                S.region = r;
+                S.syncmask[4] = S.syncmask[5] = S.syncmask[6] = S.syncmask[7] = 0;
+            }
+            jumped = true;
+            __syncthreads();
+            const uint32_t r = S.region;
+            for (uint32_t c = S.slice_off[s1 + 1] + threadIdx.x; c < S.slice_off[T]; c += NT) {
+                const uint32_t u = (cand[c] & 0xFFFFu) >> 1, sc = cand[c] >> 16;
+                if (tree_related(u, r)) atomicOr(&S.syncmask[4 + (sc >> 5)], 1u << (sc & 31u));
+            }
         }
         // clear the candidate bitmap of s1
         for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {

@@ -115,6 +115,7 @@ extern "C" int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k,
     std::memset(&P, 0, sizeof(P));
     if (build_ops(n, k, P.ops) != QRAM_OK) return QRAM_E_ARG;
     build_occupancy(n, k, P.ops, P.occ2);
+    build_orbit(n, k, P.ops, &P.orbit);
     P.enc = encoding; P.n = n; P.k = k; P.T = 6 * n + 2 * k; P.D = num_branches;
     P.nodes = (1 << n) - 1; P.M = 2 * P.nodes; P.nthreads = threads; P.hist_pad = hist_pad(n, k);
     P.mem = memory; P.addr = addr; P.bus = bus; P.amp_re = amp_re; P.amp_im = amp_im;
