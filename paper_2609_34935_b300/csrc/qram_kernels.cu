@@ -102,6 +102,21 @@ __device__ void bad_range(int enc, int n, uint32_t v, uint32_t &lo, uint32_t &hi
     hi = (p + 1u) << (n - l);
 }
 
+// set (or clear) the addresses under node v in a bitmap over addresses
+__device__ __forceinline__ void mark_leaves(uint32_t *bits, int n, uint32_t v, bool set) {
+    const int l = layer_of(v);
+    const uint32_t p = v - ((1u << l) - 1u);
+    uint32_t lo = p << (n - l);
+    const uint32_t hi = (p + 1u) << (n - l);
+    while (lo < hi) {
+        const uint32_t wd = lo >> 5, b0 = lo & 31u;
+        const uint32_t nb = min(32u - b0, hi - lo);
+        const uint32_t m = nb == 32u ? 0xFFFFFFFFu : (((1u << nb) - 1u) << b0);
+        if (set) atomicOr(&bits[wd], m); else atomicAnd(&bits[wd], ~m);
+        lo += nb;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // block reductions (fixed order: deterministic for a given block size)
 __device__ __forceinline__ double warp_sum(double x) {
@@ -133,6 +148,10 @@ struct Smem {
     double sA, sB, sC;
     double dn, al, qt[kMaxK];      // per-epoch data factors (qubit): norm^2, final overlap, 1/(1 + a^(2 m_t))
     uint32_t region;               // after a jump: root of the subtree that can hold excitations
+    uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
+    int16_t etab[4][16];           // lazy epochs: address exposure by nibble of the address
+    int16_t dtab[4][16];           // qutrit: data exposure by nibble of j (0, 1) and of j ^ d (2, 3)
+    int32_t econst;                // qutrit: exposure of the routers (every address bit is excited)
 };
 
 // Block sums of doubles.  FP64 issue is scarce on this part (about two
@@ -852,7 +871,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         return;
     }
     if (threadIdx.x == 0) { S.status = valid ? QRAM_OK : QRAM_E_ARG; S.refcol = -1; S.nbad = 0; S.nJ = 0; }
-    for (int w = threadIdx.x; w < 512; w += NT) S.badbits[w] = 0;
+    for (int w = threadIdx.x; w < 512; w += NT) { S.badbits[w] = 0; S.hitbits[w] = 0; }
     for (int w = threadIdx.x; w < 1024; w += NT) S.candbits[w] = 0;
     __syncthreads();
 
@@ -1095,12 +1114,42 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             S.dn = dn;
             S.al = al;
         }
+        if (lazy && !jumped && threadIdx.x < 128) {
+            // exposure tables of the closed form (Eq. (12); Prop. 1 for the
+            // qutrit data slots) after damping slices 1..sw
+            const int sw = final_epoch ? T - 1 : s1 - 1;
+            const int g = (threadIdx.x >> 4) & 3, v = threadIdx.x & 15;
+            int e = 0;
+            if (threadIdx.x < 64) {
+                if (qubit)                                           // a qubit router is excited when its bit is 1
+                    for (int q = 0; q < 4; ++q) {
+                        const int p = 4 * g + q, l = n - 1 - p;      // address bit p is routed at layer l
+                        if (p < n && ((v >> q) & 1)) e += ov(2 * l + 1, T - 2 * l - 2, sw);
+                    }
+                S.etab[g][v] = (int16_t)e;
+            } else if (!qubit) {
+                for (int q = 0; q < 4; ++q) {
+                    const int t = 4 * (g & 1) + q;
+                    if (t >= P.k || !((v >> q) & 1)) continue;
+                    const int tin = 2 * n + 2 * t + 1, tf = 3 * n + 2 * t + 1, tout = 4 * n + 2 * t + 1;
+                    e += g < 2 ? ov(tin, tf - 1, sw) : ov(tf, tout - 1, sw);
+                }
+                S.dtab[g][v] = (int16_t)e;
+            }
+            if (threadIdx.x == 64) {
+                int c = 0;
+                if (!qubit) for (int l = 0; l < n; ++l) c += ov(2 * l + 1, T - 2 * l - 2, sw);
+                S.econst = c;
+            }
+        }
         __syncthreads();
         if (!final_epoch) {
             for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {
                 const uint32_t site = cand[c] & 0xFFFFu;
+                const int b = 2 * layer_of(site >> 1) + (int)(site & 1u);
                 atomicOr(&S.candbits[site >> 5], 1u << (site & 31u));
-                atomicOr(&S.cl2, 1u << (2 * layer_of(site >> 1) + (int)(site & 1u)));
+                atomicOr(&S.cl2, 1u << b);
+                if (lazy && !jumped && ((P.orbit.occ[s1] >> b) & 1u)) mark_leaves(S.hitbits, n, site >> 1, true);
             }
         }
         __syncthreads();
@@ -1122,10 +1171,19 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             const uint32_t pos = final_epoch ? 0u : (S.cl2 & P.orbit.occ[s1]);
             for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
                 const uint32_t i = __ldg(P.addr + b);
-                const int E = good_exposure(P, b, sw);
+                int E = S.etab[0][i & 15u] + S.etab[1][(i >> 4) & 15u] + S.etab[2][(i >> 8) & 15u] +
+                        S.etab[3][(i >> 12) & 15u];
+                const bool hit = pos && ((S.hitbits[i >> 5] >> (i & 31u)) & 1u);
+                uint32_t j = 0, d = 0;
+                if (!qubit || hit) { j = __ldg(P.bus + b); d = __ldg(P.mem + i); }
+                if (!qubit) {
+                    const uint32_t x = j ^ d;
+                    E += S.econst + S.dtab[0][j & 15u] + S.dtab[1][(j >> 4) & 15u] + S.dtab[2][x & 15u] +
+                         S.dtab[3][(x >> 4) & 15u];
+                }
                 bool all = false;
                 uint32_t tm = 0;
-                if (pos) tm = orbit_hits(P, S.candbits, pos, s1, i, __ldg(P.bus + b), __ldg(P.mem + i), all);
+                if (hit) tm = orbit_hits(P, S.candbits, pos, s1, i, j, d, all);
                 double qp = 1.0;
                 for (uint32_t x = tm; x; x &= x - 1u) qp *= S.qt[__ffs(x) - 1];
                 if (uni) {
@@ -1365,7 +1423,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 bool all = false;
                 if (b < (uint32_t)P.D) {
                     i = __ldg(P.addr + b); j = __ldg(P.bus + b); d = __ldg(P.mem + i);
-                    tm = orbit_hits(P, S.candbits, pos, s1, i, j, d, all);
+                    if ((S.hitbits[i >> 5] >> (i & 31u)) & 1u) tm = orbit_hits(P, S.candbits, pos, s1, i, j, d, all);
                     cnt = all ? ncw : (tm ? ncw - (ncw >> __popc(tm)) : 0u);
                 }
                 uint32_t tot;
@@ -1559,10 +1617,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 if (tree_related(u, r)) atomicOr(&S.syncmask[4 + (sc >> 5)], 1u << (sc & 31u));
             }
         }
-        // clear the candidate bitmap of s1
+        // clear the candidate bitmaps of s1
         for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {
             const uint32_t site = cand[c] & 0xFFFFu;
             atomicAnd(&S.candbits[site >> 5], ~(1u << (site & 31u)));
+            if (lazy_pre) mark_leaves(S.hitbits, n, site >> 1, false);
         }
         __syncthreads();
         s_prev = s1;
