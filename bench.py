@@ -189,7 +189,11 @@ def main():
     ap.add_argument("--full-per-batch", type=int, default=20, help="full-mode trajectories per gamma batch")
     ap.add_argument("--serving", action="store_true", help="run the serving-stream benchmark instead")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--profile-case", type=float, default=None, metavar="GAMMA",
+                    help="one launch of 296 trajectories (148 CTAs of 512 threads) at this gamma, for ncu")
     args = ap.parse_args()
+    if args.profile_case is not None:
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     if args.serving:
@@ -371,6 +375,25 @@ def main():
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_profile_case(gamma: float):
+    """Small case of the bench kernel for a profiler capture: the bench
+    problem, one launch, one CTA per SM, two trajectories per CTA."""
+    import torch
+    from paper_2609_34935_b300 import QramSim
+    sim = QramSim(_problem(), seed=SEED, device=0)
+    sim.set_variant(512)
+    sim.set_launch_ctas(148)
+    sim.set_gamma_bound(G_HI)
+    g = torch.full((296,), gamma, dtype=torch.float64, device="cuda:0")
+    raw = sim.run_pruned(0, g)
+    torch.cuda.synchronize()
+    r = sim.results(raw)
+    print(json.dumps({"profile_case": gamma, "status_max": int(r["status"].max()),
+                      "mean_fidelity": float(r["fidelity"].mean()), "jumps": float(r["jumps"].mean())}))
+    sim.close()
+    return 0
 
 
 def run_serving(args):

@@ -575,9 +575,208 @@ __device__ __forceinline__ bool fast_slice(const SliceOps &op, CompR &c, const C
     return true;
 }
 
+// ---- register generic path: path A as bits, a few other sites in registers --
+// The same gate semantics as slow_slice for a component whose excitations off
+// its address path (path B and the off-path list together) fit in kHX
+// registers: path A follows the fast path's bit operations, the other sites
+// form an unsorted list with compile-time indices (so it stays in registers),
+// and a router of path A that points away from A exchanges its data slot with
+// that list.  Returns *okp = 0, leaving c and xs untouched, when the list
+// would overflow.
+constexpr int kHX = 8;
+
+struct HX {
+    uint32_t v[kHX];     // site << 2 | level (1: excited / L, 2: R); 0 = empty
+};
+
+__device__ __forceinline__ int hx_get(const HX &X, uint32_t site) {
+    int l = 0;
+#pragma unroll
+    for (int q = 0; q < kHX; ++q)
+        if (X.v[q] != 0u && (X.v[q] >> 2) == site) l = (int)(X.v[q] & 3u);
+    return l;
+}
+
+// set the level of a site (0 removes it); false if the list is full
+__device__ __forceinline__ bool hx_set(HX &X, uint32_t site, int lvl) {
+    bool done = false;
+#pragma unroll
+    for (int q = 0; q < kHX; ++q)
+        if (!done && X.v[q] != 0u && (X.v[q] >> 2) == site) {
+            X.v[q] = lvl ? ((site << 2) | (uint32_t)lvl) : 0u;
+            done = true;
+        }
+    if (done || lvl == 0) return true;
+#pragma unroll
+    for (int q = 0; q < kHX; ++q)
+        if (!done && X.v[q] == 0u) { X.v[q] = (site << 2) | (uint32_t)lvl; done = true; }
+    return done;
+}
+
+__device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t *xs, const Ctx C, int *okp) {
+    *okp = 0;
+    const bool qubit = C.enc == QRAM_QUBIT;
+    const int n = C.n;
+    if (__popc(c.pwB) + (int)c.nexc > kHX) return c;
+    HX X;
+#pragma unroll
+    for (int q = 0; q < kHX; ++q) X.v[q] = 0u;
+    {
+        const uint32_t iB = b_addr(c, C);
+        for (uint32_t w = c.pwB; w; w &= w - 1u) {
+            const int b = __ffs(w) - 1;
+            hx_set(X, 2u * path_node(iB, n, b >> 1) + (uint32_t)(b & 1), 1);
+        }
+        for (uint32_t q = 0; q < c.nexc; ++q) hx_set(X, xs[q] >> 1, (xs[q] & 1u) ? 2 : 1);
+    }
+    uint32_t pw = c.pw, pwR = c.pwR, cb = c.cb, sign = c.sign;
+    // load / bus act on d_0, which is on path A (as in fast_slice)
+    if (op.load >= 0) {
+        const uint32_t b = routed_bit(C.i, n, op.load);
+        if (qubit) pw ^= b << 1;
+        else {
+            const uint32_t e0 = (pw >> 1) & 1u, r0 = (pwR >> 1) & 1u;
+            if (!e0) { pw |= 2u; pwR = (pwR & ~2u) | (b << 1); }
+            else if (r0 == b) { pw &= ~2u; pwR &= ~2u; }
+        }
+    }
+    if (op.bus >= 0) {
+        const uint32_t e0 = (pw >> 1) & 1u, r0 = (pwR >> 1) & 1u;
+        const uint32_t b = (cb >> op.bus) & 1u;
+        if (qubit) {
+            pw = (pw & ~2u) | (b << 1);
+            cb = (cb & ~(1u << op.bus)) | (e0 << op.bus);
+        } else if (!(e0 && !r0)) {
+            pw = (pw & ~2u) | (b << 1);
+            pwR = (pwR & ~2u) | (b << 1);
+            cb = (cb & ~(1u << op.bus)) | (e0 << op.bus);
+        }
+    }
+    if (op.iswap) {
+        uint32_t t = (pw ^ (pw >> 1)) & op.iswap2;
+        pw ^= t | (t << 1);
+        t = (pwR ^ (pwR >> 1)) & op.iswap2;
+        pwR ^= t | (t << 1);
+#pragma unroll
+        for (int q = 0; q < kHX; ++q)
+            if (X.v[q] != 0u && ((op.iswap >> layer_of(X.v[q] >> 3)) & 1u)) X.v[q] ^= 4u;   // router <-> data
+    }
+    if (op.cswap) {
+        // routers do not move: read them before moving data
+        HX Y = X;
+#pragma unroll
+        for (int q = 0; q < kHX; ++q) {
+            const uint32_t e = X.v[q], site = e >> 2, u = site >> 1;
+            if (e == 0u || !(site & 1u)) continue;
+            const int L = layer_of(u);
+            if (((op.cswap >> L) & 1u) && L + 1 < n && u != path_node(C.i, n, L)) {
+                const int r = hx_get(X, 2u * u);
+                if (!qubit && r == 0) continue;
+                const uint32_t child = qubit ? 2u * u + 1u + (uint32_t)r : 2u * u + (uint32_t)r;
+                Y.v[q] = ((2u * child + 1u) << 2) | (e & 3u);
+            } else if (L >= 1 && ((op.cswap >> (L - 1)) & 1u)) {
+                const uint32_t par = (u - 1u) >> 1;
+                if (par == path_node(C.i, n, L - 1)) continue;           // exchange with path A below
+                const int r = hx_get(X, 2u * par);
+                if (!qubit && r == 0) continue;
+                const uint32_t child = qubit ? 2u * par + 1u + (uint32_t)r : 2u * par + (uint32_t)r;
+                if (child == u) Y.v[q] = ((2u * par + 1u) << 2) | (e & 3u);
+            }
+        }
+        X = Y;
+        for (uint32_t m = op.cswap; m; m &= m - 1u) {
+            const int L = __ffs(m) - 1;
+            if (L + 1 >= n) continue;
+            const uint32_t uA = path_node(C.i, n, L);
+            const uint32_t re = (pw >> (2 * L)) & 1u, rR = (pwR >> (2 * L)) & 1u;
+            int r;                                    // router level of A's node
+            if (qubit) r = (int)re;
+            else { r = re ? (rR ? 2 : 1) : 0; if (r == 0) continue; }
+            const uint32_t child = qubit ? 2u * uA + 1u + (uint32_t)r : 2u * uA + (uint32_t)r;
+            const int bA = 2 * L + 1, bC = 2 * L + 3;
+            if (child == path_node(C.i, n, L + 1)) {   // aligned: data moves along A
+                uint32_t t = ((pw >> bA) ^ (pw >> bC)) & 1u;
+                pw ^= (t << bA) | (t << bC);
+                t = ((pwR >> bA) ^ (pwR >> bC)) & 1u;
+                pwR ^= (t << bA) | (t << bC);
+            } else {                                  // A's data slot <-> the other child's
+                const int lo = hx_get(X, 2u * child + 1u);
+                const uint32_t ea = (pw >> bA) & 1u, ra = (pwR >> bA) & 1u;
+                const int la = ea ? (ra ? 2 : 1) : 0;
+                if (!hx_set(X, 2u * child + 1u, la)) return c;
+                pw = (pw & ~(1u << bA)) | ((lo ? 1u : 0u) << bA);
+                pwR = (pwR & ~(1u << bA)) | ((lo == 2 ? 1u : 0u) << bA);
+            }
+        }
+    }
+    if (op.fetch >= 0) {
+        const int L = n - 1;
+        const uint32_t lo = (1u << L) - 1u;
+        const uint32_t re = (pw >> (2 * L)) & 1u, de = (pw >> (2 * L + 1)) & 1u;
+        if (qubit) {
+            if (de) {
+                const uint32_t cell = ((C.i >> 1) << 1) | re;
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) sign ^= 1u;
+            }
+#pragma unroll
+            for (int q = 0; q < kHX; ++q) {
+                const uint32_t e = X.v[q], site = e >> 2, u = site >> 1;
+                if (e == 0u || !(site & 1u) || layer_of(u) != L) continue;
+                const uint32_t cell = 2u * (u - lo) + (uint32_t)hx_get(X, 2u * u);
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) sign ^= 1u;
+            }
+        } else {
+            if (re) {
+                const uint32_t cell = ((C.i >> 1) << 1) | ((pwR >> (2 * L)) & 1u);
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) {
+                    const uint32_t dR = (pwR >> (2 * L + 1)) & 1u;
+                    const uint32_t bit = 1u << (2 * L + 1);
+                    if (!de) { pw |= bit; pwR |= bit; }
+                    else if (dR) { pw &= ~bit; pwR &= ~bit; }
+                }
+            }
+            uint32_t flip[kHX];
+#pragma unroll
+            for (int q = 0; q < kHX; ++q) {
+                const uint32_t e = X.v[q], site = e >> 2, u = site >> 1;
+                flip[q] = 0u;
+                if (e == 0u || (site & 1u) || layer_of(u) != L) continue;
+                const uint32_t cell = 2u * (u - lo) + ((e & 3u) == 2u ? 1u : 0u);
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) flip[q] = 2u * u + 2u;   // data site + 1
+            }
+#pragma unroll
+            for (int q = 0; q < kHX; ++q) {
+                if (!flip[q]) continue;
+                const uint32_t ds = flip[q] - 1u;
+                const int d = hx_get(X, ds);
+                if (!hx_set(X, ds, d == 0 ? 2 : (d == 2 ? 0 : d))) return c;
+            }
+        }
+    }
+    // sorted off-path list (insertion into xs in site order)
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int q = 0; q < kHX; ++q) cnt += X.v[q] != 0u ? 1u : 0u;
+    uint32_t prev = 0u;
+    for (uint32_t k = 0; k < cnt; ++k) {
+        uint32_t best = 0xFFFFFFFFu;
+#pragma unroll
+        for (int q = 0; q < kHX; ++q)
+            if (X.v[q] != 0u && X.v[q] > prev && X.v[q] < best) best = X.v[q];
+        const uint32_t site = best >> 2;
+        xs[k] = (uint16_t)((site << 1) | ((best & 3u) == 2u ? 1u : 0u));
+        prev = best;
+    }
+    c.pw = pw; c.pwR = qubit ? 0u : pwR; c.pwB = 0u; c.ldiv = -1; c.nexc = cnt; c.cb = cb; c.sign = sign;
+    *okp = 1;
+    return c;
+}
+
 __device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16_t *xs, const Ctx &C) {
     if (fast_slice(op, c, C)) return true;
     int okv;
+    const CompR h = hybrid_slice(op, c, xs, C, &okv);
+    if (okv) { c = h; return true; }
     c = slow_slice(op, c, xs, C, &okv);
     return okv != 0;
 }
