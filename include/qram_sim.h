@@ -16,12 +16,17 @@
  *   - Schedule: T = 6n + 2k slices; slices 1 .. T-1 carry gates, each
  *     followed by one joint damping layer over all M sites (Sec. II.B).
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed
- *     and counter (node or 0, slice | stream << 24, traj_lo, traj_hi);
- *     stream 1 draws the candidate set of Theorem 3 (router site from words
- *     0-1, data site from words 2-3, candidate iff the 64-bit word is below
- *     floor(gamma 2^64)), stream 2 the auxiliary draw of each damping layer,
- *     stream 3 the final tree measurement.  A trajectory is a pure function
- *     of (seed, trajectory index, gamma).
+ *     and counter (c0, c1 | stream << 24, traj_lo, traj_hi).  Stream 1
+ *     draws the candidate set of Theorem 3 (sampler version 2): every
+ *     (slice, site) pair is a candidate independently with probability
+ *     gamma; the pairs, numbered (slice - 1) * M + site, are cut into blocks
+ *     of 2048 and the candidates of block g follow from geometric gaps, draw
+ *     r being the 64-bit word (0,1) or (2,3) of counter (g, r / 2) and its
+ *     gap the greedy 13-bit inverse of 64-bit fixed-point powers of
+ *     1 - gamma (q_0 = 2^64 - floor(gamma 2^64), q_{m+1} = q_m^2 / 2^64,
+ *     floored).  Stream 2 (c0 = 0, c1 = slice) is the auxiliary draw of each
+ *     damping layer, stream 3 (c0 = c1 = 0) the final tree measurement.  A
+ *     trajectory is a pure function of (seed, trajectory index, gamma).
  *   - Memory: "host" pointers are read during the call only; "device"
  *     pointers are CUDA global memory owned by the caller.  The library
  *     owns only its scratch, allocated on the device of the simulator.
@@ -41,6 +46,9 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* candidate sampler implemented by this library (see "Random numbers") */
+#define QRAM_SAMPLER_VERSION 2
 
 enum {
     QRAM_OK = 0,
@@ -68,7 +76,7 @@ typedef struct {
     const double *amp_re;      /* host, D; sum |amp|^2 = 1 within 1e-12 */
     const double *amp_im;      /* host, D */
     uint64_t seed;             /* Philox key */
-    uint32_t sampler_version;  /* must be 1 (per-node Philox candidate draw) */
+    uint32_t sampler_version;  /* must be QRAM_SAMPLER_VERSION (geometric-gap candidate draw) */
 } qram_problem_t;
 
 /* Per-trajectory result, written by qram_run_pruned / qram_run_full. */

@@ -69,6 +69,8 @@ def lib():
         L.oracle_philox.restype = None
         L.oracle_threshold.argtypes = [f64]
         L.oracle_threshold.restype = u64
+        L.oracle_gap.argtypes = [u64, f64]
+        L.oracle_gap.restype = C.c_uint32
         L.oracle_maxe.restype = i32
         _lib = L
     return _lib
@@ -282,6 +284,12 @@ def philox(ctr, seed: int):
     o = np.zeros(4, np.uint32)
     lib().oracle_philox(_ptr(c), seed, _ptr(o))
     return [int(x) for x in o]
+
+
+def gap(u: int, gamma: float) -> int:
+    """Geometric gap of a 64-bit uniform word: non-candidate sites before the
+    next candidate (the fault stream of the random-number convention)."""
+    return int(lib().oracle_gap(int(u), float(gamma)))
 
 
 def threshold(gamma: float) -> int:

@@ -46,11 +46,21 @@
  *      the leaf data slot of a node whose router is L/R when the routed
  *      memory bit is 1.
  *   S4 random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
- *      counter = (node or 0, slice | stream << 24, traj_lo, traj_hi) with
- *      streams FAULT=1, AUX=2, FINAL=3.  FAULT: words (0,1) decide the
- *      router site, words (2,3) the data site; candidate iff the 64-bit word
- *      is below floor(gamma * 2^64).  AUX/FINAL: u = (w >> 11) * 2^-53 with
- *      w = word0 | word1 << 32.
+ *      counter = (c0, c1 | stream << 24, traj_lo, traj_hi) with streams
+ *      FAULT=1, AUX=2, FINAL=3.  AUX/FINAL: c0 = 0, c1 = slice (0 for FINAL),
+ *      u = (w >> 11) * 2^-53 with w = word0 | word1 << 32.
+ *      FAULT: every (slice, site) pair is a candidate independently with
+ *      probability gamma.  The pairs are numbered x = (slice - 1) * M + site
+ *      (M = 2 * nodes) and cut into blocks of 2048; inside block g the
+ *      candidates follow from geometric gaps.  Draw r of block g is the
+ *      64-bit word (0,1) (r even) or (2,3) (r odd) of the counter
+ *      (g, r / 2, ...).  With thr = floor(gamma * 2^64), q_0 = 2^64 - thr
+ *      and q_{m+1} = floor(q_m^2 / 2^64) (64-bit fixed-point powers of
+ *      1 - gamma), the gap of a word u is built greedily from m = 12 down
+ *      to 0: starting from acc = 2^64 - 1, j gains 2^m whenever
+ *      floor(acc * q_m / 2^64) > u (and acc takes that value); so
+ *      P(gap >= j) = (1 - gamma)^j up to 64-bit rounding.  A gap that
+ *      reaches the block end ends the block.  gamma with thr = 0 draws none.
  *   S5 canonical mask order: the empty mask first, then masks as sorted
  *      lists of (site, level) compared lexicographically, a proper prefix
  *      first; the selected J is the first mask whose cumulative weight
@@ -592,6 +602,37 @@ void oracle_bad_range(int encoding, int n, uint32_t v, uint32_t *lo, uint32_t *h
     oracle_bad_range(encoding, n, par, lo, hi);
 }
 
+/* geometric gap of a 64-bit uniform word (S4) */
+#define OR_GAP_BLOCK 2048u
+#define OR_GAP_BITS 13
+static uint64_t umulhi64(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
+
+static void gap_powers(uint64_t thr, uint64_t q[OR_GAP_BITS])
+{
+    q[0] = (uint64_t)0 - thr;                       /* 2^64 - thr, thr >= 1 */
+    for (int m = 0; m + 1 < OR_GAP_BITS; m++) q[m + 1] = umulhi64(q[m], q[m]);
+}
+
+static uint32_t gap_of(uint64_t u, const uint64_t q[OR_GAP_BITS])
+{
+    uint64_t acc = ~(uint64_t)0;
+    uint32_t j = 0;
+    for (int m = OR_GAP_BITS - 1; m >= 0; m--) {
+        uint64_t t = umulhi64(acc, q[m]);
+        if (t > u) { acc = t; j += 1u << m; }
+    }
+    return j;
+}
+
+uint32_t oracle_gap(uint64_t u, double gamma)
+{
+    uint64_t q[OR_GAP_BITS];
+    uint64_t thr = oracle_threshold(gamma);
+    if (thr == 0) return 0xFFFFFFFFu;
+    gap_powers(thr, q);
+    return gap_of(u, q);
+}
+
 /* candidates of one trajectory in (slice, site) order; returns count */
 static int sample_candidates(const osched *S, uint64_t seed, uint64_t traj, double gamma,
                              int32_t **cs, int32_t **cq, int *nc_out)
@@ -600,25 +641,30 @@ static int sample_candidates(const osched *S, uint64_t seed, uint64_t traj, doub
     int cap = 256, nc = 0;
     int32_t *a = malloc(cap * sizeof(int32_t)), *b = malloc(cap * sizeof(int32_t));
     if (!a || !b) { free(a); free(b); return OR_E_OOM; }
-    uint32_t nodes = (1u << S->n) - 1;
-    for (int s = 1; s < S->T; s++)
-        for (uint32_t v = 0; v < nodes; v++) {
-            uint32_t o[4];
-            draw(seed, v, (uint32_t)s, 1u, traj, o);
-            uint64_t ur = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
-            uint64_t ud = (uint64_t)o[2] | ((uint64_t)o[3] << 32);
-            for (int slot = 0; slot < 2; slot++) {
-                if ((slot ? ud : ur) < thr) {
-                    if (nc == cap) {
-                        cap *= 2;
-                        int32_t *a2 = realloc(a, cap * sizeof(int32_t)), *b2 = realloc(b, cap * sizeof(int32_t));
-                        if (!a2 || !b2) { free(a2 ? a2 : a); free(b2 ? b2 : b); return OR_E_OOM; }
-                        a = a2; b = b2;
-                    }
-                    a[nc] = s; b[nc] = (int32_t)(2 * v + slot); nc++;
-                }
+    *cs = a; *cq = b; *nc_out = 0;
+    if (thr == 0) return 0;
+    uint64_t q[OR_GAP_BITS];
+    gap_powers(thr, q);
+    const uint64_t M = 2 * (((uint64_t)1 << S->n) - 1), X = (uint64_t)(S->T - 1) * M;
+    for (uint64_t g = 0; g * OR_GAP_BLOCK < X; g++) {
+        uint64_t pos = g * OR_GAP_BLOCK, end = pos + OR_GAP_BLOCK < X ? pos + OR_GAP_BLOCK : X;
+        uint32_t o[4] = {0, 0, 0, 0};
+        for (uint32_t r = 0;; r++) {
+            if ((r & 1u) == 0) draw(seed, (uint32_t)g, r >> 1, 1u, traj, o);
+            uint64_t u = (r & 1u) ? ((uint64_t)o[2] | ((uint64_t)o[3] << 32)) : ((uint64_t)o[0] | ((uint64_t)o[1] << 32));
+            uint32_t G = gap_of(u, q);
+            if ((uint64_t)G >= end - pos) break;
+            pos += G;
+            if (nc == cap) {
+                cap *= 2;
+                int32_t *a2 = realloc(a, cap * sizeof(int32_t)), *b2 = realloc(b, cap * sizeof(int32_t));
+                if (!a2 || !b2) { free(a2 ? a2 : a); free(b2 ? b2 : b); return OR_E_OOM; }
+                a = a2; b = b2;
             }
+            a[nc] = (int32_t)(1 + pos / M); b[nc] = (int32_t)(pos % M); nc++;
+            pos += 1;
         }
+    }
     *cs = a; *cq = b; *nc_out = nc;
     return 0;
 }

@@ -35,6 +35,9 @@ class QramError(RuntimeError):
         self.code = code
 
 
+SAMPLER_VERSION = 2          # candidate sampler of the library (geometric gaps)
+
+
 class _Problem(C.Structure):
     _fields_ = [("encoding", C.c_int32), ("n", C.c_int32), ("k", C.c_int32), ("memory", C.c_void_p),
                 ("num_branches", C.c_int32), ("addr", C.c_void_p), ("bus", C.c_void_p),
@@ -142,7 +145,7 @@ class QramSim:
         re = np.ascontiguousarray(amp.real)
         im = np.ascontiguousarray(amp.imag)
         p = _Problem(self.encoding, self.n, self.k, mem.ctypes.data, len(addr), addr.ctypes.data,
-                     bus.ctypes.data, re.ctypes.data, im.ctypes.data, int(seed) & (2 ** 64 - 1), 1)
+                     bus.ctypes.data, re.ctypes.data, im.ctypes.data, int(seed) & (2 ** 64 - 1), SAMPLER_VERSION)
         h = C.c_void_p()
         _check(self.lib.qram_sim_create(C.byref(p), device, self.stream.cuda_stream, C.byref(h)), "qram_sim_create")
         self.h = h
@@ -339,7 +342,7 @@ class QramServer:
         keep += [mem, addr, bus, re, im, g]
         p = _Problem(int(problem.encoding), int(problem.n), int(problem.k), mem.ctypes.data, len(addr),
                      addr.ctypes.data, bus.ctypes.data, re.ctypes.data, im.ctypes.data,
-                     int(seed) & (2 ** 64 - 1), 1)
+                     int(seed) & (2 ** 64 - 1), SAMPLER_VERSION)
         return _Request(p, int(traj0), len(g), g.ctypes.data, int(mode)), keep
 
     def submit(self, problem, seed: int, traj0: int, gammas, mode: int = 0) -> int:

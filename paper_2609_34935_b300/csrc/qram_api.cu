@@ -134,16 +134,19 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 // per-slot candidate capacities for a damping-rate bound gmax: mean + 12 sigma
 void cand_caps(int n, int k, double gmax, int threads, uint32_t *cand_cap, uint32_t *seg_cap) {
     const int NWARP = threads / 32;
-    const double items = (double)(6 * n + 2 * k - 1) * (double)((1u << n) - 1);
-    const double per = std::ceil(items / NWARP);
+    // fault sites: (slice, site) pairs; a warp takes a contiguous run of
+    // blocks of kGapBlock pairs
+    const double sites = (double)(6 * n + 2 * k - 1) * 2.0 * (double)((1u << n) - 1);
+    const double nblk = std::ceil(sites / kGapBlock);
+    const double per = std::min(sites, std::ceil(nblk / NWARP) * kGapBlock);
     auto cap = [&](double m) {
         const double p = std::min(1.0, std::max(gmax, 0.0));
-        const double mean = 2.0 * m * p, sd = std::sqrt(2.0 * m * p * (1.0 - p) + 1.0);
+        const double mean = m * p, sd = std::sqrt(m * p * (1.0 - p) + 1.0);
         double c = mean + 12.0 * sd + 64.0;
-        c = std::min(c, 2.0 * m + 64.0);
+        c = std::min(c, m + 64.0);
         return (uint32_t)(std::ceil(c / 32.0) * 32.0);
     };
-    *cand_cap = cap(items);
+    *cand_cap = cap(sites);
     *seg_cap = cap(per);
 }
 
@@ -414,7 +417,7 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     *out = nullptr;
     if (p->encoding != QRAM_QUTRIT && p->encoding != QRAM_QUBIT) return QRAM_E_ARG;
     if (p->n < 1 || p->n > kMaxN || p->k < 1 || p->k > kMaxK || p->k > p->n) return QRAM_E_ARG;
-    if (p->sampler_version != 1) return QRAM_E_ARG;
+    if (p->sampler_version != QRAM_SAMPLER_VERSION) return QRAM_E_ARG;
     const uint32_t N = 1u << p->n;
     if (p->num_branches < 1 || (uint32_t)p->num_branches > N) return QRAM_E_ARG;
     if (!p->memory || !p->addr || !p->bus || !p->amp_re || !p->amp_im) return QRAM_E_ARG;

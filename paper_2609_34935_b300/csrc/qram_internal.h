@@ -13,6 +13,10 @@ constexpr int kMaxK = 8;
 constexpr int kMaxT = 6 * kMaxN + 2 * kMaxK;   // 100
 constexpr int kXcap = 32;                      // off-path excitations per component
 constexpr int kMaxJ = 64;                      // elements of one joint outcome J
+// fault stream: (slice, site) pairs are cut into blocks of kGapBlock, and the
+// geometric gaps inside a block are at most 2^kGapBits - 1
+constexpr uint32_t kGapBlock = 2048;
+constexpr int kGapBits = 13;
 // Damping exponents are bounded by (2n+k)(T-1) (at most 2n+k excited sites
 // per slice); histograms over them need (2n+k)(T-1)+1 <= 3565 bins.
 constexpr int kHistMax = 3584;

@@ -3,10 +3,11 @@
 // One CTA simulates one trajectory at a time and takes the next trajectory
 // index from a global counter (persistent, work-stealing launch).  Per
 // trajectory (Algorithm 1):
-//   1. candidate sampling (Theorem 3 step 1): one Philox4x32-10 call per
-//      (slice, node); each warp scans a contiguous range of (slice, node)
-//      pairs, so concatenating the per-warp segments yields the candidates
-//      in (slice, site) order without a sort;
+//   1. candidate sampling (Theorem 3 step 1): geometric gaps between
+//      candidates over the (slice, site) pairs, one Philox4x32-10 word per
+//      candidate (plus one per block of 2048 pairs); each warp takes a
+//      contiguous run of blocks, so concatenating the per-warp segments
+//      yields the candidates in (slice, site) order without a sort;
 //   2. marking (Algorithm 1 step 1): every candidate marks bad(v), Eq. (7)
 //      for qutrits and Eq. (9) for qubits, into a shared-memory bitmap;
 //   3. explicit set: bad branches + the first good branch (pruned) or every
@@ -148,6 +149,7 @@ struct Smem {
     double sA, sB, sC;
     double dn, al, qt[kMaxK];      // per-epoch data factors (qubit): norm^2, final overlap, 1/(1 + a^(2 m_t))
     uint32_t region;               // after a jump: root of the subtree that can hold excitations
+    uint64_t gq[kGapBits];         // fault stream: 64-bit fixed-point (1 - gamma)^(2^m)
     uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
     int16_t etab[4][16];           // lazy epochs: address exposure by nibble of the address
     int16_t dtab[4][16];           // qutrit: data exposure by nibble of j (0, 1) and of j ^ d (2, 3)
@@ -1090,40 +1092,69 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             cand[c] = v;
         }
     } else if (valid && thr > 0) {
+        // geometric gaps over the (slice, site) pairs in blocks of kGapBlock;
+        // each warp takes a contiguous run of blocks, one block per lane
+        // per round, and writes its candidates in order into its segment
         const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-        const uint32_t total = (uint32_t)(T - 1) * nodes;
-        const uint32_t per = (total + NW - 1) / NW;
-        const uint32_t beg = w * per, end = min(total, beg + per);
+        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+        const uint32_t tl = (uint32_t)traj, th = (uint32_t)(traj >> 32);
+        if (threadIdx.x == 0) {
+            S.gq[0] = 0ull - thr;                                  // 2^64 - thr
+            for (int m = 0; m + 1 < kGapBits; ++m) S.gq[m + 1] = __umul64hi(S.gq[m], S.gq[m]);
+        }
+        __syncthreads();
+        const uint32_t M = 2u * nodes, X = (uint32_t)(T - 1) * M;
+        const uint32_t nblk = (X + kGapBlock - 1) / kGapBlock;
+        const uint32_t per = (nblk + NW - 1) / NW;
+        const uint32_t g0 = w * per, g1 = min(nblk, g0 + per);
         uint32_t *seg = scr.wseg + (slot * NW + w) * scr.seg_cap;
         uint32_t cnt = 0;
         bool overflow = false;
-        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-        const uint32_t tl = (uint32_t)traj, th = (uint32_t)(traj >> 32);
-        // (slice, node) of item beg + lane
-        uint32_t idx = beg + lane;
-        uint32_t s = 1 + idx / nodes, v = idx % nodes;
-        const uint32_t step_s = 32u / nodes, step_v = 32u % nodes;
-        for (uint32_t base = beg; base < end; base += 32) {
-            bool cr = false, cd = false;
-            if (idx < end) {
-                uint32_t c0 = v, c1 = s | (1u << 24), c2 = tl, c3 = th;
-                philox(c0, c1, c2, c3, k0, k1);
-                const uint64_t ur = (uint64_t)c0 | ((uint64_t)c1 << 32);
-                const uint64_t ud = (uint64_t)c2 | ((uint64_t)c3 << 32);
-                cr = ur < thr;
-                cd = ud < thr;
+        for (uint32_t gb = g0; gb < g1; gb += 32) {
+            const uint32_t g = gb + lane;
+            // pass 1 counts this lane's candidates, pass 2 writes them after
+            // those of the lower lanes
+            uint32_t mine = 0, off = 0;
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) {
+                    uint32_t x = mine;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                        if (lane >= (uint32_t)o) x += y;
+                    }
+                    off = cnt + x - mine;
+                    cnt += __shfl_sync(0xFFFFFFFFu, x, 31);
+                    if (mine == 0) continue;
+                }
+                if (g >= g1) continue;
+                uint32_t pos = g * kGapBlock;
+                const uint32_t end = min(pos + kGapBlock, X);
+                uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0, k = 0;
+                for (uint32_t r = 0;; ++r) {
+                    if ((r & 1u) == 0) {
+                        o0 = g; o1 = (r >> 1) | (1u << 24); o2 = tl; o3 = th;
+                        philox(o0, o1, o2, o3, k0, k1);
+                    }
+                    const uint64_t u = (r & 1u) ? ((uint64_t)o2 | ((uint64_t)o3 << 32)) : ((uint64_t)o0 | ((uint64_t)o1 << 32));
+                    uint64_t acc = ~0ull;
+                    uint32_t G = 0;
+#pragma unroll
+                    for (int m = kGapBits - 1; m >= 0; --m) {
+                        const uint64_t t = __umul64hi(acc, S.gq[m]);
+                        if (t > u) { acc = t; G += 1u << m; }
+                    }
+                    if (G >= end - pos) break;
+                    pos += G;
+                    if (pass == 0) ++mine;
+                    else {
+                        const uint32_t q = off + k++;
+                        if (q < scr.seg_cap) seg[q] = ((1u + pos / M) << 16) | (pos % M);
+                        else overflow = true;
+                    }
+                    ++pos;
+                }
             }
-            const uint32_t br = __ballot_sync(0xFFFFFFFFu, cr), bd = __ballot_sync(0xFFFFFFFFu, cd);
-            if (br | bd) {
-                const uint32_t lt = (1u << lane) - 1u;
-                uint32_t pos = cnt + __popc(br & lt) + __popc(bd & lt);
-                if (cr) { if (pos < scr.seg_cap) seg[pos] = (s << 16) | (2u * v); else overflow = true; ++pos; }
-                if (cd) { if (pos < scr.seg_cap) seg[pos] = (s << 16) | (2u * v + 1u); else overflow = true; }
-                cnt += __popc(br) + __popc(bd);
-            }
-            idx += 32;
-            s += step_s; v += step_v;
-            if (v >= nodes) { v -= nodes; ++s; }
         }
         overflow = __any_sync(0xFFFFFFFFu, overflow);
         if (lane == 0) S.wcount[w] = overflow ? 0xFFFFFFFFu : cnt;

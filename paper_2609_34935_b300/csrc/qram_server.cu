@@ -120,7 +120,7 @@ int start(qram_server *S, Req *r) {
     qram_problem_t p;
     p.encoding = r->enc; p.n = r->n; p.k = r->k; p.memory = r->memory.data();
     p.num_branches = r->D; p.addr = r->addr.data(); p.bus = r->bus.data();
-    p.amp_re = r->re.data(); p.amp_im = r->im.data(); p.seed = r->seed; p.sampler_version = 1;
+    p.amp_re = r->re.data(); p.amp_im = r->im.data(); p.seed = r->seed; p.sampler_version = QRAM_SAMPLER_VERSION;
     if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) return QRAM_E_CUDA;
     if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) return QRAM_E_CUDA;
     int rc = qram_sim_create(&p, S->device, r->stream, &r->sim);
@@ -193,7 +193,7 @@ void loop(qram_server *S) {
 bool valid_request(const qram_request_t *q) {
     const qram_problem_t &p = q->problem;
     if (p.encoding != QRAM_QUTRIT && p.encoding != QRAM_QUBIT) return false;
-    if (p.n < 1 || p.n > 14 || p.k < 1 || p.k > 8 || p.k > p.n || p.sampler_version != 1) return false;
+    if (p.n < 1 || p.n > 14 || p.k < 1 || p.k > 8 || p.k > p.n || p.sampler_version != QRAM_SAMPLER_VERSION) return false;
     if (p.num_branches < 1 || p.num_branches > (1 << p.n)) return false;
     if (!p.memory || !p.addr || !p.bus || !p.amp_re || !p.amp_im) return false;
     if (q->ntraj < 1 || !q->gamma || (q->mode != 0 && q->mode != 1)) return false;

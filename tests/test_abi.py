@@ -44,11 +44,11 @@ def test_create_rejects_bad_problems_without_gpu():
     re_ = np.ascontiguousarray(p.amp.real)
     im_ = np.ascontiguousarray(p.amp.imag)
     pr = Q._Problem(1, 3, 4, mem.ctypes.data, len(a), a.ctypes.data, b.ctypes.data, re_.ctypes.data,
-                    im_.ctypes.data, 1, 1)
+                    im_.ctypes.data, 1, Q.SAMPLER_VERSION)
     h = ctypes.c_void_p()
     assert lib.qram_sim_create(ctypes.byref(pr), 0, None, ctypes.byref(h)) == 1
     pr.k = 2
-    pr.sampler_version = 2
+    pr.sampler_version = 1                  # the per-node draw is not implemented
     assert lib.qram_sim_create(ctypes.byref(pr), 0, None, ctypes.byref(h)) == 1
 
 

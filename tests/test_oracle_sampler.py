@@ -1,5 +1,6 @@
 """Oracle pins for the noise sampler and the classifier: Philox4x32-10
-against an independent implementation, the candidate rate, Eq. (7), Eq. (9),
+against an independent implementation, the geometric gaps of the fault
+stream against the inverse CDF, the candidate rate, Eq. (7), Eq. (9),
 Eq. (22), and the probability that an address stays good."""
 import math
 import os
@@ -67,6 +68,43 @@ def test_philox_against_independent_implementation(tmp_path):
 def test_threshold_exact():
     for g in [1e-5, 1e-3, 0.0123, 0.2, 0.5, 2.0 ** -60, 0.0]:
         assert core.threshold(g) == math.floor(Fraction(g) * 2 ** 64)
+
+
+@pytest.mark.parametrize("gamma", [1e-5, 3e-4, 0.01, 0.2, 0.6])
+def test_gap_is_geometric_inverse_cdf(gamma):
+    """The fault stream's gap of a uniform word u is the inverse CDF of the
+    geometric law: the largest j with (1 - gamma)^j > u / 2^64, capped at
+    2^13 - 1.  The fixed-point powers carry an absolute error of a few
+    2^-64 per factor, so the bracket (1-gamma)^(g+1) <= u/2^64 < (1-gamma)^g
+    is checked with an absolute slack of 1e-14 in probability."""
+    rng = np.random.default_rng(int(gamma * 1e6) + 3)
+    words = [int(x) for x in rng.integers(0, 2 ** 64, size=400, dtype=np.uint64)]
+    words += [0, 1, 2 ** 63, 2 ** 64 - 1, 2 ** 64 - 2 ** 20]
+    q = 1.0 - gamma
+    eps = 1e-14
+    for u in words:
+        v = u / 2.0 ** 64
+        g = core.gap(u, gamma)
+        assert q ** g > v - eps, (u, g)
+        if g < 2 ** 13 - 1:
+            assert q ** (g + 1) <= v + eps, (u, g)
+        else:
+            assert q ** g <= 2.0 * (v + eps) or q ** (2 ** 13) < 1e-300 or v < q ** (2 ** 13) + eps
+    # gamma = 1/2, where the powers are exact: acc starts at 2^64 - 1, so the
+    # first boundary sits at floor((2^64 - 1) / 2) = 2^63 - 1
+    for u, want in [(2 ** 63, 0), (2 ** 63 - 1, 0), (2 ** 63 - 2, 1), (2 ** 62 - 1, 1), (2 ** 62 - 2, 2)]:
+        assert core.gap(u, 0.5) == want
+    assert core.gap(12345, 0.0) == 0xFFFFFFFF                # no candidates at all
+
+
+def test_gap_law_small_gamma_mean():
+    """Mean gap over a stream of words against 1/gamma - 1 (truncated law)."""
+    gamma = 0.05
+    rng = np.random.default_rng(9)
+    g = np.array([core.gap(int(u), gamma) for u in rng.integers(0, 2 ** 64, size=20000, dtype=np.uint64)])
+    q = 1 - gamma
+    want = q / gamma                                          # E[G], tail beyond 8191 negligible
+    assert abs(g.mean() - want) < 5 * math.sqrt(q) / gamma / math.sqrt(len(g))
 
 
 def test_candidate_rate_binomial():
