@@ -148,6 +148,9 @@ struct Smem {
     int status;
     double sA, sB, sC;
     double dn, al, qt[kMaxK];      // per-epoch data factors (qubit): norm^2, final overlap, 1/(1 + a^(2 m_t))
+    double fW, fO;                 // per-epoch scale of the weight sums and of the overlap sum
+    double hdat[2 * kMaxN + 1];    // per trajectory: (1 + a^(2m)) / 2 and 1 / (1 + a^(2m)), m <= 2n
+    double rdat[2 * kMaxN + 1];
     uint32_t region;               // after a jump: root of the subtree that can hold excitations
     uint64_t gq[kGapBits];         // fault stream: 64-bit fixed-point (1 - gamma)^(2^m)
     uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
@@ -175,9 +178,10 @@ __device__ double block_sum(double x, double *red, Smem<NT> &S) {
     return S.sA;
 }
 
-// three sums at once
+// three sums at once, each scaled by its factor (applied once, by one thread)
 template <int NT>
-__device__ void block_sum3(double &a, double &b, double &c, Smem<NT> &S) {
+__device__ void block_sum3(double &a, double &b, double &c, Smem<NT> &S, double fa = 1.0, double fb = 1.0,
+                           double fc = 1.0) {
     constexpr int NW = NT / 32;
     a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -188,7 +192,7 @@ __device__ void block_sum3(double &a, double &b, double &c, Smem<NT> &S) {
         const double ra = warp_sum(lane < NW ? S.redA[lane] : 0.0);
         const double rb = warp_sum(lane < NW ? S.redB[lane] : 0.0);
         const double rc = warp_sum(lane < NW ? S.redC[lane] : 0.0);
-        if (lane == 0) { S.sA = ra; S.sB = rb; S.sC = rc; }
+        if (lane == 0) { S.sA = ra * fa; S.sB = rb * fb; S.sC = rc * fc; }
     }
     __syncthreads();
     a = S.sA; b = S.sB; c = S.sC;
@@ -1246,17 +1250,22 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
 
     // ---- 3. explicit set ----------------------------------------------------
     const double a = sqrt(1.0 - (valid ? gamma : 0.0));
-    if (threadIdx.x < 64) {
-        double p = 1.0;
-        for (int j = 0; j < (int)threadIdx.x; ++j) p *= a;
-        S.powlo[threadIdx.x] = p;
+    if (threadIdx.x < 128) {                        // a^j and a^(64 j) by binary powering
+        const int j = (int)threadIdx.x & 63;
+        double x = a, p = 1.0;
+        if (threadIdx.x >= 64) for (int q = 0; q < 6; ++q) x *= x;   // a^64
+        for (int q = 0; q < 6; ++q) {
+            if ((j >> q) & 1) p *= x;
+            x *= x;
+        }
+        if (threadIdx.x < 64) S.powlo[j] = p; else S.powhi[j] = p;
     }
     __syncthreads();
-    if (threadIdx.x < 64) {
-        const double a64 = S.powlo[63] * a;
-        double p = 1.0;
-        for (int j = 0; j < (int)threadIdx.x; ++j) p *= a64;
-        S.powhi[threadIdx.x] = p;
+    if (threadIdx.x <= 2u * (uint32_t)n) {          // data-qubit factors of Lemma 1 by exposure m
+        const double am = apow(S, (int)threadIdx.x);
+        const double h = 1.0 + am * am;
+        S.hdat[threadIdx.x] = 0.5 * h;
+        S.rdat[threadIdx.x] = 1.0 / h;
     }
     uint32_t *expl = scr.expl + slot * (size_t)P.D;
     // pruned mode keeps every branch implicit until a jump fires (the state
@@ -1314,6 +1323,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     bool jumped = false;
     uint32_t jumps = 0, first_jump = 0, jump_sites = 0;
     const double k2 = qubit ? ldexp(1.0, -P.k) : 1.0;   // |first-wall factor|^2
+    const double inv_k2 = qubit ? ldexp(1.0, P.k) : 1.0;
     for (;;) {
         // next slice whose candidates can matter: before the first fired jump
         // every component is on a noiseless orbit, so a candidate on a position
@@ -1332,17 +1342,21 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             const int sw = final_epoch ? T - 1 : s1 - 1;
             double dn = 1.0, al = 1.0;
             if (qubit) {
-                const double an = apow(S, 2 * n);
                 for (int q = 0; q < P.k; ++q) {
-                    const double am = apow(S, ov(2 * n + 2 * q + 1, 4 * n + 2 * q, sw));
-                    const double h = 1.0 + am * am;
-                    dn *= 0.5 * h;
-                    S.qt[q] = 1.0 / h;
-                    al *= 0.5 * (1.0 + an);
+                    const int m = ov(2 * n + 2 * q + 1, 4 * n + 2 * q, sw);
+                    dn *= S.hdat[m];
+                    S.qt[q] = S.rdat[m];
+                    al *= S.hdat[n];                      // (1 + a^(2n)) / 2: a fully exposed data qubit
                 }
             }
             S.dn = dn;
             S.al = al;
+            // lazy epochs count branches (|c|^2 without the wall factor, data
+            // factors apart); explicit epochs count components (uni: |c|^2 2^-k)
+            const bool lp = lazy && !jumped;
+            const double w2c = uni ? w2u * inv_k2 : 1.0;
+            S.fW = lp ? w2c * dn : (uni ? w2u : 1.0);
+            S.fO = lp ? w2c * al : (uni ? w2u : 1.0);
         }
         if (lazy && !jumped && threadIdx.x < 128) {
             // exposure tables of the closed form (Eq. (12); Prop. 1 for the
@@ -1580,14 +1594,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 hall[b] = 0; hemp[b] = 0; hov[b] = 0;
             }
         }
-        block_sum3(wsum, wempty, ovl, S);
-        if (lazy_pre) {
-            // histogram counts are per branch: |c|^2 without the wall factor
-            const double sc = uni ? w2u / k2 : 1.0;
-            wsum *= sc * S.dn; wempty *= sc * S.dn; ovl *= sc * S.al;
-        } else if (uni) {
-            wsum *= w2u; wempty *= w2u; ovl *= w2u;
-        }
+        block_sum3(wsum, wempty, ovl, S, S.fW, S.fW, S.fO);
         // good branches of the eager form: closed-form weights before the
         // first jump (Eq. (18))
         double wgs = 0.0, ogs = 0.0;
