@@ -118,6 +118,14 @@ __device__ __forceinline__ void mark_leaves(uint32_t *bits, int n, uint32_t v, b
     }
 }
 
+// dynamic shared memory (32-bit words): three exponent histograms, at least
+// the 3 x 512 doubles of a block sum
+__host__ __device__ inline uint32_t dyn_words(int n, int k) {
+    const uint32_t H = (uint32_t)((2 * n + k) * (6 * n + 2 * k - 1) + 1);
+    const uint32_t hist = 3u * ((H + 31u) & ~31u);
+    return hist > 3u * 2u * 512u ? hist : 3u * 2u * 512u;
+}
+
 // ---------------------------------------------------------------------------
 // block reductions (fixed order: deterministic for a given block size)
 __device__ __forceinline__ double warp_sum(double x) {
@@ -147,6 +155,7 @@ struct Smem {
     int t;
     int status;
     double sA, sB, sC;
+    double *part;                  // 3 NT doubles of the dynamic area, zero between block sums
     double dn, al, qt[kMaxK];      // per-epoch data factors (qubit): norm^2, final overlap, 1/(1 + a^(2 m_t))
     double fW, fO;                 // per-epoch scale of the weight sums and of the overlap sum
     double hdat[2 * kMaxN + 1];    // per trajectory: (1 + a^(2m)) / 2 and 1 / (1 + a^(2m)), m <= 2n
@@ -159,20 +168,25 @@ struct Smem {
     int32_t econst;                // qutrit: exposure of the routers (every address bit is excited)
 };
 
-// Block sums of doubles.  FP64 issue is scarce on this part (about two
-// lanes per clock per SM), so each warp reduces its own values and a single
-// warp reduces the per-warp partials; every thread then reads the result.
+// Block sums of doubles.  FP64 issue is scarce on this part (a warp-wide
+// FP64 instruction holds a sub-partition for tens of cycles), so instead of
+// a shuffle tree in every warp each thread parks its partial in S.part (NT
+// doubles per value, zero between uses) and one warp adds them up, lane l
+// taking partials l, l + 32, ... and a shuffle tree finishing; that warp
+// leaves the area zero again.  The order is fixed: deterministic.
 template <int NT>
 __device__ double block_sum(double x, double *red, Smem<NT> &S) {
-    constexpr int NW = NT / 32;
-    x = warp_sum(x);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    (void)red;
+    double *part = S.part;
     __syncthreads();
-    if (lane == 0) red[w] = x;
+    part[threadIdx.x] = x;
     __syncthreads();
-    if (w == 0) {
-        const double v = warp_sum(lane < NW ? red[lane] : 0.0);
-        if (lane == 0) S.sA = v;
+    if (threadIdx.x < 32) {
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < NT / 32; ++q) { r += part[q * 32 + threadIdx.x]; part[q * 32 + threadIdx.x] = 0.0; }
+        r = warp_sum(r);
+        if (threadIdx.x == 0) S.sA = r;
     }
     __syncthreads();
     return S.sA;
@@ -182,17 +196,22 @@ __device__ double block_sum(double x, double *red, Smem<NT> &S) {
 template <int NT>
 __device__ void block_sum3(double &a, double &b, double &c, Smem<NT> &S, double fa = 1.0, double fb = 1.0,
                            double fc = 1.0) {
-    constexpr int NW = NT / 32;
-    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *part = S.part;
     __syncthreads();
-    if (lane == 0) { S.redA[w] = a; S.redB[w] = b; S.redC[w] = c; }
+    part[threadIdx.x] = a;
+    part[NT + threadIdx.x] = b;
+    part[2 * NT + threadIdx.x] = c;
     __syncthreads();
-    if (w == 0) {
-        const double ra = warp_sum(lane < NW ? S.redA[lane] : 0.0);
-        const double rb = warp_sum(lane < NW ? S.redB[lane] : 0.0);
-        const double rc = warp_sum(lane < NW ? S.redC[lane] : 0.0);
-        if (lane == 0) { S.sA = ra * fa; S.sB = rb * fb; S.sC = rc * fc; }
+    if (threadIdx.x < 32) {
+        double ra = 0.0, rb = 0.0, rc = 0.0;
+#pragma unroll
+        for (int q = 0; q < NT / 32; ++q) {
+            const int i = q * 32 + (int)threadIdx.x;
+            ra += part[i]; rb += part[NT + i]; rc += part[2 * NT + i];
+            part[i] = 0.0; part[NT + i] = 0.0; part[2 * NT + i] = 0.0;
+        }
+        ra = warp_sum(ra); rb = warp_sum(rb); rc = warp_sum(rc);
+        if (threadIdx.x == 0) { S.sA = ra * fa; S.sB = rb * fb; S.sC = rc * fc; }
     }
     __syncthreads();
     a = S.sA; b = S.sB; c = S.sC;
@@ -1868,8 +1887,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) traj_kernel(const __grid_constant__ Params P) {
     __shared__ Smem<NT> S;
-    extern __shared__ uint32_t dyn_hist[];          // 3 exponent histograms of hist_pad bins, kept zero between uses
-    for (int b = threadIdx.x; b < 3 * P.hist_pad; b += NT) dyn_hist[b] = 0;
+    // 3 exponent histograms of hist_pad bins, or the partials of a block sum;
+    // kept zero between uses
+    extern __shared__ __align__(16) uint32_t dyn_hist[];
+    for (uint32_t b = threadIdx.x; b < dyn_words(P.n, P.k); b += NT) dyn_hist[b] = 0;
+    if (threadIdx.x == 0) S.part = reinterpret_cast<double *>(dyn_hist);
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) S.t = (int)atomicAdd(P.work, 1u);
@@ -1912,7 +1934,7 @@ int hist_pad(int n, int k) {
     return (H + 31) & ~31;
 }
 
-size_t dyn_smem_bytes(int n, int k) { return 3 * (size_t)hist_pad(n, k) * sizeof(uint32_t); }
+size_t dyn_smem_bytes(int n, int k) { return (size_t)dyn_words(n, k) * sizeof(uint32_t); }
 
 bool valid_threads(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 
