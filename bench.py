@@ -63,6 +63,40 @@ def world_throughput(t_local: float, steps: int, ntraj: int, dist=None) -> tuple
     return world * steps * ntraj / t, t
 
 
+# INT32 operations per unit of counted work: a fault-stream draw is half a
+# Philox4x32-10 call (10 rounds of 2 wide multiplies, 4 xors, 2 key adds)
+# plus the 13-step fixed-point gap search; a component-slice is the path-word
+# gate arithmetic; a branch-epoch is the closed-form exposure (4 table
+# lookups and adds), the hit test and a histogram count; a component-epoch
+# is the pack/unpack, mask and histogram bookkeeping of an explicit pass
+OPS_PER_UNIT = {"draws": 140, "comp_slices": 12, "branch_epochs": 12, "comp_epochs": 30}
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traj_kernel_qubit_n12k4_traffic.json")
+
+
+def _kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2609_34935_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "qram_sim.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic_per_step():
+    """DRAM bytes of one step launch from the committed ncu record, only if it
+    was taken on the kernel sources of this tree."""
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    return rec.get("dram_bytes_per_step_launch") if rec.get("sources_sha256") == _kernel_sources_hash() else None
+
+
 def _problem():
     return W.data_loading(W.QUBIT, N, K, seed=SEED)
 
@@ -238,6 +272,7 @@ def main():
     barrier()
     clocks = Clocks(local)
     clocks.start()
+    sim.work_counters(reset=True)
     l0 = sim.launch_count
     ev = []
     barrier()
@@ -253,6 +288,7 @@ def main():
     barrier()
     launches = sim.launch_count - l0
     ms = [a.elapsed_time(b) for a, b in ev]
+    work = sim.work_counters(reset=True)
     cl = clocks.stop()
     res = sim.results(out)
     value, t_dev = world_throughput(sum(ms) / 1e3, args.steps, NTRAJ, dist)
@@ -321,23 +357,20 @@ def main():
     e2e_val = world * NTRAJ / float(np.mean(e2e_t))
 
     # ---- roofline of the trajectory kernel ---------------------------------
-    nodes = (1 << N) - 1
-    T = 6 * N + 2 * K
-    philox_calls = NTRAJ * (T - 1) * nodes
-    comp_slices = float(np.sum(res["explicit_comps"].astype(np.float64))) * (T - 1)   # upper bound (deaths)
-    ops = philox_calls * 84 + comp_slices * 12
+    # algorithmic INT32 work counted by the kernel itself over the timed steps
+    ops = sum(work[k] * OPS_PER_UNIT[k] for k in OPS_PER_UNIT) / args.steps
     sm_mhz = cl.get("sm_mhz") or 2032.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_int = nsm * 64 * sm_mhz * 1e6 / 1e12          # Tops/s: 64 INT32 lanes/SM/clock
     launch_s = t_dev / args.steps
     achieved = ops / launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "Tops/s (INT32)",
-            "frac": achieved / peak_int, "traffic": None,
-            "note": "algorithmic INT32 ops per launch (84 per Philox4x32-10 candidate draw of a (slice, node); "
-                    "12 per explicit component-slice of path-word gates, counted as explicit components x (T-1)) "
-                    "/ launch time from CUDA events; peak derived: SMs x 64 INT32 lanes/clock x median SM clock "
-                    "under load (not a measured peak)",
-            "philox_calls": philox_calls, "component_slices_upper": comp_slices, "variant_threads": variant}
+            "frac": achieved / peak_int, "traffic": _traffic_per_step(),
+            "note": "algorithmic INT32 ops per step launch from the kernel's work counters x ops per unit "
+                    f"{OPS_PER_UNIT} / launch time from CUDA events; peak derived: SMs x 64 INT32 lanes/clock x "
+                    "median SM clock under load (not a measured peak); traffic: DRAM read+write bytes of one "
+                    "step launch from an ncu capture of the same kernel sources, else null",
+            "work_per_step": {k: v / args.steps for k, v in work.items()}, "variant_threads": variant}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -213,6 +213,19 @@ int qram_sync(qram_sim_t *sim);
 /* Number of kernel launches issued by this simulator since creation. */
 uint64_t qram_launch_count(const qram_sim_t *sim);
 
+/* Work done by this simulator's trajectory launches since creation or the
+ * last reset.  No counterpart in the paper: instrumentation for the
+ * roofline of the trajectory kernel.  out (host, 4 entries):
+ *   out[0] fault-stream draws (one 64-bit word per geometric gap),
+ *   out[1] explicit component-slices (gate slices applied to explicit
+ *          components, pruned and full mode),
+ *   out[2] branch-epochs of the closed-form weights before the first jump,
+ *   out[3] component-epochs of the explicit passes.
+ * Each trajectory adds its counts when it finishes.  Waits for the
+ * simulator's stream; reset != 0 zeroes the counters afterwards.  Returns
+ * QRAM_E_ARG for null pointers, QRAM_E_CUDA on a CUDA error. */
+int qram_work_counters(qram_sim_t *sim, uint64_t *out, int reset);
+
 /* ---------------------------------------------------------------------------
  * Serving loop (continuous batching; no paper counterpart, the paper runs
  * one query at a time).  A server owns one device.  Requests are queued by

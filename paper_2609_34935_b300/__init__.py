@@ -90,6 +90,7 @@ def load_library(build_if_missing: bool = True):
     L.qram_sync.argtypes = [vp]
     L.qram_launch_count.argtypes = [vp]
     L.qram_launch_count.restype = u64
+    L.qram_work_counters.argtypes = [vp, vp, C.c_int]
     L.qram_server_create.argtypes = [C.c_size_t, C.c_int, u32, C.POINTER(vp)]
     L.qram_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
     L.qram_server_estimate.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
@@ -318,6 +319,14 @@ class QramSim:
     @property
     def launch_count(self) -> int:
         return int(self.lib.qram_launch_count(self.h))
+
+    def work_counters(self, reset: bool = False) -> dict:
+        """Work of the trajectory launches since creation or the last reset:
+        fault-stream draws, explicit component-slices, closed-form
+        branch-epochs, explicit component-epochs (waits for the stream)."""
+        o = np.zeros(4, np.uint64)
+        _check(self.lib.qram_work_counters(self.h, o.ctypes.data, 1 if reset else 0), "qram_work_counters")
+        return {"draws": int(o[0]), "comp_slices": int(o[1]), "branch_epochs": int(o[2]), "comp_epochs": int(o[3])}
 
 
 class QramServer:

@@ -228,6 +228,7 @@ Params base_params(qram_sim *S) {
     P.scr = S->scr;
     P.work = S->d_work;
     P.w2u = S->d_w2u;
+    P.ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(S->d_work) + 32);
     std::memcpy(P.ops, S->ops, sizeof(P.ops));
     std::memcpy(P.occ2, S->occ2, sizeof(P.occ2));
     P.orbit = S->orbit;
@@ -467,6 +468,7 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
         !ok(cudaMemcpyAsync(S->d_re, p->amp_re, D * 8, cudaMemcpyHostToDevice, st)) ||
         !ok(cudaMemcpyAsync(S->d_im, p->amp_im, D * 8, cudaMemcpyHostToDevice, st)))
         rc = QRAM_E_CUDA;
+    if (!rc && !ok(cudaMemsetAsync(S->d_work, 0, 64, st))) rc = QRAM_E_CUDA;     // counter + work counters
     if (!rc && !ok(launch_uniform_weight(S->d_re, S->d_im, S->D, S->enc == QRAM_QUBIT ? S->k : 0, S->d_w2u, st)))
         rc = QRAM_E_CUDA;
     if (!rc) S->launches++;
@@ -737,6 +739,16 @@ int qram_sync(qram_sim_t *S) {
 }
 
 uint64_t qram_launch_count(const qram_sim_t *S) { return S ? S->launches : 0; }
+
+int qram_work_counters(qram_sim_t *S, uint64_t *out, int reset) {
+    if (!S || !out) return QRAM_E_ARG;
+    DeviceGuard g(S->device);
+    char *c = reinterpret_cast<char *>(S->d_work) + 32;
+    if (!ok(cudaMemcpyAsync(out, c, 32, cudaMemcpyDeviceToHost, S->stream))) return QRAM_E_CUDA;
+    if (reset && !ok(cudaMemsetAsync(c, 0, 32, S->stream))) return QRAM_E_CUDA;
+    if (!ok(cudaStreamSynchronize(S->stream))) return QRAM_E_CUDA;
+    return QRAM_OK;
+}
 
 // Stop a running launch of this simulator from taking new trajectories: the
 // work counter is raised past any trajectory count (the CTAs finish the

@@ -99,6 +99,8 @@ struct Params {
     const uint32_t *input_error;   // if non-null and nonzero at run time: every trajectory is QRAM_E_ARG
     const double *w2u;             // device scalar: |c|^2 (times 2^-k for qubits) when every column shares it, else 0
     const uint64_t *traj0_dev;     // if non-null, the first trajectory index is read here (graph replays)
+    unsigned long long *ctr;       // if non-null: work counters (draws, explicit comp-slices, lazy branch-epochs,
+                                   // explicit comp-epochs), added once per trajectory
     int hist_pad;                  // bins per exponent histogram (dynamic shared memory: 3 of them)
     SliceOps ops[kMaxT];
     uint32_t occ2[kMaxT];  // per slice: path-word positions any noiseless orbit can hold excited

@@ -163,6 +163,7 @@ struct Smem {
     uint32_t region;               // after a jump: root of the subtree that can hold excitations
     uint64_t gq[kGapBits];         // fault stream: 64-bit fixed-point (1 - gamma)^(2^m)
     uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
+    uint32_t wk[4];                // work of this trajectory (see Params::ctr)
     int16_t etab[4][16];           // lazy epochs: address exposure by nibble of the address
     int16_t dtab[4][16];           // qutrit: data exposure by nibble of j (0, 1) and of j ^ d (2, 3)
     int32_t econst;                // qutrit: exposure of the routers (every address bit is excited)
@@ -1094,7 +1095,10 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         }
         return;
     }
-    if (threadIdx.x == 0) { S.status = valid ? QRAM_OK : QRAM_E_ARG; S.refcol = -1; S.nbad = 0; S.nJ = 0; }
+    if (threadIdx.x == 0) {
+        S.status = valid ? QRAM_OK : QRAM_E_ARG; S.refcol = -1; S.nbad = 0; S.nJ = 0;
+        S.wk[0] = S.wk[1] = S.wk[2] = S.wk[3] = 0;
+    }
     for (int w = threadIdx.x; w < 512; w += NT) { S.badbits[w] = 0; S.hitbits[w] = 0; }
     for (int w = threadIdx.x; w < 1024; w += NT) S.candbits[w] = 0;
     __syncthreads();
@@ -1131,7 +1135,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         const uint32_t per = (nblk + NW - 1) / NW;
         const uint32_t g0 = w * per, g1 = min(nblk, g0 + per);
         uint32_t *seg = scr.wseg + (slot * NW + w) * scr.seg_cap;
-        uint32_t cnt = 0;
+        uint32_t cnt = 0, draws = 0;
         bool overflow = false;
         for (uint32_t gb = g0; gb < g1; gb += 32) {
             const uint32_t g = gb + lane;
@@ -1167,7 +1171,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         const uint64_t t = __umul64hi(acc, S.gq[m]);
                         if (t > u) { acc = t; G += 1u << m; }
                     }
-                    if (G >= end - pos) break;
+                    if (G >= end - pos) { if (pass == 0) draws += r + 1; break; }
                     pos += G;
                     if (pass == 0) ++mine;
                     else {
@@ -1180,7 +1184,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             }
         }
         overflow = __any_sync(0xFFFFFFFFu, overflow);
-        if (lane == 0) S.wcount[w] = overflow ? 0xFFFFFFFFu : cnt;
+        draws = __reduce_add_sync(0xFFFFFFFFu, draws);
+        if (lane == 0) { S.wcount[w] = overflow ? 0xFFFFFFFFu : cnt; atomicAdd(&S.wk[0], draws); }
         __syncthreads();
         uint32_t off = 0, tot = 0;
         bool bad = false;
@@ -1483,6 +1488,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         // while this chunk evolves
         uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
         if (threadIdx.x < ncomp_pass) nxt = scr.cs[cbase + threadIdx.x];
+        uint32_t nsl = 0;                                  // component-slices evolved by this thread
         for (uint32_t r0 = 0; r0 < ncomp_pass; r0 += NT) {
             const uint32_t r = r0 + threadIdx.x;
             bool alive = r < ncomp_pass;
@@ -1513,6 +1519,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             }
             if (alive) {
                 const int slast = final_epoch ? T - 1 : s1;
+                nsl += (uint32_t)(slast - s_prev);
                 for (int s = s_prev + 1; s <= slast; ++s) {
                     if (!apply_slice(P.ops[s], c, xs, C)) { capfail = true; break; }
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
@@ -1595,6 +1602,12 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             }
         }
         if (lane == 0) S.segn[warp] = wcur;
+        nsl = __reduce_add_sync(0xFFFFFFFFu, nsl);
+        if (lane == 0 && nsl) atomicAdd(&S.wk[1], nsl);
+        if (threadIdx.x == 0) {
+            if (lazy_pre) S.wk[2] += (uint32_t)P.D;
+            else S.wk[3] += ncomp_pass;
+        }
         if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
         __syncthreads();
         if (threadIdx.x == 0 && compact) S.ncomp = wr;
@@ -1653,6 +1666,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 R.q_ground = ground ? 1 : 0;
                 R.status = (uint8_t)S.status;
                 if (P.out) P.out[t] = R;
+                if (P.ctr)
+                    for (int q = 0; q < 4; ++q) atomicAdd(P.ctr + q, (unsigned long long)S.wk[q]);
                 if (P.dump_mode) {
                     P.dump.scal[0] = Wtot;
                     P.dump.scal[1] = jumped ? 1.0 : 0.0;

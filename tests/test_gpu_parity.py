@@ -286,3 +286,30 @@ def test_autotune_picks_a_variant_and_caches(tmp_path):
     sim.set_variant(256)
     assert sim.autotune("pruned", 3e-3, 1500, cache=cache) == best      # served from the cache
     sim.close()
+
+
+def test_work_counters_exact():
+    """The kernel's work counters obey exact identities: every block of the
+    fault stream ends with one terminating draw (draws = candidates + blocks);
+    a full launch without damping evolves every component through T - 1
+    slices; a pruned one without damping only folds the closed form once."""
+    enc, n, k, ntraj = W.QUBIT, 6, 2, 200
+    p = W.data_loading(enc, n, k, seed=77)
+    sim = _sim(p, 77)
+    T = cf.slices(n, k)
+    nblk = math.ceil((T - 1) * 2 * ((1 << n) - 1) / 2048)
+    sim.work_counters(reset=True)
+    r = sim.results(sim.run_pruned(0, torch.full((ntraj,), 3e-3, dtype=torch.float64, device="cuda")))
+    w = sim.work_counters(reset=True)
+    assert w["draws"] == int(r["ncand"].sum()) + ntraj * nblk
+    g0 = torch.zeros(ntraj, dtype=torch.float64, device="cuda")
+    sim.results(sim.run_full(0, g0))
+    w = sim.work_counters(reset=True)
+    assert w["draws"] == 0
+    assert w["comp_slices"] == ntraj * p.D * (1 << k) * (T - 1)
+    assert w["comp_epochs"] == ntraj * p.D * (1 << k)
+    sim.results(sim.run_pruned(0, g0))
+    w = sim.work_counters(reset=True)
+    assert w["comp_slices"] == 0 and w["comp_epochs"] == 0
+    assert w["branch_epochs"] == ntraj * p.D
+    sim.close()
