@@ -223,11 +223,15 @@ def main():
     ap.add_argument("--full-per-batch", type=int, default=20, help="full-mode trajectories per gamma batch")
     ap.add_argument("--serving", action="store_true", help="run the serving-stream benchmark instead")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--scan", action="store_true",
+                    help="fidelity vs n (qubit, k=3, 500-branch random input, 200 trajectories per point)")
     ap.add_argument("--profile-case", type=float, default=None, metavar="GAMMA",
                     help="one launch of 296 trajectories (148 CTAs of 512 threads) at this gamma, for ncu")
     args = ap.parse_args()
     if args.profile_case is not None:
         return run_profile_case(args.profile_case)
+    if args.scan:
+        return run_scan(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.serving:
@@ -408,6 +412,20 @@ def main():
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_scan(args):
+    """Fidelity versus n for gamma in {1e-5, 1e-4, 1e-3} (the damping-only
+    analog of the paper's Fig. 2), one JSON line with the table."""
+    import torch
+    from paper_2609_34935_b300.scan import fidelity_vs_n
+    t0 = time.perf_counter()
+    rows = fidelity_vs_n(W.QUBIT, range(3, 13), (1e-5, 1e-4, 1e-3), k=3, D=500, ntraj=200)
+    torch.cuda.synchronize()
+    print(json.dumps({"scan": "mean fidelity vs n, qubit, k=3, 500-branch random input (one column per "
+                              "address), 200 trajectories per point, damping only",
+                      "seconds": time.perf_counter() - t0, "rows": rows}), flush=True)
+    return 0
 
 
 def run_profile_case(gamma: float):

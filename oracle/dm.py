@@ -45,8 +45,27 @@ def _events(n: int, k: int):
     return T, ev
 
 
-def simulate(encoding: int, n: int, k: int, memory, gamma: float, addr=None, bus=None, amp=None):
-    """Returns (F_rho, trace, marginal distribution over (address, bus))."""
+def _weyl(d: int):
+    """Non-identity Pauli (d = 2: X, Z, Y) or Weyl operators X^a Z^b (d = 3)."""
+    X = np.roll(np.eye(d, dtype=np.complex128), 1, axis=0)          # |j> -> |j+1 mod d>
+    w = np.exp(2j * math.pi / d)
+    Z = np.diag([w ** j for j in range(d)])
+    ops = []
+    for a_ in range(d):
+        for b_ in range(d):
+            if a_ or b_:
+                ops.append(np.linalg.matrix_power(X, a_) @ np.linalg.matrix_power(Z, b_))
+    return ops
+
+
+def simulate(encoding: int, n: int, k: int, memory, gamma: float, addr=None, bus=None, amp=None,
+             eps: float = 0.0, depol_first: bool = True):
+    """Returns (F_rho, trace, marginal distribution over (address, bus)).
+
+    eps: depolarizing channel of strength eps on every tree site after the
+    gates of every slice (Sec. II.B): with probability eps one of the
+    non-identity Paulis (qubits) or Weyl operators (qutrits), uniformly.
+    depol_first: the depolarizing layer precedes the damping layer."""
     nodes = (1 << n) - 1
     M = 2 * nodes
     base = 2 if encoding == 1 else 3
@@ -158,6 +177,26 @@ def simulate(encoding: int, n: int, k: int, memory, gamma: float, addr=None, bus
         kraus = [np.diag([1, a, a]).astype(np.complex128),
                  np.array([[0, sq, 0], [0, 0, 0], [0, 0, 0]], dtype=np.complex128),
                  np.array([[0, 0, sq], [0, 0, 0], [0, 0, 0]], dtype=np.complex128)]
+    weyl = _weyl(base) if eps > 0 else []
+
+    def depolarize(rho):
+        for q in range(M):
+            acc = (1.0 - eps) * rho
+            for Wop in weyl:
+                acc += (eps / len(weyl)) * on_axis(rho, q, Wop)
+            rho = acc
+        return rho
+
+    def damp(rho):
+        if gamma == 0.0:
+            return rho
+        for q in range(M):
+            acc = np.zeros_like(rho)
+            for K in kraus:
+                acc += on_axis(rho, q, K)
+            rho = acc
+        return rho
+
     for s in range(1, T):
         if encoding == 1 and s == 2 * n + 1:
             for t in range(k):
@@ -172,11 +211,11 @@ def simulate(encoding: int, n: int, k: int, memory, gamma: float, addr=None, bus
         if encoding == 1 and s == 4 * n + 2 * k - 1:
             for t in range(k):
                 rho = on_axis(rho, B0 + t, H)
-        for q in range(M):
-            acc = np.zeros_like(rho)
-            for K in kraus:
-                acc += on_axis(rho, q, K)
-            rho = acc
+        if eps > 0 and depol_first:
+            rho = depolarize(rho)
+        rho = damp(rho)
+        if eps > 0 and not depol_first:
+            rho = depolarize(rho)
     F = float(np.real(psi_id.conj() @ rho @ psi_id))
     tr = float(np.real(np.trace(rho)))
     diag = np.real(np.diag(rho))

@@ -838,6 +838,19 @@ __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *
 // hold any candidate this slice: path sites elsewhere cannot be in J.
 __device__ __forceinline__ uint32_t mask_first(const CompR &c, const uint16_t *xs, const Ctx &C,
                                                const uint32_t *candbits, uint32_t cl2, uint32_t &cnt) {
+    if (c.nexc == 0 && c.pwB == 0) {
+        // path A only: its sites increase with the path-word bit (deeper layer, larger node)
+        uint32_t first = 0xFFFFFFFFu;
+        cnt = 0;
+        for (uint32_t w = c.pw & cl2; w; w &= w - 1u) {
+            const int b = __ffs(w) - 1;
+            const uint32_t site = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
+            if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+            if (cnt == 0) first = (site << 1) | ((C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 1u : 0u);
+            ++cnt;
+        }
+        return first;
+    }
     uint32_t wA = c.nexc ? c.pw : (c.pw & cl2), wB = c.pwB & cl2, xi = 0, first = 0xFFFFFFFFu;
     const uint32_t iB = wB ? b_addr(c, C) : 0u;
     cnt = 0;

@@ -313,3 +313,24 @@ def test_work_counters_exact():
     assert w["comp_slices"] == 0 and w["comp_epochs"] == 0
     assert w["branch_epochs"] == ntraj * p.D
     sim.close()
+
+
+@pytest.mark.parametrize("n,gamma", [(3, 1e-3), (5, 3e-3), (6, 1e-2)])
+def test_fidelity_scan_points_match_oracle(n, gamma):
+    """Points of the fidelity-vs-n scan (scan input: distinct addresses,
+    random bus words, equal weights): every trajectory against the oracle,
+    and the scan's mean and standard error against the oracle's numbers."""
+    from paper_2609_34935_b300.scan import fidelity_vs_n
+    k, D, ntraj, seed = 3, 500, 200, 6001
+    rows = fidelity_vs_n(W.QUBIT, [n], [gamma], k=k, D=D, ntraj=ntraj, seed=seed)
+    assert len(rows) == 1
+    p = W.uniform_random_input(W.QUBIT, n, k, D, seed + 97 * n)
+    ref = core.run(p, seed + n, 0, np.full(ntraj, gamma))
+    sim = _sim(p, seed + n)
+    got = sim.results(sim.run_pruned(0, torch.full((ntraj,), gamma, dtype=torch.float64, device="cuda:0")))
+    sim.close()
+    _cmp_results(got, ref)
+    f = ref["fidelity"]
+    assert abs(rows[0]["mean_fidelity"] - f.mean()) < TOL
+    assert abs(rows[0]["se"] - f.std(ddof=1) / math.sqrt(ntraj)) < 1e-8
+    assert rows[0]["D"] == min(D, 1 << n)

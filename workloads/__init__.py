@@ -10,6 +10,8 @@ zero bus input; memory with i.i.d. uniform bits):
   - ``data_loading(n, k, seed)``: D = 2^n columns, c_i = 2^{-n/2}, bus 0.
   - ``random_columns(n, k, D, seed)``: D distinct addresses, random bus
     words, random complex amplitudes (one column per address, Sec. IV.D).
+  - ``uniform_random_input(n, k, D, seed)``: min(D, 2^n) distinct addresses
+    with random bus words and equal weights (the fidelity-scan input).
   - ``gamma_batches(ntraj, batch, lo, hi, seed)``: a damping rate per batch
     of trajectories, log-uniform in [lo, hi].
 """
@@ -60,6 +62,20 @@ def random_columns(encoding: int, n: int, k: int, D: int, seed: int) -> Problem:
     amp = rng.normal(size=D) + 1j * rng.normal(size=D)
     amp /= np.sqrt(np.sum(np.abs(amp) ** 2))
     return Problem(encoding, n, k, memory_bits(n, k, seed), addr, bus, amp.astype(np.complex128))
+
+
+def uniform_random_input(encoding: int, n: int, k: int, D: int, seed: int) -> Problem:
+    """The scan input of Sec. V.A restricted to one bus column per address:
+    min(D, 2^n) distinct addresses drawn without replacement, a uniform random
+    bus word each, equal weights (the paper draws D of the 2^(n+k)
+    address-bus components; several columns per address are outside the
+    input class of Sec. IV.D)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 0x2E5))
+    Dn = min(D, 1 << n)
+    addr = np.sort(rng.choice(1 << n, size=Dn, replace=False)).astype(np.uint32)
+    bus = rng.integers(0, 1 << k, size=Dn, dtype=np.uint32)
+    amp = np.full(Dn, 1.0 / np.sqrt(Dn), dtype=np.complex128)
+    return Problem(encoding, n, k, memory_bits(n, k, seed), addr, bus, amp)
 
 
 def gamma_batches(ntraj: int, batch: int, lo: float, hi: float, seed: int) -> np.ndarray:
