@@ -206,6 +206,16 @@ int qram_dump_state(qram_sim_t *sim, int mode, uint64_t traj, double gamma, uint
                     uint32_t *addr, uint32_t *bus, uint64_t *config_hash, double *re, double *im,
                     uint32_t *count);
 
+/* Low-weight truncation of the predicted good branches in qram_dump_state
+ * (Sec. IV, cost discussion after Eq. (22)): each good branch ends in a
+ * superposition over all 2^k output words whose amplitude falls by
+ * beta/alpha = O(n gamma) per unit of Hamming distance from the ideal word
+ * (Eq. (14)); with w_max >= 0 only the words within distance w_max are
+ * emitted, the dropped amplitudes being O((n gamma)^(w_max + 1)).
+ * w_max = -1 (the default) emits all 2^k words.  Qubit encoding only (the
+ * qutrit good branch is a single word); returns QRAM_E_ARG for w_max < -1. */
+int qram_set_dump_weight(qram_sim_t *sim, int w_max);
+
 /* Waits for the simulator's stream; returns QRAM_E_CUDA on an asynchronous
  * CUDA error, else QRAM_OK. */
 int qram_sync(qram_sim_t *sim);

@@ -65,7 +65,10 @@ def simulate(encoding: int, n: int, k: int, memory, gamma: float, addr=None, bus
     eps: depolarizing channel of strength eps on every tree site after the
     gates of every slice (Sec. II.B): with probability eps one of the
     non-identity Paulis (qubits) or Weyl operators (qutrits), uniformly.
-    depol_first: the depolarizing layer precedes the damping layer."""
+    depol_first: the depolarizing layer precedes the damping layer.
+    Parity unpinned for eps > 0: App. C restricts the channel to the active
+    positions of an undefined routing front, and Tab. IV's Pauli row is not
+    reproduced with every site active; only trace preservation is checked."""
     nodes = (1 << n) - 1
     M = 2 * nodes
     base = 2 if encoding == 1 else 3

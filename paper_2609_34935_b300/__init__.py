@@ -91,6 +91,7 @@ def load_library(build_if_missing: bool = True):
     L.qram_launch_count.argtypes = [vp]
     L.qram_launch_count.restype = u64
     L.qram_work_counters.argtypes = [vp, vp, C.c_int]
+    L.qram_set_dump_weight.argtypes = [vp, C.c_int]
     L.qram_server_create.argtypes = [C.c_size_t, C.c_int, u32, C.POINTER(vp)]
     L.qram_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
     L.qram_server_estimate.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
@@ -227,7 +228,11 @@ class QramSim:
         _check(self.lib.qram_fidelity(self.h, _dptr(raw), raw.shape[0], C.byref(m), C.byref(s)), "qram_fidelity")
         return m.value, s.value
 
-    def dump_state(self, mode: str, traj: int, gamma: float, cap: int = 1 << 18):
+    def dump_state(self, mode: str, traj: int, gamma: float, cap: int = 1 << 18, w_max: int = -1):
+        """Final normalised state of one trajectory; w_max >= 0 keeps only the
+        good-branch output words within that Hamming distance of the ideal
+        word (low-weight truncation)."""
+        _check(self.lib.qram_set_dump_weight(self.h, int(w_max)), "qram_set_dump_weight")
         while True:
             addr = np.zeros(cap, np.uint32)
             bus = np.zeros(cap, np.uint32)

@@ -35,6 +35,7 @@ struct qram_sim {
     double *d_fid2 = nullptr;
     double *d_gmax = nullptr;
     double *d_w2u = nullptr;
+    uint32_t *d_colof = nullptr;    // complete qubit input: column of each address
     const uint32_t *hist_cand = nullptr, *hist_off = nullptr;
     uint32_t nhist = 0;
     SliceOps ops[kMaxT]{};
@@ -46,6 +47,7 @@ struct qram_sim {
     size_t dyn = 0;             // dynamic shared memory per CTA
     int scr_threads = 0;        // variant the scratch was laid out for
     double gamma_bound = 0.0;
+    int dump_wmax = -1;         // low-weight truncation of the dumped good branches
 };
 
 namespace {
@@ -228,6 +230,7 @@ Params base_params(qram_sim *S) {
     P.scr = S->scr;
     P.work = S->d_work;
     P.w2u = S->d_w2u;
+    P.col_of = S->d_colof;
     P.ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(S->d_work) + 32);
     std::memcpy(P.ops, S->ops, sizeof(P.ops));
     std::memcpy(P.occ2, S->occ2, sizeof(P.occ2));
@@ -469,6 +472,15 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
         !ok(cudaMemcpyAsync(S->d_im, p->amp_im, D * 8, cudaMemcpyHostToDevice, st)))
         rc = QRAM_E_CUDA;
     if (!rc && !ok(cudaMemsetAsync(S->d_work, 0, 64, st))) rc = QRAM_E_CUDA;     // counter + work counters
+    // every address present (qubit): the closed-form weights factorise over the address bits
+    if (!rc && S->enc == QRAM_QUBIT && D == N) {
+        std::vector<uint32_t> col(N);
+        for (uint32_t b = 0; b < (uint32_t)D; ++b) col[p->addr[b]] = b;
+        if (!ok(cudaMallocAsync((void **)&S->d_colof, N * 4, st)) ||
+            !ok(cudaMemcpyAsync(S->d_colof, col.data(), N * 4, cudaMemcpyHostToDevice, st)) ||
+            !ok(cudaStreamSynchronize(st)))                 // the host vector goes out of scope
+            rc = QRAM_E_CUDA;
+    }
     if (!rc && !ok(launch_uniform_weight(S->d_re, S->d_im, S->D, S->enc == QRAM_QUBIT ? S->k : 0, S->d_w2u, st)))
         rc = QRAM_E_CUDA;
     if (!rc) S->launches++;
@@ -482,7 +494,8 @@ void qram_sim_destroy(qram_sim_t *S) {
     {
         DeviceGuard g(S->device);
         cudaStream_t st = S->stream;
-        void *bufs[] = {S->d_mem, S->d_addr, S->d_bus, S->d_re, S->d_im, S->d_work, S->d_fid2, S->d_gmax, S->d_w2u, S->scratch};
+        void *bufs[] = {S->d_mem,  S->d_addr, S->d_bus,  S->d_re,  S->d_im,    S->d_work,
+                        S->d_fid2, S->d_gmax, S->d_w2u,  S->d_colof, S->scratch};
         for (void *b : bufs) if (b) cudaFreeAsync(b, st);
         cudaStreamSynchronize(st);
         cudaGetLastError();
@@ -694,6 +707,7 @@ int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32
         P.mode = mode == 0 ? kPruned : kFull;
         P.out = (qram_result_t *)(b + o_res);
         P.dump_mode = 1;
+        P.dump_wmax = S->dump_wmax;
         P.dump.col = (uint32_t *)(b + o_col); P.dump.bus = (uint32_t *)(b + o_bus); P.dump.hash = (uint64_t *)(b + o_hash);
         P.dump.re = (double *)(b + o_re); P.dump.im = (double *)(b + o_im); P.dump.cap = ecap;
         P.dump.count = (uint32_t *)(b + o_cnt); P.dump.scal = (double *)(b + o_scal);
@@ -739,6 +753,12 @@ int qram_sync(qram_sim_t *S) {
 }
 
 uint64_t qram_launch_count(const qram_sim_t *S) { return S ? S->launches : 0; }
+
+int qram_set_dump_weight(qram_sim_t *S, int w_max) {
+    if (!S || w_max < -1) return QRAM_E_ARG;
+    S->dump_wmax = w_max;
+    return QRAM_OK;
+}
 
 int qram_work_counters(qram_sim_t *S, uint64_t *out, int reset) {
     if (!S || !out) return QRAM_E_ARG;

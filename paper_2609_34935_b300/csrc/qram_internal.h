@@ -96,9 +96,11 @@ struct Params {
     uint32_t *work;       // work-stealing counter
     DumpOut dump;
     int dump_mode;
+    int dump_wmax;                 // good branches in the dump: output words within this Hamming distance (-1: all)
     const uint32_t *input_error;   // if non-null and nonzero at run time: every trajectory is QRAM_E_ARG
     const double *w2u;             // device scalar: |c|^2 (times 2^-k for qubits) when every column shares it, else 0
     const uint64_t *traj0_dev;     // if non-null, the first trajectory index is read here (graph replays)
+    const uint32_t *col_of;        // qubit input over every address (D = 2^n): column of each address, else null
     unsigned long long *ctr;       // if non-null: work counters (draws, explicit comp-slices, lazy branch-epochs,
                                    // explicit comp-epochs), added once per trajectory
     int hist_pad;                  // bins per exponent histogram (dynamic shared memory: 3 of them)

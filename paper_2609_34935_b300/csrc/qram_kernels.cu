@@ -164,6 +164,8 @@ struct Smem {
     uint64_t gq[kGapBits];         // fault stream: 64-bit fixed-point (1 - gamma)^(2^m)
     uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
     uint32_t wk[4];                // work of this trajectory (see Params::ctr)
+    double fprod2[kMaxT];          // product-form lazy weights: prod_l (1 + a^(2 ov_l(s))) per slice s
+    double fprod1;                 // prod_l (1 + a^(ov_l(T-1))): the final overlap
     int16_t etab[4][16];           // lazy epochs: address exposure by nibble of the address
     int16_t dtab[4][16];           // qutrit: data exposure by nibble of j (0, 1) and of j ^ d (2, 3)
     int32_t econst;                // qutrit: exposure of the routers (every address bit is excited)
@@ -1285,6 +1287,12 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         return;
     }
 
+    // pruned mode keeps every branch implicit until a jump fires (the state
+    // dump reads the explicit set at the end, so it keeps the eager form)
+    const bool lazy = P.mode == kPruned && P.orbit.ok && !P.dump_mode;
+    // lazy epochs in product form: qubit input over every address, equal weights
+    const bool factored = lazy && P.col_of != nullptr && P.w2u != nullptr && *P.w2u > 0.0;
+
     // ---- 3. explicit set ----------------------------------------------------
     const double a = sqrt(1.0 - (valid ? gamma : 0.0));
     if (threadIdx.x < 128) {                        // a^j and a^(64 j) by binary powering
@@ -1304,10 +1312,19 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         S.hdat[threadIdx.x] = 0.5 * h;
         S.rdat[threadIdx.x] = 1.0 / h;
     }
+    for (int sw = (int)threadIdx.x; factored && sw < T; sw += NT) {
+        // sum over every address of a^(2E) after damping slices 1..s: the
+        // address bits enter independently (Eq. (12))
+        double p2 = 1.0, p1 = 1.0;
+        for (int l = 0; l < n; ++l) {
+            const double x = apow(S, ov(2 * l + 1, T - 2 * l - 2, sw));
+            p2 *= 1.0 + x * x;
+            p1 *= 1.0 + x;
+        }
+        S.fprod2[sw] = p2;
+        if (sw == T - 1) S.fprod1 = p1;
+    }
     uint32_t *expl = scr.expl + slot * (size_t)P.D;
-    // pruned mode keeps every branch implicit until a jump fires (the state
-    // dump reads the explicit set at the end, so it keeps the eager form)
-    const bool lazy = P.mode == kPruned && P.orbit.ok && !P.dump_mode;
     if (lazy) {
         // only the size of the explicit set is reported: B plus the reference
         if (threadIdx.x == 0) S.nexpl = S.nbad + (S.refcol >= 0 ? 1u : 0u);
@@ -1450,6 +1467,32 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             // where those qubits are 0 in the empty-mask weight.
             const int sw = final_epoch ? T - 1 : s1 - 1;
             const uint32_t pos = final_epoch ? 0u : (S.cl2 & P.orbit.occ[s1]);
+            if (factored) {
+                // Every address present with equal weights (qubit): the sum of
+                // a^(2E) over all branches factorises over the address bits,
+                // prod_l (1 + a^(2 ov_l)); only the branches under the slice's
+                // candidates (the hit bitmap) need a look, and only to take
+                // their non-empty-mask weight out of the empty-mask sum.
+                if (threadIdx.x == 0) {
+                    wsum = S.fprod2[sw];
+                    wempty = S.fprod2[sw];                   // the final orbit is the ground tree
+                    if (final_epoch) ovl = S.fprod1;         // Walsh coefficient +1 on every branch
+                }
+                for (uint32_t i = threadIdx.x; pos && i < (1u << n); i += NT) {
+                    if ((S.hitbits[i >> 5] >> (i & 31u)) & 1u) {
+                        const uint32_t b = __ldg(P.col_of + i);
+                        const int E = S.etab[0][i & 15u] + S.etab[1][(i >> 4) & 15u] + S.etab[2][(i >> 8) & 15u] +
+                                      S.etab[3][(i >> 12) & 15u];
+                        bool all = false;
+                        const uint32_t tm = orbit_hits(P, S.candbits, pos, s1, i, __ldg(P.bus + b), __ldg(P.mem + i), all);
+                        if (!all && !tm) continue;
+                        const double ae = apow(S, E);
+                        double qp = 1.0;
+                        for (uint32_t x = tm; x; x &= x - 1u) qp *= S.qt[__ffs(x) - 1];
+                        wempty -= all ? ae * ae : ae * ae * (1.0 - qp);
+                    }
+                }
+            } else
             for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
                 const uint32_t i = __ldg(P.addr + b);
                 int E = S.etab[0][i & 15u] + S.etab[1][(i >> 4) & 15u] + S.etab[2][(i >> 8) & 15u] +
@@ -1624,7 +1667,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
         __syncthreads();
         if (threadIdx.x == 0 && compact) S.ncomp = wr;
-        if (uni) {
+        if (uni && !(lazy_pre && factored)) {
             // fold the histograms (and leave them zero for the next epoch)
             __syncthreads();
             for (int b = threadIdx.x; b < H; b += NT) {
@@ -2079,6 +2122,7 @@ __global__ void dump_finalize_kernel(const Params P, uint32_t n_in, uint32_t *ou
             const uint32_t bout = j ^ dm;
             for (uint32_t w = 0; w < nw; ++w) {
                 const int hw = __popc(w ^ bout);
+                if (P.dump_wmax >= 0 && hw > P.dump_wmax) continue;        // low-weight truncation
                 double A = ae;
                 for (int q = 0; q < P.k; ++q) A *= q < hw ? be : al;
                 const uint32_t o = atomicAdd(out_n, 1u);

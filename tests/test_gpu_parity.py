@@ -334,3 +334,31 @@ def test_fidelity_scan_points_match_oracle(n, gamma):
     assert abs(rows[0]["mean_fidelity"] - f.mean()) < TOL
     assert abs(rows[0]["se"] - f.std(ddof=1) / math.sqrt(ntraj)) < 1e-8
     assert rows[0]["D"] == min(D, 1 << n)
+
+
+@pytest.mark.parametrize("wmax", [0, 1])
+def test_dump_low_weight_truncation(wmax):
+    """The truncated dump keeps exactly the good-branch output words within
+    Hamming distance w_max of the ideal word (and every explicit component),
+    with the same amplitudes as the complete dump."""
+    n, k, gamma = 5, 4, 4e-3
+    p = W.data_loading(W.QUBIT, n, k, seed=91)
+    sim = _sim(p, 91)
+    seen_drop = False
+    for traj in range(6):
+        ga, gb, gh, gz = sim.dump_state("pruned", traj, gamma)
+        ta, tb, th, tz = sim.dump_state("pruned", traj, gamma, w_max=wmax)
+        full = {(int(a), int(b), int(h)): z for a, b, h, z in zip(ga, gb, gh, gz)}
+        trunc = {(int(a), int(b), int(h)): z for a, b, h, z in zip(ta, tb, th, tz)}
+        for key, z in full.items():
+            a, b, h = key
+            ideal = int(p.bus[list(p.addr).index(a)]) ^ int(p.memory[a])
+            keep = h != 0 or bin(b ^ ideal).count("1") <= wmax or key in trunc
+            if not keep:
+                seen_drop = True
+                continue
+            assert key in trunc and abs(trunc[key] - z) < TOL
+        assert set(trunc) <= set(full)
+    sim.dump_state("pruned", 0, gamma, w_max=-1)
+    assert seen_drop
+    sim.close()

@@ -119,3 +119,22 @@ def test_no_jump_trajectories_equal_F0(enc, n, k, gamma):
     assert len(nj) > 20
     assert np.all(nj["q_ground"] == 1)
     assert np.max(np.abs(nj["fidelity"] - F0)) < 1e-13
+
+
+@pytest.mark.parametrize("n,k,gamma,wmax", [(6, 4, 1e-3, 0), (8, 3, 1e-4, 1), (10, 8, 1e-3, 2), (4, 2, 1e-2, 0)])
+def test_low_weight_truncation_bound(n, k, gamma, wmax):
+    """Sec. IV cost discussion: each unit of Hamming weight costs beta/alpha
+    = O(n gamma) in amplitude, so the words dropped at weight > w_max carry
+    relative amplitudes at most (n gamma)^(w_max + 1), and the kept words'
+    norm deficit is the binomial tail of the Eq. (11) amplitudes."""
+    a = math.sqrt(1 - gamma)
+    al, be = cf.alpha(a, 2 * n), cf.beta(a, 2 * n)
+    assert be / al <= n * gamma
+    top = cf.hamming_amplitude(0, 0, k, a, n)
+    drop = [cf.hamming_amplitude(c, 0, k, a, n) for c in range(1 << k) if bin(c).count("1") > wmax]
+    assert max(abs(x) for x in drop) / abs(top) <= (n * gamma) ** (wmax + 1)
+    tail = sum(x * x for x in drop)
+    want = sum(math.comb(k, w) * al ** (2 * (k - w)) * be ** (2 * w) for w in range(wmax + 1, k + 1))
+    assert abs(tail - want) <= 1e-15 * max(1.0, want)
+    total = sum(cf.hamming_amplitude(c, 0, k, a, n) ** 2 for c in range(1 << k))
+    assert abs(total - (al * al + be * be) ** k) < 1e-14
