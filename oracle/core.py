@@ -41,7 +41,8 @@ class _Problem(C.Structure):
 class _Hist(C.Structure):
     _fields_ = [("ncand", C.c_int32), ("cand_slice", C.c_void_p), ("cand_site", C.c_void_p),
                 ("aux_u", C.c_void_p), ("final_u", C.c_double),
-                ("nflip", C.c_int32), ("flip_slice", C.c_void_p), ("flip_site", C.c_void_p)]
+                ("nflip", C.c_int32), ("flip_slice", C.c_void_p), ("flip_site", C.c_void_p),
+                ("eps", C.c_double)]
 
 
 TRAJ_DTYPE = np.dtype([("fidelity", "f8"), ("fidelity_unsampled", "f8"), ("p_ground", "f8"),
@@ -58,6 +59,8 @@ def lib():
         L = C.CDLL(build())
         vp, i32, u64, f64 = C.c_void_p, C.c_int32, C.c_uint64, C.c_double
         L.oracle_run.argtypes = [vp, u64, u64, i32, vp, i32, vp]
+        L.oracle_run_eps.argtypes = [vp, u64, u64, i32, vp, f64, i32, vp]
+        L.oracle_sample_paulis.argtypes = [vp, u64, u64, f64, vp, vp, vp, i32, vp]
         L.oracle_run_one.argtypes = [vp, u64, u64, f64, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_sample_faults.argtypes = [vp, u64, u64, f64, vp, vp, i32, vp, vp, vp, vp]
         L.oracle_schedule.argtypes = [i32, i32, vp, vp, vp, i32, vp]
@@ -108,13 +111,14 @@ def _check(rc, what):
         raise OracleError(f"{what}: oracle error {rc}")
 
 
-def run(prob, seed: int, traj0: int, gammas, nthreads: int | None = None) -> np.ndarray:
-    """Full evolution of trajectories traj0 .. traj0+len(gammas)-1."""
+def run(prob, seed: int, traj0: int, gammas, nthreads: int | None = None, eps: float = 0.0) -> np.ndarray:
+    """Full evolution of trajectories traj0 .. traj0+len(gammas)-1; eps is the
+    depolarizing strength per (slice, site), eps < 0 meaning eps = gamma."""
     g = np.ascontiguousarray(gammas, dtype=np.float64)
     out = np.zeros(len(g), dtype=TRAJ_DTYPE)
     b = _Bound(prob)
     nt = nthreads or os.cpu_count() or 1
-    _check(lib().oracle_run(b.ref, seed, traj0, len(g), _ptr(g), nt, _ptr(out)), "oracle_run")
+    _check(lib().oracle_run_eps(b.ref, seed, traj0, len(g), _ptr(g), float(eps), nt, _ptr(out)), "oracle_run")
     return out
 
 
@@ -137,11 +141,16 @@ class Dump:
     amp: np.ndarray        # normalised
 
 
-def run_one(prob, seed: int, traj: int, gamma: float, hist: History | None = None, cap: int = 1 << 20):
+def run_one(prob, seed: int, traj: int, gamma: float, hist: History | None = None, cap: int = 1 << 20,
+            eps: float = 0.0):
     b = _Bound(prob)
     T = 6 * prob.n + 2 * prob.k
     keep = []
     hp = None
+    if hist is None and eps != 0.0:                # sampled history with depolarizing events
+        h = _Hist(0, None, None, None, math.nan, 0, None, None, float(eps))
+        keep.append(h)
+        hp = C.byref(h)
     if hist is not None:
         cs = np.ascontiguousarray(hist.cand_slice, dtype=np.int32)
         cq = np.ascontiguousarray(hist.cand_site, dtype=np.int32)
@@ -187,6 +196,24 @@ def run_one(prob, seed: int, traj: int, gamma: float, hist: History | None = Non
             ne = int(dn[r])
             configs.append(tuple((int(ds[r * maxe + e]), int(dl[r * maxe + e])) for e in range(ne)))
         return out[0], Dump(da[:m].copy(), db[:m].copy(), configs, dr[:m] + 1j * di[:m])
+
+
+def sample_paulis(prob, seed: int, traj: int, eps: float):
+    """Depolarizing fault events (slice, site, operator index) of one trajectory."""
+    b = _Bound(prob)
+    cap = 1 << 16
+    while True:
+        sl = np.zeros(cap, np.int32)
+        st = np.zeros(cap, np.int32)
+        ty = np.zeros(cap, np.int32)
+        ne = C.c_int32(0)
+        rc = lib().oracle_sample_paulis(b.ref, seed, traj, float(eps), _ptr(sl), _ptr(st), _ptr(ty), cap, C.byref(ne))
+        if rc == E_CAP:
+            cap = int(ne.value) + 16
+            continue
+        _check(rc, "oracle_sample_paulis")
+        m = int(ne.value)
+        return sl[:m].copy(), st[:m].copy(), ty[:m].copy()
 
 
 def sample_faults(prob, seed: int, traj: int, gamma: float):

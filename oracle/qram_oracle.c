@@ -61,6 +61,17 @@
  *      floor(acc * q_m / 2^64) > u (and acc takes that value); so
  *      P(gap >= j) = (1 - gamma)^j up to 64-bit rounding.  A gap that
  *      reaches the block end ends the block.  gamma with thr = 0 draws none.
+ *   S4b depolarizing faults (Sec. II.B; App. A): every (slice, site) pair
+ *      carries a fault with probability eps, drawn like the FAULT stream but
+ *      on stream PAULI=4; the operator of the event found by draw r of block
+ *      g is floor(word0 * ntypes / 2^32) of counter (g, r | 5 << 24, ...):
+ *      qubits Z, X, XZ (ntypes 3), qutrits the eight Weyl operators X^a Z^b
+ *      in row order of (a, b) (ntypes 8).  Events act after the gates (and
+ *      the walls) of their slice and before its damping layer, and mark
+ *      bad(v) like damping candidates.  Reading: every tree site is active
+ *      in every slice (App. C's "routing front" is not defined in the
+ *      paper); parity unpinned against Tab. IV's Pauli row, pinned against
+ *      the density-matrix oracle under the same reading.
  *   S5 canonical mask order: the empty mask first, then masks as sorted
  *      lists of (site, level) compared lexicographically, a proper prefix
  *      first; the selected J is the first mask whose cumulative weight
@@ -101,6 +112,7 @@ typedef struct {
     double final_u;                          /* NaN = use the FINAL stream */
     int32_t nflip;
     const int32_t *flip_slice, *flip_site;   /* X flips after the gates (qubit) */
+    double eps;                              /* depolarizing strength (sampled events) */
 } ohist;
 
 typedef struct {
@@ -633,16 +645,27 @@ uint32_t oracle_gap(uint64_t u, double gamma)
     return gap_of(u, q);
 }
 
-/* candidates of one trajectory in (slice, site) order; returns count */
+/* fault positions of one stream in (slice, site) order; with ct, also each
+ * event's operator index (S4b); returns count */
+static int sample_stream(const osched *S, uint64_t seed, uint64_t traj, double gamma, uint32_t stream,
+                         uint32_t ntypes, int32_t **cs, int32_t **cq, int32_t **ct, int *nc_out);
+
 static int sample_candidates(const osched *S, uint64_t seed, uint64_t traj, double gamma,
                              int32_t **cs, int32_t **cq, int *nc_out)
 {
+    return sample_stream(S, seed, traj, gamma, 1u, 0u, cs, cq, NULL, nc_out);
+}
+
+static int sample_stream(const osched *S, uint64_t seed, uint64_t traj, double gamma, uint32_t stream,
+                         uint32_t ntypes, int32_t **cs, int32_t **cq, int32_t **ct, int *nc_out)
+{
     uint64_t thr = oracle_threshold(gamma);
     int cap = 256, nc = 0;
-    int32_t *a = malloc(cap * sizeof(int32_t)), *b = malloc(cap * sizeof(int32_t));
-    if (!a || !b) { free(a); free(b); return OR_E_OOM; }
+    int32_t *a = malloc(cap * sizeof(int32_t)), *b = malloc(cap * sizeof(int32_t)), *c = malloc(cap * sizeof(int32_t));
+    if (!a || !b || !c) { free(a); free(b); free(c); return OR_E_OOM; }
     *cs = a; *cq = b; *nc_out = 0;
-    if (thr == 0) return 0;
+    if (ct) *ct = c;
+    if (thr == 0) { if (!ct) free(c); return 0; }
     uint64_t q[OR_GAP_BITS];
     gap_powers(thr, q);
     const uint64_t M = 2 * (((uint64_t)1 << S->n) - 1), X = (uint64_t)(S->T - 1) * M;
@@ -650,7 +673,7 @@ static int sample_candidates(const osched *S, uint64_t seed, uint64_t traj, doub
         uint64_t pos = g * OR_GAP_BLOCK, end = pos + OR_GAP_BLOCK < X ? pos + OR_GAP_BLOCK : X;
         uint32_t o[4] = {0, 0, 0, 0};
         for (uint32_t r = 0;; r++) {
-            if ((r & 1u) == 0) draw(seed, (uint32_t)g, r >> 1, 1u, traj, o);
+            if ((r & 1u) == 0) draw(seed, (uint32_t)g, r >> 1, stream, traj, o);
             uint64_t u = (r & 1u) ? ((uint64_t)o[2] | ((uint64_t)o[3] << 32)) : ((uint64_t)o[0] | ((uint64_t)o[1] << 32));
             uint32_t G = gap_of(u, q);
             if ((uint64_t)G >= end - pos) break;
@@ -658,14 +681,22 @@ static int sample_candidates(const osched *S, uint64_t seed, uint64_t traj, doub
             if (nc == cap) {
                 cap *= 2;
                 int32_t *a2 = realloc(a, cap * sizeof(int32_t)), *b2 = realloc(b, cap * sizeof(int32_t));
-                if (!a2 || !b2) { free(a2 ? a2 : a); free(b2 ? b2 : b); return OR_E_OOM; }
-                a = a2; b = b2;
+                int32_t *c2 = realloc(c, cap * sizeof(int32_t));
+                if (!a2 || !b2 || !c2) { free(a2 ? a2 : a); free(b2 ? b2 : b); free(c2 ? c2 : c); return OR_E_OOM; }
+                a = a2; b = b2; c = c2;
             }
-            a[nc] = (int32_t)(1 + pos / M); b[nc] = (int32_t)(pos % M); nc++;
+            a[nc] = (int32_t)(1 + pos / M); b[nc] = (int32_t)(pos % M);
+            if (ntypes) {                               /* the event's operator: multiply-shift of a fresh word */
+                uint32_t w[4];
+                draw(seed, (uint32_t)g, r, 5u, traj, w);
+                c[nc] = (int32_t)(((uint64_t)w[0] * ntypes) >> 32);
+            }
+            nc++;
             pos += 1;
         }
     }
     *cs = a; *cq = b; *nc_out = nc;
+    if (ct) *ct = c; else free(c);
     return 0;
 }
 
@@ -705,6 +736,24 @@ int oracle_sample_faults(const oproblem *P, uint64_t seed, uint64_t traj, double
     return nc > cap ? OR_E_CAP : OR_OK;
 }
 
+/* depolarizing fault events of one trajectory (S4b): slice, site, operator */
+int oracle_sample_paulis(const oproblem *P, uint64_t seed, uint64_t traj, double eps, int32_t *out_slice,
+                         int32_t *out_site, int32_t *out_type, int32_t cap, int32_t *nev)
+{
+    osched *S = malloc(sizeof(osched));
+    if (!S) return OR_E_OOM;
+    int rc = build_schedule(P->n, P->k, S);
+    if (rc) { free(S); return rc; }
+    int32_t *ps, *pq, *pt; int np;
+    rc = sample_stream(S, seed, traj, eps, 4u, P->encoding == ENC_QUBIT ? 3u : 8u, &ps, &pq, &pt, &np);
+    free(S);
+    if (rc) return rc;
+    for (int e = 0; e < np && e < cap; e++) { out_slice[e] = ps[e]; out_site[e] = pq[e]; out_type[e] = pt[e]; }
+    *nev = np;
+    free(ps); free(pq); free(pt);
+    return np > cap ? OR_E_CAP : OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* one trajectory: full evolution of every branch                           */
 
@@ -716,8 +765,26 @@ static int check_problem(const oproblem *P)
     return 0;
 }
 
+/* depolarizing fault (S4b): operator index t -> X^a Z^b with (a, b) the
+ * (t+1)-th pair of {0..d-1}^2 in row order (qubit: Z, X, XZ; qutrit: the
+ * eight Weyl operators), X|j> = |j+1 mod d>, Z|j> = w^j |j>, w = exp(2 pi i/d);
+ * applied to one site of one component */
+static int apply_weyl(ocomp *x, uint32_t site, int qubit, int t)
+{
+    const int d = qubit ? 2 : 3;
+    const int a = (t + 1) / d, b = (t + 1) % d;
+    const int j = get_lvl(x, site);                 /* qubit: LV_W = 0, LV_L = 1 */
+    const int m = (b * j) % d;
+    if (m) {                                        /* w^m: -1 (qubit); -1/2 +- i sqrt(3)/2 (qutrit) */
+        const double c = qubit ? -1.0 : -0.5, sn = qubit ? 0.0 : (m == 1 ? 0.5 : -0.5) * sqrt(3.0);
+        const double re = x->re * c - x->im * sn, im = x->re * sn + x->im * c;
+        x->re = re; x->im = im;
+    }
+    return set_lvl(x, site, (j + a) % d);
+}
+
 static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t traj, double gamma,
-                    const ohist *H, otraj_out *out, ostate *dump, uint8_t *occupancy)
+                    double eps, const ohist *H, otraj_out *out, ostate *dump, uint8_t *occupancy)
 {
     int n = S->n, k = S->k, T = S->T, qubit = P->encoding == ENC_QUBIT;
     memset(out, 0, sizeof(*out));
@@ -734,11 +801,19 @@ static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t 
         }
     } else if ((rc = sample_candidates(S, seed, traj, gamma, &cs, &cq, &nc))) return rc;
     out->ncand = (uint32_t)nc;
+    /* depolarizing fault events (S4b) */
+    int32_t *ps = NULL, *pq = NULL, *pt = NULL; int np = 0;
+    if (eps > 0.0 && (rc = sample_stream(S, seed, traj, eps, 4u, qubit ? 3u : 8u, &ps, &pq, &pt, &np))) {
+        free(cs); free(cq); return rc;
+    }
 
     uint8_t *badmap = malloc(1u << n);
-    if (!badmap) { free(cs); free(cq); return OR_E_OOM; }
-    classify(P, n, cq, nc, badmap, &out->bad, &out->ref);
-    free(badmap);
+    int32_t *allq = malloc((size_t)(nc + np + 1) * sizeof(int32_t));
+    if (!badmap || !allq) { free(badmap); free(allq); free(cs); free(cq); free(ps); free(pq); free(pt); return OR_E_OOM; }
+    for (int c = 0; c < nc; c++) allq[c] = cq[c];
+    for (int e = 0; e < np; e++) allq[nc + e] = pq[e];            /* every fault marks, whatever its type */
+    classify(P, n, allq, nc + np, badmap, &out->bad, &out->ref);
+    free(badmap); free(allq);
 
     /* initial sparse state: one component per input column, tree in ground */
     ostate st = { 0 };
@@ -762,6 +837,10 @@ static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t 
                         uint32_t q = (uint32_t)H->flip_site[f];
                         if ((rc = set_lvl(&st.c[r], q, get_lvl(&st.c[r], q) ? LV_W : LV_L))) goto fail;
                     }
+        for (int e = 0; e < np; e++)                  /* depolarizing faults of this slice */
+            if (ps[e] == s)
+                for (size_t r = 0; r < st.n; r++)
+                    if ((rc = apply_weyl(&st.c[r], (uint32_t)pq[e], qubit, pt[e]))) goto fail;
         if (occupancy)
             for (size_t r = 0; r < st.n; r++)
                 for (int e = 0; e < st.c[r].ne; e++) occupancy[(size_t)s * S->M + st.c[r].site[e]] = 1;
@@ -819,10 +898,10 @@ static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t 
         out->fidelity_unsampled = W > 0 ? ov / W : 0.0;
     }
     if (dump) { *dump = st; st.c = NULL; }
-    free(st.c); free(cs); free(cq);
+    free(st.c); free(cs); free(cq); free(ps); free(pq); free(pt);
     return 0;
 fail:
-    free(st.c); free(cs); free(cq);
+    free(st.c); free(cs); free(cq); free(ps); free(pq); free(pt);
     return rc;
 }
 
@@ -831,7 +910,7 @@ fail:
 
 typedef struct {
     const oproblem *P; const osched *S; uint64_t seed, traj0; int ntraj;
-    const double *gamma; otraj_out *out; int next; int rc;
+    const double *gamma; double eps; otraj_out *out; int next; int rc;
     pthread_mutex_t mu;
 } ojob;
 
@@ -843,14 +922,26 @@ static void *worker(void *arg)
         int t = J->next++;
         pthread_mutex_unlock(&J->mu);
         if (t >= J->ntraj) break;
-        int rc = run_traj(J->P, J->S, J->seed, J->traj0 + (uint64_t)t, J->gamma[t], NULL, &J->out[t], NULL, NULL);
+        const double e = J->eps < 0.0 ? J->gamma[t] : J->eps;       /* eps < 0: eps = gamma */
+        int rc = run_traj(J->P, J->S, J->seed, J->traj0 + (uint64_t)t, J->gamma[t], e, NULL, &J->out[t], NULL, NULL);
         if (rc) { pthread_mutex_lock(&J->mu); J->rc = rc; pthread_mutex_unlock(&J->mu); }
     }
     return NULL;
 }
 
+int oracle_run_eps(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj, const double *gamma,
+                   double eps, int32_t nthreads, otraj_out *out);
+
 int oracle_run(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj,
                const double *gamma, int32_t nthreads, otraj_out *out)
+{
+    return oracle_run_eps(P, seed, traj0, ntraj, gamma, 0.0, nthreads, out);
+}
+
+/* eps: depolarizing strength per (slice, site); eps < 0 takes eps = gamma
+ * per trajectory (the paper's benchmark setting) */
+int oracle_run_eps(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj, const double *gamma,
+                   double eps, int32_t nthreads, otraj_out *out)
 {
     int rc = check_problem(P);
     if (rc) return rc;
@@ -860,7 +951,8 @@ int oracle_run(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj,
     for (int t = 0; t < ntraj; t++) if (!(gamma[t] >= 0.0 && gamma[t] < 1.0)) { free(S); return OR_E_ARG; }
     ojob J;
     memset(&J, 0, sizeof(J));
-    J.P = P; J.S = S; J.seed = seed; J.traj0 = traj0; J.ntraj = ntraj; J.gamma = gamma; J.out = out;
+    if (!(eps < 1.0)) { free(S); return OR_E_ARG; }
+    J.P = P; J.S = S; J.seed = seed; J.traj0 = traj0; J.ntraj = ntraj; J.gamma = gamma; J.eps = eps; J.out = out;
     pthread_mutex_init(&J.mu, NULL);
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
@@ -885,7 +977,7 @@ int oracle_run_one(const oproblem *P, uint64_t seed, uint64_t traj, double gamma
     if (!S) return OR_E_OOM;
     if ((rc = build_schedule(P->n, P->k, S))) { free(S); return rc; }
     ostate st = { 0 };
-    rc = run_traj(P, S, seed, traj, gamma, H, out, &st, NULL);
+    rc = run_traj(P, S, seed, traj, gamma, H ? H->eps : 0.0, H, out, &st, NULL);
     free(S);
     if (rc) return rc;
     double W = 0.0;
@@ -916,7 +1008,7 @@ int oracle_occupancy(const oproblem *P, uint8_t *occ)
     int32_t dummy = 0;
     H.cand_slice = &dummy; H.cand_site = &dummy; H.ncand = 0; H.final_u = 0.0;
     otraj_out o;
-    rc = run_traj(P, S, 0, 0, 0.0, &H, &o, NULL, occ);
+    rc = run_traj(P, S, 0, 0, 0.0, 0.0, &H, &o, NULL, occ);
     free(S);
     return rc;
 }
