@@ -206,6 +206,19 @@ int qram_dump_state(qram_sim_t *sim, int mode, uint64_t traj, double gamma, uint
                     uint32_t *addr, uint32_t *bus, uint64_t *config_hash, double *re, double *im,
                     uint32_t *count);
 
+/* Depolarizing faults on top of the amplitude damping (Sec. II.B; App. A;
+ * the paper's benchmark setting eps = gamma): every (slice, site) pair of the
+ * tree carries, with probability eps, one of the non-identity Pauli
+ * operators Z, X, XZ (qubit) or the eight Weyl operators X^a Z^b (qutrit),
+ * uniformly, applied after the slice's gates and before its damping layer.
+ * Events are drawn on their own fault stream (stream 4, operator words on
+ * stream 5; see "Random numbers") and mark bad(v) like damping candidates.
+ * eps_equals_gamma != 0 ignores eps and takes each trajectory's damping rate.
+ * With eps > 0 every branch is evolved explicitly in both modes (faults on
+ * idle sites reach the good branches, which the closed forms of the damping
+ * path do not describe).  0 <= eps < 1, else QRAM_E_ARG.  Default 0. */
+int qram_set_depolarizing(qram_sim_t *sim, double eps, int eps_equals_gamma);
+
 /* Low-weight truncation of the predicted good branches in qram_dump_state
  * (Sec. IV, cost discussion after Eq. (22)): each good branch ends in a
  * superposition over all 2^k output words whose amplitude falls by

@@ -92,6 +92,7 @@ def load_library(build_if_missing: bool = True):
     L.qram_launch_count.restype = u64
     L.qram_work_counters.argtypes = [vp, vp, C.c_int]
     L.qram_set_dump_weight.argtypes = [vp, C.c_int]
+    L.qram_set_depolarizing.argtypes = [vp, C.c_double, C.c_int]
     L.qram_server_create.argtypes = [C.c_size_t, C.c_int, u32, C.POINTER(vp)]
     L.qram_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
     L.qram_server_estimate.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
@@ -249,6 +250,12 @@ class QramSim:
             _check(rc, "qram_dump_state")
             m = cnt.value
             return addr[:m], bus[:m], hsh[:m], re[:m] + 1j * im[:m]
+
+    def set_depolarizing(self, eps: float, eps_equals_gamma: bool = False):
+        """Depolarizing faults of strength eps per (slice, site) on top of the
+        damping (eps_equals_gamma: each trajectory's damping rate)."""
+        _check(self.lib.qram_set_depolarizing(self.h, float(eps), 1 if eps_equals_gamma else 0),
+               "qram_set_depolarizing")
 
     def set_gamma_bound(self, gmax: float):
         _check(self.lib.qram_set_gamma_bound(self.h, gmax), "qram_set_gamma_bound")

@@ -48,6 +48,8 @@ struct qram_sim {
     int scr_threads = 0;        // variant the scratch was laid out for
     double gamma_bound = 0.0;
     int dump_wmax = -1;         // low-weight truncation of the dumped good branches
+    double eps = 0.0;           // depolarizing strength
+    int eps_gamma = 0;          // the strength of each trajectory is its damping rate
 };
 
 namespace {
@@ -153,7 +155,7 @@ void cand_caps(int n, int k, double gmax, int threads, uint32_t *cand_cap, uint3
 }
 
 struct Layout {
-    size_t o_cand, o_seg, o_expl, o_cs, o_exc, o_selk, o_selw, total;
+    size_t o_cand, o_pev, o_seg, o_expl, o_cs, o_exc, o_selk, o_selw, total;
     uint32_t cc, sc, ecap, selseg;
 };
 
@@ -164,6 +166,7 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax, i
     const int NWARP = threads / 32;
     size_t off = 0;
     L.o_cand = off; off = align_up(off + slots * L.cc * 4);
+    L.o_pev = off; off = align_up(off + slots * L.cc * 4);
     L.o_seg = off; off = align_up(off + slots * NWARP * (size_t)L.sc * 4);
     L.o_expl = off; off = align_up(off + slots * (size_t)D * 4);
     L.o_cs = off; off = align_up(off + slots * (size_t)L.ecap * 16);
@@ -180,6 +183,7 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax, i
 }
 
 int ensure_scratch(qram_sim *S, double gmax) {
+    gmax = std::max(gmax, S->eps);                     // depolarizing events share the candidate capacity
     const Layout L = scratch_layout(S->enc, S->n, S->k, S->D, (size_t)S->slots, gmax, S->threads);
     if (S->scratch && S->scr_threads == S->threads && S->scr.cand_cap >= L.cc && S->scr.seg_cap >= L.sc &&
         S->scr.ecap >= L.ecap)
@@ -192,6 +196,7 @@ int ensure_scratch(qram_sim *S, double gmax) {
     S->scratch = p;
     S->scratch_bytes = L.total;
     S->scr.cand = (uint32_t *)(b + L.o_cand);
+    S->scr.pev = (uint32_t *)(b + L.o_pev);
     S->scr.wseg = (uint32_t *)(b + L.o_seg);
     S->scr.expl = (uint32_t *)(b + L.o_expl);
     S->scr.cs = (uint4 *)(b + L.o_cs);
@@ -231,6 +236,8 @@ Params base_params(qram_sim *S) {
     P.work = S->d_work;
     P.w2u = S->d_w2u;
     P.col_of = S->d_colof;
+    P.eps = S->eps;
+    P.eps_gamma = S->eps_gamma;
     P.ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(S->d_work) + 32);
     std::memcpy(P.ops, S->ops, sizeof(P.ops));
     std::memcpy(P.occ2, S->occ2, sizeof(P.occ2));
@@ -372,6 +379,7 @@ size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, int t
     if (base) {
         char *b = (char *)base;
         scr->cand = (uint32_t *)(b + L.o_cand);
+        scr->pev = (uint32_t *)(b + L.o_pev);
         scr->wseg = (uint32_t *)(b + L.o_seg);
         scr->expl = (uint32_t *)(b + L.o_expl);
         scr->cs = (uint4 *)(b + L.o_cs);
@@ -753,6 +761,13 @@ int qram_sync(qram_sim_t *S) {
 }
 
 uint64_t qram_launch_count(const qram_sim_t *S) { return S ? S->launches : 0; }
+
+int qram_set_depolarizing(qram_sim_t *S, double eps, int eps_equals_gamma) {
+    if (!S || !(eps >= 0.0 && eps < 1.0)) return QRAM_E_ARG;
+    S->eps = eps;
+    S->eps_gamma = eps_equals_gamma ? 1 : 0;
+    return QRAM_OK;
+}
 
 int qram_set_dump_weight(qram_sim_t *S, int w_max) {
     if (!S || w_max < -1) return QRAM_E_ARG;

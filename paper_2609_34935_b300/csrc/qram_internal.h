@@ -38,6 +38,7 @@ struct SliceOps {
 // Per-CTA-slot scratch (device), sized at launch for the worst case.
 struct Scratch {
     uint32_t *cand;      // [slots][cand_cap]  packed (slice << 16) | site
+    uint32_t *pev;       // [slots][cand_cap]  depolarizing events (slice << 18) | (operator << 15) | site
     uint32_t *wseg;      // [slots][nwarps][seg_cap] per-warp candidate segments
     uint32_t *expl;      // [slots][D] explicit input columns
     // [slots][ecap] packed components, one 16-byte load/store each:
@@ -101,6 +102,8 @@ struct Params {
     const double *w2u;             // device scalar: |c|^2 (times 2^-k for qubits) when every column shares it, else 0
     const uint64_t *traj0_dev;     // if non-null, the first trajectory index is read here (graph replays)
     const uint32_t *col_of;        // qubit input over every address (D = 2^n): column of each address, else null
+    double eps;                    // depolarizing strength per (slice, site)
+    int eps_gamma;                 // nonzero: the strength of each trajectory is its damping rate
     unsigned long long *ctr;       // if non-null: work counters (draws, explicit comp-slices, lazy branch-epochs,
                                    // explicit comp-epochs), added once per trajectory
     int hist_pad;                  // bins per exponent histogram (dynamic shared memory: 3 of them)

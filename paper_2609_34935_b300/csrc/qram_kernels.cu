@@ -140,6 +140,7 @@ struct Smem {
     uint32_t badbits[512];         // 2^14 addresses
     uint32_t candbits[1024];       // M <= 32766 sites, candidates of the current slice
     uint32_t slice_off[kMaxT + 2];
+    uint32_t pslice_off[kMaxT + 2];   // per-slice offsets of the depolarizing events
     double powlo[64], powhi[64];   // a^j, a^(64 j)
     double redA[NW], redB[NW], redC[NW];
     uint32_t scanw[NW];
@@ -926,6 +927,44 @@ __device__ __noinline__ CompR clear_site(CompR c, uint16_t *xs, const Ctx C, uin
     return c;
 }
 
+// A depolarizing fault on one site of one component: operator t is X^a Z^b
+// with (a, b) the (t+1)-th pair of {0..d-1}^2 in row order (qubit: Z, X,
+// XZ; qutrit: the eight Weyl operators), X|j> = |j+1 mod d>, Z|j> = w^j|j>.
+// The phase goes to sign: -1 (qubit) or w^sign, w = exp(2 pi i / 3)
+// (qutrit, sign in 0..2).  Path-A sites change in registers; other sites
+// through the generic representation.  By value (callers keep registers);
+// *okp = 0 if a capacity was exceeded.
+__device__ __noinline__ CompR pauli_site(CompR c, uint16_t *xs, const Ctx C, uint32_t site, uint32_t t, int *okp) {
+    *okp = 1;
+    const bool qubit = C.enc == QRAM_QUBIT;
+    const int d = qubit ? 2 : 3;
+    const int a = ((int)t + 1) / d, bz = ((int)t + 1) % d;
+    const uint32_t iB = b_addr(c, C);
+    int bpos;
+    const int where = locate(c, xs, C, iB, site, bpos);
+    int j = 0;                                        // current level: 0 ground, 1 L / excited, 2 R
+    if (where == 0) j = (!qubit && ((c.pwR >> bpos) & 1u)) ? 2 : 1;
+    else if (where == 1) j = 1;
+    else if (where == 2) j = (xs[bpos] & 1u) ? 2 : 1;
+    const int m = (bz * j) % d;
+    if (m) c.sign = qubit ? (c.sign ^ 1u) : ((c.sign + (uint32_t)m) % 3u);
+    const int nj = (j + a) % d;
+    if (nj == j) return c;
+    const uint32_t u = site >> 1;
+    const int L = layer_of(u);
+    if (L < C.n && u == path_node(C.i, C.n, L)) {
+        const int b = 2 * L + (int)(site & 1u);
+        c.pw = (c.pw & ~(1u << b)) | ((nj ? 1u : 0u) << b);
+        c.pwR = (c.pwR & ~(1u << b)) | ((nj == 2 ? 1u : 0u) << b);
+        return c;
+    }
+    Ents E;
+    to_ents(c, xs, C, E);
+    if (!ent_set(E, site, nj)) { *okp = 0; return c; }
+    if (!from_ents(c, xs, C, E)) *okp = 0;
+    return c;
+}
+
 // FNV-1a over the sorted (site << 2 | level) list; 0 for the ground state
 __device__ __noinline__ uint64_t config_hash(const CompR c, const uint16_t *xs, const Ctx C) {
     if (is_ground(c)) return 0;
@@ -954,7 +993,7 @@ __device__ __forceinline__ void unpack(const uint4 v, bool qubit, CompR &c, uint
     c.pwB = qubit ? v.y : 0u;
     c.e = (int32_t)(v.z & 0xFFFu);
     c.cb = (v.z >> 12) & 0xFFu;
-    c.sign = (v.z >> 20) & 1u;
+    c.sign = ((v.z >> 20) & 1u) | (((v.w >> 28) & 1u) << 1);
     c.nexc = (v.z >> 21) & 0x3Fu;
     c.ldiv = (int32_t)((v.z >> 27) & 0xFu) - 1;
     col = v.w & 0x3FFFu;
@@ -967,7 +1006,7 @@ __device__ __forceinline__ uint4 pack(const CompR &c, bool qubit, uint32_t col, 
     v.y = qubit ? c.pwB : c.pwR;
     v.z = ((uint32_t)c.e & 0xFFFu) | ((c.cb & 0xFFu) << 12) | ((c.sign & 1u) << 20) | ((c.nexc & 0x3Fu) << 21) |
           ((uint32_t)(c.ldiv + 1) << 27);
-    v.w = col | (addr << 14);
+    v.w = col | (addr << 14) | (((c.sign >> 1) & 1u) << 28);
     return v;
 }
 
@@ -1087,6 +1126,112 @@ __device__ __forceinline__ int data_exposure(const Params &P, uint32_t cw, int s
 }
 
 // ---------------------------------------------------------------------------
+// One fault stream of a trajectory by geometric gaps over the (slice, site)
+// pairs, in blocks of kGapBlock: each warp takes a contiguous run of blocks,
+// one block per lane per round, counts its events, then writes them after
+// those of the lower lanes, and the warp segments are concatenated into dst
+// in (slice, site) order.  Events are packed (slice << 16) | site, or, with
+// operator types (ntypes > 0), (slice << 18) | (type << 15) | site, the type
+// being floor(word0 * ntypes / 2^32) of counter (g, r | 5 << 24).  Returns
+// the number of events (block-uniform); sets QRAM_E_CAP and returns 0 on
+// overflow.
+template <int NT>
+__device__ uint32_t sample_stream(const Params &P, Smem<NT> &S, uint64_t thr, uint32_t stream, uint32_t ntypes,
+                                  uint64_t traj, uint32_t *dst) {
+    constexpr int NW = NT / 32;
+    const Scratch &scr = P.scr;
+    const size_t slot = blockIdx.x;
+    const int T = P.T;
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    const uint32_t tl = (uint32_t)traj, th = (uint32_t)(traj >> 32);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        S.gq[0] = 0ull - thr;                                  // 2^64 - thr
+        for (int m = 0; m + 1 < kGapBits; ++m) S.gq[m + 1] = __umul64hi(S.gq[m], S.gq[m]);
+    }
+    __syncthreads();
+    const uint32_t M = 2u * (uint32_t)P.nodes, X = (uint32_t)(T - 1) * M;
+    const uint32_t nblk = (X + kGapBlock - 1) / kGapBlock;
+    const uint32_t per = (nblk + NW - 1) / NW;
+    const uint32_t g0 = w * per, g1 = min(nblk, g0 + per);
+    uint32_t *seg = scr.wseg + (slot * NW + w) * scr.seg_cap;
+    uint32_t cnt = 0, draws = 0;
+    bool overflow = false;
+    for (uint32_t gb = g0; gb < g1; gb += 32) {
+        const uint32_t g = gb + lane;
+        uint32_t mine = 0, off = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+                uint32_t x = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                    if (lane >= (uint32_t)o) x += y;
+                }
+                off = cnt + x - mine;
+                cnt += __shfl_sync(0xFFFFFFFFu, x, 31);
+                if (mine == 0) continue;
+            }
+            if (g >= g1) continue;
+            uint32_t pos = g * kGapBlock;
+            const uint32_t end = min(pos + kGapBlock, X);
+            uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0, k = 0;
+            for (uint32_t r = 0;; ++r) {
+                if ((r & 1u) == 0) {
+                    o0 = g; o1 = (r >> 1) | (stream << 24); o2 = tl; o3 = th;
+                    philox(o0, o1, o2, o3, k0, k1);
+                }
+                const uint64_t u = (r & 1u) ? ((uint64_t)o2 | ((uint64_t)o3 << 32)) : ((uint64_t)o0 | ((uint64_t)o1 << 32));
+                uint64_t acc = ~0ull;
+                uint32_t G = 0;
+#pragma unroll
+                for (int m = kGapBits - 1; m >= 0; --m) {
+                    const uint64_t t = __umul64hi(acc, S.gq[m]);
+                    if (t > u) { acc = t; G += 1u << m; }
+                }
+                if (G >= end - pos) { if (pass == 0) draws += r + 1; break; }
+                pos += G;
+                if (pass == 0) ++mine;
+                else {
+                    const uint32_t q = off + k++;
+                    uint32_t v;
+                    if (ntypes) {
+                        uint32_t w0 = g, w1 = r | (5u << 24), w2 = tl, w3 = th;
+                        philox(w0, w1, w2, w3, k0, k1);
+                        const uint32_t ty = (uint32_t)(((uint64_t)w0 * ntypes) >> 32);
+                        v = ((1u + pos / M) << 18) | (ty << 15) | (pos % M);
+                    } else {
+                        v = ((1u + pos / M) << 16) | (pos % M);
+                    }
+                    if (q < scr.seg_cap) seg[q] = v;
+                    else overflow = true;
+                }
+                ++pos;
+            }
+        }
+    }
+    overflow = __any_sync(0xFFFFFFFFu, overflow);
+    draws = __reduce_add_sync(0xFFFFFFFFu, draws);
+    if (lane == 0) { S.wcount[w] = overflow ? 0xFFFFFFFFu : cnt; atomicAdd(&S.wk[0], draws); }
+    __syncthreads();
+    uint32_t off = 0, tot = 0;
+    bool bad = false;
+    for (uint32_t q = 0; q < NW; ++q) {
+        if (S.wcount[q] == 0xFFFFFFFFu) bad = true;
+        else { if (q < w) off += S.wcount[q]; tot += S.wcount[q]; }
+    }
+    if (bad || tot > scr.cand_cap) {
+        if (threadIdx.x == 0) S.status = QRAM_E_CAP;
+        tot = 0;
+    } else {
+        for (uint32_t c = lane; c < cnt; c += 32) dst[off + c] = seg[c];
+    }
+    __syncthreads();
+    return tot;
+}
+
+// ---------------------------------------------------------------------------
 // one trajectory
 template <int NT>
 __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist) {
@@ -1134,91 +1279,20 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             cand[c] = v;
         }
     } else if (valid && thr > 0) {
-        // geometric gaps over the (slice, site) pairs in blocks of kGapBlock;
-        // each warp takes a contiguous run of blocks, one block per lane
-        // per round, and writes its candidates in order into its segment
-        const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-        const uint32_t tl = (uint32_t)traj, th = (uint32_t)(traj >> 32);
-        if (threadIdx.x == 0) {
-            S.gq[0] = 0ull - thr;                                  // 2^64 - thr
-            for (int m = 0; m + 1 < kGapBits; ++m) S.gq[m + 1] = __umul64hi(S.gq[m], S.gq[m]);
-        }
-        __syncthreads();
-        const uint32_t M = 2u * nodes, X = (uint32_t)(T - 1) * M;
-        const uint32_t nblk = (X + kGapBlock - 1) / kGapBlock;
-        const uint32_t per = (nblk + NW - 1) / NW;
-        const uint32_t g0 = w * per, g1 = min(nblk, g0 + per);
-        uint32_t *seg = scr.wseg + (slot * NW + w) * scr.seg_cap;
-        uint32_t cnt = 0, draws = 0;
-        bool overflow = false;
-        for (uint32_t gb = g0; gb < g1; gb += 32) {
-            const uint32_t g = gb + lane;
-            // pass 1 counts this lane's candidates, pass 2 writes them after
-            // those of the lower lanes
-            uint32_t mine = 0, off = 0;
-            for (int pass = 0; pass < 2; ++pass) {
-                if (pass == 1) {
-                    uint32_t x = mine;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-                        if (lane >= (uint32_t)o) x += y;
-                    }
-                    off = cnt + x - mine;
-                    cnt += __shfl_sync(0xFFFFFFFFu, x, 31);
-                    if (mine == 0) continue;
-                }
-                if (g >= g1) continue;
-                uint32_t pos = g * kGapBlock;
-                const uint32_t end = min(pos + kGapBlock, X);
-                uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0, k = 0;
-                for (uint32_t r = 0;; ++r) {
-                    if ((r & 1u) == 0) {
-                        o0 = g; o1 = (r >> 1) | (1u << 24); o2 = tl; o3 = th;
-                        philox(o0, o1, o2, o3, k0, k1);
-                    }
-                    const uint64_t u = (r & 1u) ? ((uint64_t)o2 | ((uint64_t)o3 << 32)) : ((uint64_t)o0 | ((uint64_t)o1 << 32));
-                    uint64_t acc = ~0ull;
-                    uint32_t G = 0;
-#pragma unroll
-                    for (int m = kGapBits - 1; m >= 0; --m) {
-                        const uint64_t t = __umul64hi(acc, S.gq[m]);
-                        if (t > u) { acc = t; G += 1u << m; }
-                    }
-                    if (G >= end - pos) { if (pass == 0) draws += r + 1; break; }
-                    pos += G;
-                    if (pass == 0) ++mine;
-                    else {
-                        const uint32_t q = off + k++;
-                        if (q < scr.seg_cap) seg[q] = ((1u + pos / M) << 16) | (pos % M);
-                        else overflow = true;
-                    }
-                    ++pos;
-                }
-            }
-        }
-        overflow = __any_sync(0xFFFFFFFFu, overflow);
-        draws = __reduce_add_sync(0xFFFFFFFFu, draws);
-        if (lane == 0) { S.wcount[w] = overflow ? 0xFFFFFFFFu : cnt; atomicAdd(&S.wk[0], draws); }
-        __syncthreads();
-        uint32_t off = 0, tot = 0;
-        bool bad = false;
-        for (uint32_t q = 0; q < NW; ++q) {
-            if (S.wcount[q] == 0xFFFFFFFFu) bad = true;
-            else { if (q < w) off += S.wcount[q]; tot += S.wcount[q]; }
-        }
-        if (bad || tot > scr.cand_cap) {
-            if (threadIdx.x == 0) S.status = QRAM_E_CAP;
-            tot = 0;
-        } else {
-            for (uint32_t c = lane; c < cnt; c += 32) cand[off + c] = seg[c];
-        }
-        ncand = tot;
+        ncand = sample_stream<NT>(P, S, thr, 1u, 0u, traj, cand);
     }
     __syncthreads();
     if (S.status == QRAM_E_ARG) ncand = 0;
     if (threadIdx.x == 0) S.ncand = ncand;
+    // depolarizing fault events (their own stream; every branch explicit)
+    const double eps = P.eps_gamma ? gamma : P.eps;
+    const bool depol = valid && eps > 0.0 && eps < 1.0;
+    uint32_t *pev = scr.pev + slot * scr.cand_cap;
+    uint32_t npev = 0;
+    if (depol) {
+        const uint64_t thr_e = (uint64_t)__double2ull_rz(eps * 18446744073709551616.0);
+        if (thr_e > 0) npev = sample_stream<NT>(P, S, thr_e, 4u, P.enc == QRAM_QUBIT ? 3u : 8u, traj, pev);
+    }
 
     // per-slice offsets (candidates are sorted by (slice, site))
     if (threadIdx.x < 8) S.syncmask[threadIdx.x] = 0;   // [4..7] are set at each fired jump
@@ -1226,7 +1300,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     for (uint32_t c = threadIdx.x; c < ncand; c += NT) {
         const uint32_t s = cand[c] >> 16, q = cand[c] & 0xFFFFu;
         const int L = layer_of(q >> 1);
-        if ((P.occ2[s] >> (2 * L + (int)(q & 1u))) & 1u)   // a noiseless orbit can hold it excited
+        if (depol || ((P.occ2[s] >> (2 * L + (int)(q & 1u))) & 1u))   // a noiseless orbit can hold it excited
             atomicOr(&S.syncmask[s >> 5], 1u << (s & 31u));
     }
     for (int s = threadIdx.x; s <= T; s += NT) {
@@ -1234,11 +1308,16 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         const uint32_t key = (uint32_t)s << 16;
         while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (cand[mid] < key) lo = mid + 1; else hi = mid; }
         S.slice_off[s] = lo;
+        lo = 0; hi = npev;
+        const uint32_t pkey = (uint32_t)s << 18;
+        while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (pev[mid] < pkey) lo = mid + 1; else hi = mid; }
+        S.pslice_off[s] = lo;
     }
-    // ---- 2. marking: every candidate marks bad(v) ---------------------------
-    for (uint32_t c = threadIdx.x; c < ncand; c += NT) {
+    // ---- 2. marking: every fault marks bad(v), whatever its type --------------
+    for (uint32_t c = threadIdx.x; c < ncand + npev; c += NT) {
         uint32_t lo, hi;
-        bad_range(P.enc, n, (cand[c] & 0xFFFFu) >> 1, lo, hi);
+        const uint32_t site = c < ncand ? (cand[c] & 0xFFFFu) : (pev[c - ncand] & 0x7FFFu);
+        bad_range(P.enc, n, site >> 1, lo, hi);
         while (lo < hi) {
             const uint32_t wd = lo >> 5, b0 = lo & 31u;
             const uint32_t nb = min(32u - b0, hi - lo);
@@ -1289,7 +1368,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
 
     // pruned mode keeps every branch implicit until a jump fires (the state
     // dump reads the explicit set at the end, so it keeps the eager form)
-    const bool lazy = P.mode == kPruned && P.orbit.ok && !P.dump_mode;
+    const bool lazy = P.mode == kPruned && P.orbit.ok && !P.dump_mode && !depol;
     // lazy epochs in product form: qubit input over every address, equal weights
     const bool factored = lazy && P.col_of != nullptr && P.w2u != nullptr && *P.w2u > 0.0;
 
@@ -1335,7 +1414,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             bool take = false;
             if (b < (uint32_t)P.D) {
                 const uint32_t i = __ldg(P.addr + b);
-                take = P.mode == kFull || ((S.badbits[i >> 5] >> (i & 31u)) & 1u) || (int)b == S.refcol;
+                take = P.mode == kFull || depol || ((S.badbits[i >> 5] >> (i & 31u)) & 1u) || (int)b == S.refcol;
             }
             uint32_t tot;
             const uint32_t pre = block_scan_flag(take, &tot, S);
@@ -1369,7 +1448,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     // equal-magnitude inputs: weights are w2u * a^(2e), summed as integer
     // histograms over e (all, empty mask / ground, signed overlap)
     const double w2u = P.w2u ? *P.w2u : 0.0;
-    const bool uni = w2u > 0.0;
+    // (a qutrit phase w^m makes the overlap complex: those weights go through FP64)
+    const bool uni = w2u > 0.0 && !(depol && P.enc == QRAM_QUTRIT);
     const int H = (2 * n + P.k) * (T - 1) + 1;
     uint32_t *hall = hist, *hemp = hist + P.hist_pad;
     int32_t *hov = (int32_t *)(hist + 2 * P.hist_pad);
@@ -1455,7 +1535,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         const int nJ = S.nJ;
         const bool compact = s_prev > 0 && nJ > 0;
         const bool lazy_pre = lazy && !jumped;       // every branch still on its noiseless orbit
-        double wsum = 0.0, wempty = 0.0, ovl = 0.0;
+        double wsum = 0.0, wempty = 0.0, ovl = 0.0, ovi = 0.0;
         bool capfail_lazy = false;
         if (lazy_pre) {
             // closed-form weights of every branch (Eq. (12), Lemma 1): the
@@ -1578,6 +1658,16 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 nsl += (uint32_t)(slast - s_prev);
                 for (int s = s_prev + 1; s <= slast; ++s) {
                     if (!apply_slice(P.ops[s], c, xs, C)) { capfail = true; break; }
+                    if (npev) {                             // depolarizing faults of slice s
+                        bool okall = true;
+                        for (uint32_t e = S.pslice_off[s]; e < S.pslice_off[s + 1]; ++e) {
+                            const uint32_t v = pev[e];
+                            int okv;
+                            c = pauli_site(c, xs, C, v & 0x7FFFu, (v >> 15) & 7u, &okv);
+                            if (!okv) { okall = false; break; }
+                        }
+                        if (!okall) { capfail = true; break; }
+                    }
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
                 if (c.e >= 4096 || (uni && c.e >= H)) capfail = true;   // exponent bound (packed in 12 bits)
@@ -1609,7 +1699,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         w = col_w2(P, lab) * k2 * ae * ae;
                         wsum += w;
                         if (ground) wempty += w;
-                        if (ovs) ovl += ovs * (col_w2(P, lab) * k2 * ae);
+                        if (ovs) {
+                            const double base = col_w2(P, lab) * k2 * ae;
+                            if (!qubit && c.sign) {                   // w^sign, w = exp(2 pi i / 3)
+                                ovl -= 0.5 * base;
+                                ovi += (c.sign == 1 ? 0.5 : -0.5) * sqrt(3.0) * base;
+                            } else {
+                                ovl += ovs * base;
+                            }
+                        }
                     } else if (c.e < H) {
                         hkey = ((uint32_t)c.e << 3) | ((ground ? 1u : 0u) << 2) | (uint32_t)(ovs + 1);
                     }
@@ -1617,12 +1715,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         const uint32_t di = atomicAdd(P.dump.count, 1u);
                         if (di < P.dump.cap) {
                             const uint32_t col = lab;
-                            const double sc = (qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0) * ae * (c.sign ? -1.0 : 1.0);
+                            const double sc = (qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0) * ae;
+                            double pr = (qubit && c.sign) ? -1.0 : 1.0, pim = 0.0;   // phase of the component
+                            if (!qubit && c.sign) { pr = -0.5; pim = (c.sign == 1 ? 0.5 : -0.5) * sqrt(3.0); }
+                            const double ar = __ldg(P.amp_re + col), ai = __ldg(P.amp_im + col);
                             P.dump.col[di] = col;
                             P.dump.bus[di] = c.cb;
                             P.dump.hash[di] = config_hash(c, xs, C);
-                            P.dump.re[di] = __ldg(P.amp_re + col) * sc;
-                            P.dump.im[di] = __ldg(P.amp_im + col) * sc;
+                            P.dump.re[di] = (ar * pr - ai * pim) * sc;
+                            P.dump.im[di] = (ar * pim + ai * pr) * sc;
                         }
                     }
                 }
@@ -1686,7 +1787,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         // good branches of the eager form: closed-form weights before the
         // first jump (Eq. (18))
         double wgs = 0.0, ogs = 0.0;
-        if (P.mode == kPruned && !jumped && !lazy) {
+        if (P.mode == kPruned && !jumped && !lazy && !depol) {
             const int sw = final_epoch ? T - 1 : s1 - 1;
             for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
                 const uint32_t i = __ldg(P.addr + b);
@@ -1705,12 +1806,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         const double Wtot = wsum + wgs, Wemp = wempty + wgs;
         if (final_epoch) {
             const double ov_all = ovl + ogs;
+            double ov_im = 0.0;                       // imaginary part (qutrit phases of depolarizing faults)
+            if (depol && !qubit) ov_im = block_sum(ovi, S.redA, S);
+            const double ov2 = ov_all * ov_all + ov_im * ov_im;
             if (threadIdx.x == 0) {
                 const double uf = uniform53(P.seed, 0, 3u, traj);
                 const bool ground = Wemp > uf * Wtot;
                 qram_result_t R;
-                R.fidelity = (ground && Wemp > 0.0) ? ov_all * ov_all / Wemp : 0.0;
-                R.fidelity_unsampled = Wtot > 0.0 ? ov_all * ov_all / Wtot : 0.0;
+                R.fidelity = (ground && Wemp > 0.0) ? ov2 / Wemp : 0.0;
+                R.fidelity_unsampled = Wtot > 0.0 ? ov2 / Wtot : 0.0;
                 R.p_ground = Wtot > 0.0 ? Wemp / Wtot : 0.0;
                 R.bad = S.nbad;
                 R.ref = S.refcol;
@@ -1727,6 +1831,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 if (P.dump_mode) {
                     P.dump.scal[0] = Wtot;
                     P.dump.scal[1] = jumped ? 1.0 : 0.0;
+                    P.dump.scal[2] = depol ? 1.0 : 0.0;           // every branch explicit: nothing to predict
                 }
             }
             __syncthreads();
@@ -1941,7 +2046,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             const uint32_t r = S.region;
             for (uint32_t c = S.slice_off[s1 + 1] + threadIdx.x; c < S.slice_off[T]; c += NT) {
                 const uint32_t u = (cand[c] & 0xFFFFu) >> 1, sc = cand[c] >> 16;
-                if (tree_related(u, r)) atomicOr(&S.syncmask[4 + (sc >> 5)], 1u << (sc & 31u));
+                if (depol || tree_related(u, r)) atomicOr(&S.syncmask[4 + (sc >> 5)], 1u << (sc & 31u));
             }
         }
         // clear the candidate bitmaps of s1
@@ -2098,7 +2203,7 @@ __global__ void dump_finalize_kernel(const Params P, uint32_t n_in, uint32_t *ou
         }
     }
     // predicted good branches (pruned mode, no jump fired)
-    if (P.mode != kPruned || d.scal[1] != 0.0) return;
+    if (P.mode != kPruned || d.scal[1] != 0.0 || d.scal[2] != 0.0) return;
     const double g = P.gamma[0];
     const double a = sqrt(1.0 - g);
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < (uint32_t)P.D; b += gridDim.x * blockDim.x) {

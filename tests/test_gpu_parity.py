@@ -362,3 +362,50 @@ def test_dump_low_weight_truncation(wmax):
     sim.dump_state("pruned", 0, gamma, w_max=-1)
     assert seen_drop
     sim.close()
+
+
+DEPOL_CASES = [
+    # encoding, n, k, gamma, eps, ntraj, input
+    (W.QUBIT, 2, 1, 0.0, 0.02, 400, "dm"),        # the Tab. IV circuit, Pauli only
+    (W.QUBIT, 2, 1, 0.02, 0.02, 400, "dm"),       # mixed
+    (W.QUBIT, 5, 3, 2e-3, 2e-3, 200, "load"),
+    (W.QUBIT, 6, 2, 1e-3, -1.0, 200, "rand"),     # eps = gamma per trajectory
+    (W.QUTRIT, 1, 1, 0.05, 0.05, 400, "load"),
+    (W.QUTRIT, 4, 2, 4e-3, 4e-3, 200, "rand"),
+]
+
+
+@pytest.mark.parametrize("enc,n,k,gamma,eps,ntraj,kind", DEPOL_CASES)
+@pytest.mark.parametrize("mode", ["pruned", "full"])
+def test_depolarizing_trajectories_match_oracle(enc, n, k, gamma, eps, ntraj, kind, mode):
+    seed = 7000 + 13 * n + k
+    p = _problem(enc, n, k, kind, seed)
+    g = np.full(ntraj, gamma)
+    ref = core.run(p, seed, 0, g, eps=eps)
+    sim = _sim(p, seed)
+    sim.set_depolarizing(max(eps, 0.0), eps_equals_gamma=eps < 0)
+    got = sim.results(sim.run(mode, 0, torch.tensor(g, device="cuda:0")))
+    _cmp_results(got, ref)
+    sim.close()
+
+
+@pytest.mark.parametrize("enc,n,k,gamma,eps", [(W.QUBIT, 3, 2, 0.03, 0.03), (W.QUTRIT, 3, 1, 0.02, 0.03)])
+def test_depolarizing_final_state_amplitudes(enc, n, k, gamma, eps):
+    seed = 8100 + n
+    p = _problem(enc, n, k, "rand", seed)
+    sim = _sim(p, seed)
+    sim.set_depolarizing(eps)
+    for traj in range(10):
+        _, d = core.run_one(p, seed, traj, gamma, None, cap=1 << 14, eps=eps)
+        want = {}
+        for a, b, cfg, amp in zip(d.addr, d.bus, d.configs, d.amp):
+            key = (int(a), int(b), _hash_cfg(cfg))
+            want[key] = want.get(key, 0) + amp
+        ga, gb, gh, gz = sim.dump_state("pruned", traj, gamma)
+        got = {}
+        for a, b, h, z in zip(ga, gb, gh, gz):
+            key = (int(a), int(b), int(h))
+            got[key] = got.get(key, 0) + z
+        for key in set(want) | set(got):
+            assert abs(want.get(key, 0) - got.get(key, 0)) < TOL, (traj, key)
+    sim.close()
