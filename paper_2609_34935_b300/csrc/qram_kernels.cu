@@ -1233,7 +1233,7 @@ __device__ uint32_t sample_stream(const Params &P, Smem<NT> &S, uint64_t thr, ui
 
 // ---------------------------------------------------------------------------
 // one trajectory
-template <int NT>
+template <int NT, bool DEPOL>
 __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist) {
     constexpr int NW = NT / 32;
     const uint64_t traj = (P.traj0_dev ? *P.traj0_dev : P.traj0) + t;
@@ -1286,7 +1286,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     if (threadIdx.x == 0) S.ncand = ncand;
     // depolarizing fault events (their own stream; every branch explicit)
     const double eps = P.eps_gamma ? gamma : P.eps;
-    const bool depol = valid && eps > 0.0 && eps < 1.0;
+    const bool depol = DEPOL && valid && eps > 0.0 && eps < 1.0;
     uint32_t *pev = scr.pev + slot * scr.cand_cap;
     uint32_t npev = 0;
     if (depol) {
@@ -2060,7 +2060,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     }
 }
 
-template <int NT, int MINB>
+// DEPOL: compiled with the depolarizing faults (a launch with eps > 0);
+// without, the event code is absent from the hot loop
+template <int NT, int MINB, bool DEPOL>
 __global__ void __launch_bounds__(NT, MINB) traj_kernel(const __grid_constant__ Params P) {
     __shared__ Smem<NT> S;
     // 3 exponent histograms of hist_pad bins, or the partials of a block sum;
@@ -2075,28 +2077,33 @@ __global__ void __launch_bounds__(NT, MINB) traj_kernel(const __grid_constant__ 
         const uint32_t t = (uint32_t)S.t;
         __syncthreads();
         if (t >= P.ntraj) break;
-        run_one<NT>(P, S, t, dyn_hist);
+        run_one<NT, DEPOL>(P, S, t, dyn_hist);
         __syncthreads();
     }
 }
 
 // launch variants (threads per CTA, minimum resident CTAs for the register cap)
-template <int NT, int MINB>
+template <int NT, int MINB, bool DEPOL>
 static cudaError_t launch_variant(const Params &p, int grid, size_t dyn, cudaStream_t s, bool occupancy_only, int *blocks) {
     // static + dynamic shared memory can exceed 48 KB: opt in
-    cudaError_t e = cudaFuncSetAttribute(traj_kernel<NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(traj_kernel<NT, MINB, DEPOL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(3 * kHistMax * sizeof(uint32_t)));
     if (e != cudaSuccess) return e;
-    if (occupancy_only) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traj_kernel<NT, MINB>, NT, dyn);
-    traj_kernel<NT, MINB><<<grid, NT, dyn, s>>>(p);
+    if (occupancy_only)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traj_kernel<NT, MINB, DEPOL>, NT, dyn);
+    traj_kernel<NT, MINB, DEPOL><<<grid, NT, dyn, s>>>(p);
     return cudaGetLastError();
 }
 
 static cudaError_t dispatch(int threads, const Params &p, int grid, size_t dyn, cudaStream_t s, bool occ, int *blocks) {
+    const bool depol = p.eps > 0.0 || p.eps_gamma;
     switch (threads) {
-    case 128: return launch_variant<128, 8>(p, grid, dyn, s, occ, blocks);
-    case 256: return launch_variant<256, 4>(p, grid, dyn, s, occ, blocks);
-    case 512: return launch_variant<512, 2>(p, grid, dyn, s, occ, blocks);
+    case 128: return depol ? launch_variant<128, 8, true>(p, grid, dyn, s, occ, blocks)
+                           : launch_variant<128, 8, false>(p, grid, dyn, s, occ, blocks);
+    case 256: return depol ? launch_variant<256, 4, true>(p, grid, dyn, s, occ, blocks)
+                           : launch_variant<256, 4, false>(p, grid, dyn, s, occ, blocks);
+    case 512: return depol ? launch_variant<512, 2, true>(p, grid, dyn, s, occ, blocks)
+                           : launch_variant<512, 2, false>(p, grid, dyn, s, occ, blocks);
     default: return cudaErrorInvalidValue;
     }
 }
