@@ -336,6 +336,27 @@ def main():
                                  "evolved_fraction": float(np.mean(rp["explicit_comps"]) / np.mean(rf["explicit_comps"])),
                                  "max_abs_fidelity_diff": float(np.max(np.abs(rp["fidelity"] - rf["fidelity"])))}
 
+    # ---- the paper's mixed setting, depolarizing faults with eps = gamma ------
+    # Every branch is explicit in both modes, and every tree site takes faults,
+    # so stray excitations pile up in every component: measured on qubit n=8,
+    # k=3 (data-loading input) where they stay within the per-component
+    # capacity for eps <= 1e-3.
+    mixed = {}
+    nm = 2000
+    pm = W.data_loading(W.QUBIT, 8, 3, seed=SEED + 8)
+    simm = QramSim(pm, seed=SEED + 8, device=local, stream=stream)
+    simm.set_gamma_bound(1e-3)
+    simm.set_depolarizing(0.0, eps_equals_gamma=True)
+    gm = torch.empty(nm, dtype=torch.float64, device=dev)
+    om = torch.empty((nm, 48), dtype=torch.uint8, device=dev)
+    for dg in (1e-5, 1e-4, 1e-3):
+        gm.fill_(dg)
+        tm_ = timed(lambda: simm.run_pruned(base + 6_000_000, gm, om))
+        rm = QramSim.results(om)
+        mixed[f"{dg:g}"] = {"traj_per_s": nm / tm_, "mean_fidelity": float(rm["fidelity"].mean()),
+                            "status_ok_fraction": float(np.mean(rm["status"] == 0))}
+    simm.close()
+
     # ---- per-query latency: one gamma batch (1000 trajectories) alone -----
     lat = []
     gb = torch.empty(BATCH, dtype=torch.float64, device=dev)
@@ -396,6 +417,10 @@ def main():
                      "subset": f"{args.full_per_batch} trajectories per gamma batch ({len(sub)} total)",
                      "max_abs_fidelity_diff_pruned_vs_full": agree},
             "per_gamma_decade": per_decade,
+            "eps_eq_gamma_per_decade": {"note": "depolarizing faults of strength eps = gamma on top of the damping "
+                                                "(the paper's benchmark setting, every tree site active), every "
+                                                "branch explicit; qubit n=8, k=3, data-loading input, 2000 "
+                                                "trajectories per decade", **mixed},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "query": "one gamma batch of 1000 trajectories launched alone", "n": int(len(lat))},
             "mean_fidelity": float(res["fidelity"].mean()), "status_ok": bool(np.all(res["status"] == 0)),
@@ -422,9 +447,17 @@ def run_scan(args):
     t0 = time.perf_counter()
     rows = fidelity_vs_n(W.QUBIT, range(3, 13), (1e-5, 1e-4, 1e-3), k=3, D=500, ntraj=200)
     torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    # with every tree site active, stray excitations exceed the per-component
+    # capacity beyond these sizes (reported as QRAM_E_CAP)
+    rows_eps = fidelity_vs_n(W.QUBIT, range(3, 9), (1e-5, 1e-4), k=3, D=500, ntraj=200, eps_equals_gamma=True)
+    rows_eps += fidelity_vs_n(W.QUBIT, range(3, 7), (1e-3,), k=3, D=500, ntraj=200, eps_equals_gamma=True)
+    torch.cuda.synchronize()
     print(json.dumps({"scan": "mean fidelity vs n, qubit, k=3, 500-branch random input (one column per "
-                              "address), 200 trajectories per point, damping only",
-                      "seconds": time.perf_counter() - t0, "rows": rows}), flush=True)
+                              "address), 200 trajectories per point; damping only, and depolarizing faults "
+                              "of the same strength (eps = gamma, every tree site active; n <= 8, n <= 6 at 1e-3)",
+                      "seconds": t1 - t0, "rows": rows,
+                      "seconds_eps_eq_gamma": time.perf_counter() - t1, "rows_eps_eq_gamma": rows_eps}), flush=True)
     return 0
 
 

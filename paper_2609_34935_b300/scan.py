@@ -1,4 +1,5 @@
-"""Fidelity versus address size (the damping-only analog of Fig. 2).
+"""Fidelity versus address size (Fig. 2; damping only, or with depolarizing
+faults of the same strength).
 
 For each (n, gamma) point: one simulator on the scan input (min(D, 2^n)
 distinct addresses, random bus words, equal weights; Sec. V.A restricted to
@@ -15,10 +16,11 @@ import workloads as W
 
 
 def fidelity_vs_n(encoding: int = W.QUBIT, ns=range(2, 11), gammas=(1e-5, 1e-4, 1e-3), k: int = 3,
-                  D: int = 500, ntraj: int = 200, seed: int = 6001, device: int = 0):
+                  D: int = 500, ntraj: int = 200, seed: int = 6001, device: int = 0, eps_equals_gamma: bool = False):
     """Returns one dict per (n, gamma): mean fidelity, its standard error, the
     bad-branch fraction, the mean number of fired jumps and the sampled
-    ground fraction."""
+    ground fraction.  eps_equals_gamma adds depolarizing faults of the same
+    strength (the setting of Fig. 2)."""
     import torch
     from . import QramSim
     rows = []
@@ -27,6 +29,8 @@ def fidelity_vs_n(encoding: int = W.QUBIT, ns=range(2, 11), gammas=(1e-5, 1e-4, 
             continue
         p = W.uniform_random_input(encoding, n, k, D, seed + 97 * n)
         sim = QramSim(p, seed=seed + n, device=device)
+        if eps_equals_gamma:
+            sim.set_depolarizing(0.0, eps_equals_gamma=True)
         for g in gammas:
             gam = torch.full((ntraj,), float(g), dtype=torch.float64, device=f"cuda:{device}")
             raw = sim.run_pruned(0, gam)
@@ -34,7 +38,7 @@ def fidelity_vs_n(encoding: int = W.QUBIT, ns=range(2, 11), gammas=(1e-5, 1e-4, 
             r = QramSim.results(raw)
             if not np.all(r["status"] == 0):
                 raise RuntimeError(f"scan point n={n} gamma={g}: status {np.unique(r['status'])}")
-            rows.append({"n": n, "gamma": float(g), "D": p.D, "mean_fidelity": mean, "se": se,
+            rows.append({"n": n, "gamma": float(g), "eps": float(g) if eps_equals_gamma else 0.0, "D": p.D, "mean_fidelity": mean, "se": se,
                          "bad_fraction": float(r["bad"].mean() / p.D), "jumps": float(r["jumps"].mean()),
                          "ground_fraction": float(r["q_ground"].mean())})
         sim.close()
