@@ -1239,7 +1239,6 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     const uint64_t traj = (P.traj0_dev ? *P.traj0_dev : P.traj0) + t;
     const double gamma = P.gamma[t];
     const int n = P.n, T = P.T;
-    const uint32_t nodes = (uint32_t)P.nodes;
     const size_t slot = blockIdx.x;
     const Scratch &scr = P.scr;
     uint32_t *cand = scr.cand + slot * scr.cand_cap;
@@ -1729,14 +1728,13 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 }
             }
             if (uni) {
-                // warp-aggregated histogram update (equal keys add once)
-                const uint32_t grp = __match_any_sync(0xFFFFFFFFu, hkey);
-                if (hkey != 0xFFFFFFFFu && (int)lane == __ffs(grp) - 1) {
-                    const uint32_t cnt = __popc(grp), e = hkey >> 3;
-                    atomicAdd(&hall[e], cnt);
-                    if ((hkey >> 2) & 1u) atomicAdd(&hemp[e], cnt);
+                // integer histogram counts (shared-memory atomics; sums are order-free)
+                if (hkey != 0xFFFFFFFFu) {
+                    const uint32_t e = hkey >> 3;
+                    atomicAdd(&hall[e], 1u);
+                    if ((hkey >> 2) & 1u) atomicAdd(&hemp[e], 1u);
                     const int ovs = (int)(hkey & 3u) - 1;
-                    if (ovs) atomicAdd(&hov[e], ovs * (int)cnt);
+                    if (ovs) atomicAdd(&hov[e], ovs);
                 }
             }
             {
