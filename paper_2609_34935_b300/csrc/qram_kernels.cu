@@ -158,6 +158,7 @@ struct Smem {
     double sA, sB, sC;
     double *part;                  // 3 NT doubles of the dynamic area, zero between block sums
     double dn, al, qt[kMaxK];      // per-epoch data factors (qubit): norm^2, final overlap, 1/(1 + a^(2 m_t))
+    double fdn[kMaxT];             // per trajectory: the norm^2 data factor dn after damping slices 1..s
     double fW, fO;                 // per-epoch scale of the weight sums and of the overlap sum
     double hdat[2 * kMaxN + 1];    // per trajectory: (1 + a^(2m)) / 2 and 1 / (1 + a^(2m)), m <= 2n
     double rdat[2 * kMaxN + 1];
@@ -173,11 +174,26 @@ struct Smem {
 };
 
 // Block sums of doubles.  FP64 issue is scarce on this part (a warp-wide
-// FP64 instruction holds a sub-partition for tens of cycles), so instead of
-// a shuffle tree in every warp each thread parks its partial in S.part (NT
-// doubles per value, zero between uses) and one warp adds them up, lane l
-// taking partials l, l + 32, ... and a shuffle tree finishing; that warp
-// leaves the area zero again.  The order is fixed: deterministic.
+// FP64 instruction holds a sub-partition's FP64 unit for tens of cycles), so
+// instead of a shuffle tree in every warp each thread parks its partial in
+// S.part (NT doubles per value, zero between uses) and one warp per value
+// adds them up: lane l takes partials l, l + 32, ... and a shuffle tree
+// finishes.  A row of 32 partials whose bits are all zero is skipped: adding
+// +0.0 changes nothing, and -0.0 is added and cleared like any value since
+// the area doubles as integer histograms.  That makes sparse sums cheap.  The
+// warp leaves its area zero again.  The order is fixed: deterministic.
+__device__ __forceinline__ double rows_sum(double *part, int rows, uint32_t lane) {
+    double r = 0.0;
+    for (int q = 0; q < rows; ++q) {
+        const double x = part[q * 32 + lane];
+        if (__any_sync(0xFFFFFFFFu, __double_as_longlong(x) != 0)) {   // bits: -0.0 is cleared too
+            r += x;
+            part[q * 32 + lane] = 0.0;
+        }
+    }
+    return warp_sum(r);
+}
+
 template <int NT>
 __device__ double block_sum(double x, double *red, Smem<NT> &S) {
     (void)red;
@@ -186,36 +202,33 @@ __device__ double block_sum(double x, double *red, Smem<NT> &S) {
     part[threadIdx.x] = x;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double r = 0.0;
-#pragma unroll
-        for (int q = 0; q < NT / 32; ++q) { r += part[q * 32 + threadIdx.x]; part[q * 32 + threadIdx.x] = 0.0; }
-        r = warp_sum(r);
+        const double r = rows_sum(part, NT / 32, threadIdx.x);
         if (threadIdx.x == 0) S.sA = r;
     }
     __syncthreads();
     return S.sA;
 }
 
-// three sums at once, each scaled by its factor (applied once, by one thread)
+// three sums at once (warps 0, 1, 2: one per value, on different
+// sub-partitions), each scaled by its factor (applied once, by one thread)
 template <int NT>
 __device__ void block_sum3(double &a, double &b, double &c, Smem<NT> &S, double fa = 1.0, double fb = 1.0,
                            double fc = 1.0) {
+    static_assert(NT >= 96, "three reducing warps");
     double *part = S.part;
     __syncthreads();
     part[threadIdx.x] = a;
     part[NT + threadIdx.x] = b;
     part[2 * NT + threadIdx.x] = c;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double ra = 0.0, rb = 0.0, rc = 0.0;
-#pragma unroll
-        for (int q = 0; q < NT / 32; ++q) {
-            const int i = q * 32 + (int)threadIdx.x;
-            ra += part[i]; rb += part[NT + i]; rc += part[2 * NT + i];
-            part[i] = 0.0; part[NT + i] = 0.0; part[2 * NT + i] = 0.0;
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    if (w < 3) {
+        const double r = rows_sum(part + w * NT, NT / 32, lane);
+        if (lane == 0) {
+            if (w == 0) S.sA = r * fa;
+            else if (w == 1) S.sB = r * fb;
+            else S.sC = r * fc;
         }
-        ra = warp_sum(ra); rb = warp_sum(rb); rc = warp_sum(rc);
-        if (threadIdx.x == 0) { S.sA = ra * fa; S.sB = rb * fb; S.sC = rc * fc; }
     }
     __syncthreads();
     a = S.sA; b = S.sB; c = S.sC;
@@ -255,6 +268,15 @@ __device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem<NT> &S) {
     for (uint32_t i = 0; i < NW; ++i) { if (i < w) base += S.scanw[i]; all += S.scanw[i]; }
     *tot = all;
     return base + pre;
+}
+
+// Entry of a warp's compact selection list (components with a non-empty
+// mask at the slice being drawn): the mask's first element (16 bits), its
+// size capped at 15 (the descent only asks "one element or more"), and for
+// equal-magnitude inputs the exponent e (12 bits), from which the descent
+// recomputes the weight w2u a^(2e) instead of the pass storing a double.
+__device__ __forceinline__ uint32_t sel_key(uint32_t c1, uint32_t mcnt, int e) {
+    return (c1 & 0xFFFFu) | (min(mcnt, 15u) << 16) | ((uint32_t)e & 0xFFFu) << 20;
 }
 
 // ---------------------------------------------------------------------------
@@ -1390,6 +1412,14 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         S.hdat[threadIdx.x] = 0.5 * h;
         S.rdat[threadIdx.x] = 1.0 / h;
     }
+    __syncthreads();
+    for (int sw = (int)threadIdx.x; P.enc == QRAM_QUBIT && sw < T; sw += NT) {
+        // data factors after damping slices 1..sw (Lemma 1): each data qubit
+        // t contributes (1 + a^(2 m_t)) / 2 to a branch's norm^2
+        double dn = 1.0;
+        for (int q = 0; q < P.k; ++q) dn *= S.hdat[ov(2 * n + 2 * q + 1, 4 * n + 2 * q, sw)];
+        S.fdn[sw] = dn;
+    }
     for (int sw = (int)threadIdx.x; factored && sw < T; sw += NT) {
         // sum over every address of a^(2E) after damping slices 1..s: the
         // address bits enter independently (Eq. (12))
@@ -1457,6 +1487,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     uint32_t jumps = 0, first_jump = 0, jump_sites = 0;
     const double k2 = qubit ? ldexp(1.0, -P.k) : 1.0;   // |first-wall factor|^2
     const double inv_k2 = qubit ? ldexp(1.0, P.k) : 1.0;
+    if (threadIdx.x == 0) {
+        double al = 1.0;                                  // (1 + a^(2n)) / 2 per fully exposed data qubit
+        if (qubit) for (int q = 0; q < P.k; ++q) al *= S.hdat[n];
+        S.al = al;
+    }
     for (;;) {
         // next slice whose candidates can matter: before the first fired jump
         // every component is on a noiseless orbit, so a candidate on a position
@@ -1470,20 +1505,13 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         const bool final_epoch = s1 >= T;
         if (threadIdx.x == 0) {
             S.cl2 = 0;
-            // data factors after damping slices 1..sw (Lemma 1): each data
-            // qubit t contributes (1 + a^(2 m_t)) / 2 to a branch's norm^2
+            // data factors after damping slices 1..sw (tabulated per trajectory)
             const int sw = final_epoch ? T - 1 : s1 - 1;
-            double dn = 1.0, al = 1.0;
-            if (qubit) {
-                for (int q = 0; q < P.k; ++q) {
-                    const int m = ov(2 * n + 2 * q + 1, 4 * n + 2 * q, sw);
-                    dn *= S.hdat[m];
-                    S.qt[q] = S.rdat[m];
-                    al *= S.hdat[n];                      // (1 + a^(2n)) / 2: a fully exposed data qubit
-                }
-            }
+            const double dn = qubit ? S.fdn[sw] : 1.0;
+            if (qubit)
+                for (int q = 0; q < P.k; ++q) S.qt[q] = S.rdat[ov(2 * n + 2 * q + 1, 4 * n + 2 * q, sw)];
             S.dn = dn;
-            S.al = al;
+            const double al = S.al;
             // lazy epochs count branches (|c|^2 without the wall factor, data
             // factors apart); explicit epochs count components (uni: |c|^2 2^-k)
             const bool lp = lazy && !jumped;
@@ -1678,7 +1706,6 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         wsum += w;
                         if (mcnt == 0) wempty += w;
                     } else {
-                        if (mcnt > 0) { const double ae = apow(S, c.e); w = w2u * ae * ae; }
                         if (c.e < H) hkey = ((uint32_t)c.e << 3) | ((mcnt == 0 ? 1u : 0u) << 2) | 1u;
                     }
                 } else {
@@ -1742,8 +1769,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ne);
                 if (ne) {
                     const uint32_t pos = wcur + __popc(bal & ((1u << lane) - 1u));
-                    selk[pos] = (c1 & 0xFFFFu) | (mcnt << 16);
-                    selw[pos] = w;
+                    selk[pos] = sel_key(c1, mcnt, uni ? c.e : 0);
+                    if (!uni) selw[pos] = w;
                 }
                 wcur += __popc(bal);
             }
@@ -1866,6 +1893,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 for (uint32_t cw = 0; cw < ncw; ++cw) {
                     const bool take = cnt && (all || (cw & tm));
                     uint32_t c1 = 0, mcnt = 0;
+                    int ce = 0;
                     double w = 0.0;
                     if (take) {
                         CompR c = orbit_state(P, s1, i, cw, j, d);
@@ -1873,13 +1901,21 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         store_comp(scr, cbase + r, c, nullptr, qubit, b, i);
                         ++r;
                         c1 = mask_first(c, nullptr, C, S.candbits, S.cl2, mcnt);
-                        const double ae = apow(S, c.e);
-                        w = w2 * ae * ae;
+                        ce = c.e;
+                        if (uni) {
+                            if (c.e >= 4096) capfail = true;             // the key holds 12 bits of e
+                        } else {
+                            const double ae = apow(S, c.e);
+                            w = w2 * ae * ae;
+                        }
                     }
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
                     if (take) {
                         const uint32_t q = wcur + __popc(bal & ((1u << lane) - 1u));
-                        if (q < scr.selseg) { selk[q] = (c1 & 0xFFFFu) | (mcnt << 16); selw[q] = w; }
+                        if (q < scr.selseg) {
+                            selk[q] = sel_key(c1, mcnt, uni ? ce : 0);
+                            if (!uni) selw[q] = w;
+                        }
                         else capfail = true;
                     }
                     wcur += __popc(bal);
@@ -1911,9 +1947,16 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         const double *sw = sw0 + q * (size_t)scr.selseg;
                         for (uint32_t e = threadIdx.x; e < S.segn[q]; e += NT) {
                             const uint32_t kv = sk[e], code = kv & 0xFFFFu;
-                            if (eq_only_single) {
-                                if (code == ceq) { if ((kv >> 16) == 1u) f += sw[e]; else mm = 1; }
-                            } else if (code <= cmax) f += sw[e];
+                            const bool in = eq_only_single ? code == ceq && ((kv >> 16) & 15u) == 1u : code <= cmax;
+                            if (eq_only_single && code == ceq && !in) mm = 1;
+                            if (in) {
+                                if (uni) {
+                                    const double ae = apow(S, (int)(kv >> 20));
+                                    f += w2u * ae * ae;
+                                } else {
+                                    f += sw[e];
+                                }
+                            }
                         }
                     }
                     if (multi) *multi = mm;
