@@ -823,12 +823,44 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
     return c;
 }
 
-__device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16_t *xs, const Ctx &C) {
+// layers holding off-path items (bit L)
+__device__ __forceinline__ uint32_t xs_layers(const CompR &c, const uint16_t *xs) {
+    uint32_t m = 0u;
+    for (uint32_t q = 0; q < c.nexc; ++q) m |= 1u << layer_of((uint32_t)xs[q] >> 2);
+    return m;
+}
+
+// Does the slice act on a layer that holds off-path items (bit L of LX)?
+// Its router/data swaps act within a layer, its controlled swaps between
+// layers L and L + 1, the fetch on the leaf layer; load and bus act on the
+// root, which is on every path.
+__device__ __forceinline__ bool slice_touches(const SliceOps &op, uint32_t LX, int n) {
+    return ((op.iswap | op.cswap | (op.cswap << 1)) & LX) != 0u || (op.fetch >= 0 && ((LX >> (n - 1)) & 1u));
+}
+
+// One slice of gates.  LX = xs_layers(c, xs), kept current here.
+__device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16_t *xs, const Ctx &C, uint32_t &LX) {
     if (fast_slice(op, c, C)) return true;
+    if (c.nexc && !slice_touches(op, LX, C.n)) {
+        // the off-path items sit this slice out: path A alone, as long as no
+        // item leaves it (an off-path list never coexists with a path B)
+        CompR a = c;
+        a.nexc = 0;
+        if (fast_slice(op, a, C) && a.ldiv < 0) {
+            a.nexc = c.nexc;
+            c = a;
+            return true;
+        }
+    }
     int okv;
     const CompR h = hybrid_slice(op, c, xs, C, &okv);
-    if (okv) { c = h; return true; }
+    if (okv) {
+        c = h;
+        LX = xs_layers(c, xs);
+        return true;
+    }
     c = slow_slice(op, c, xs, C, &okv);
+    LX = xs_layers(c, xs);
     return okv != 0;
 }
 
@@ -859,34 +891,40 @@ __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *
 }
 
 // first element (code) of the mask J(x) = C_s n X(x) and its size; the
-// code is 0xFFFF... when the mask is empty.  cl2 = path-word positions that
-// hold any candidate this slice: path sites elsewhere cannot be in J.
+// code is 0xFFFF... when the mask is empty.  The canonical order (ascending
+// site, then level) is ascending code, so the first element is the smallest
+// code: no ordered merge of paths A, B and the off-path list is needed.
+// cl2 = path-word positions (2L + slot) that hold any candidate this slice:
+// an excited site at another position, on or off the paths, cannot be in J.
 __device__ __forceinline__ uint32_t mask_first(const CompR &c, const uint16_t *xs, const Ctx &C,
                                                const uint32_t *candbits, uint32_t cl2, uint32_t &cnt) {
-    if (c.nexc == 0 && c.pwB == 0) {
-        // path A only: its sites increase with the path-word bit (deeper layer, larger node)
-        uint32_t first = 0xFFFFFFFFu;
-        cnt = 0;
-        for (uint32_t w = c.pw & cl2; w; w &= w - 1u) {
-            const int b = __ffs(w) - 1;
-            const uint32_t site = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
-            if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
-            if (cnt == 0) first = (site << 1) | ((C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 1u : 0u);
-            ++cnt;
-        }
-        return first;
-    }
-    uint32_t wA = c.nexc ? c.pw : (c.pw & cl2), wB = c.pwB & cl2, xi = 0, first = 0xFFFFFFFFu;
-    const uint32_t iB = wB ? b_addr(c, C) : 0u;
+    uint32_t first = 0xFFFFFFFFu;
     cnt = 0;
-    for (;;) {
-        const uint32_t code = next_site(c, xs, C, iB, wA, wB, xi);
-        if (code == 0xFFFFFFFFu) return first;
-        const uint32_t site = code >> 1;
+    for (uint32_t w = c.pw & cl2; w; w &= w - 1u) {
+        const int b = __ffs(w) - 1;
+        const uint32_t site = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
         if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
-        if (cnt == 0) first = code;
+        const uint32_t code = (site << 1) | ((C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 1u : 0u);
+        first = min(first, code);
         ++cnt;
     }
+    if (c.pwB & cl2) {
+        const uint32_t iB = b_addr(c, C);
+        for (uint32_t w = c.pwB & cl2; w; w &= w - 1u) {
+            const int b = __ffs(w) - 1;
+            const uint32_t site = 2u * path_node(iB, C.n, b >> 1) + (uint32_t)(b & 1);
+            if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+            first = min(first, site << 1);
+            ++cnt;
+        }
+    }
+    for (uint32_t q = 0; q < c.nexc; ++q) {
+        const uint32_t site = xs[q] >> 1;
+        if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+        first = min(first, (uint32_t)xs[q]);
+        ++cnt;
+    }
+    return first;
 }
 
 // where a site sits in the component: 0 = path A bit b, 1 = path B bit b,
@@ -1683,8 +1721,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             if (alive) {
                 const int slast = final_epoch ? T - 1 : s1;
                 nsl += (uint32_t)(slast - s_prev);
+                uint32_t LX = xs_layers(c, xs);
                 for (int s = s_prev + 1; s <= slast; ++s) {
-                    if (!apply_slice(P.ops[s], c, xs, C)) { capfail = true; break; }
+                    if (!apply_slice(P.ops[s], c, xs, C, LX)) { capfail = true; break; }
                     if (npev) {                             // depolarizing faults of slice s
                         bool okall = true;
                         for (uint32_t e = S.pslice_off[s]; e < S.pslice_off[s + 1]; ++e) {
@@ -1694,6 +1733,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                             if (!okv) { okall = false; break; }
                         }
                         if (!okall) { capfail = true; break; }
+                        LX = xs_layers(c, xs);
                     }
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
