@@ -869,25 +869,46 @@ __device__ __forceinline__ int excited_count(const CompR &c) {
 }
 
 // Mask J(x) = C_s n X(x) in canonical order (ascending site, then level):
-// checks that its first np elements equal pref[] and returns the next one.
-// Returns -2 on a prefix mismatch, -1 if the mask equals the prefix.
+// checks that its first np elements equal pref[] (ascending) and returns the
+// next one.  Returns -2 on a prefix mismatch, -1 if the mask equals the
+// prefix.  The order is ascending code, so J(x) starts with pref exactly when
+// it holds every code of pref and no other code below pref[np - 1]; the next
+// element is then the smallest code above it.  No ordered walk is needed.
 __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *xs, const Ctx &C,
                                                 const uint32_t *candbits, const uint32_t *pref, int np) {
-    const uint32_t iB = b_addr(c, C);
-    uint32_t wA = c.pw, wB = c.pwB, xi = 0;
+    const uint32_t last = np > 0 ? pref[np - 1] : 0u;
+    uint32_t next = 0xFFFFFFFFu;
     int got = 0;
-    for (;;) {
-        const uint32_t code = next_site(c, xs, C, iB, wA, wB, xi);
-        if (code == 0xFFFFFFFFu) return got == np ? -1 : -2;
-        const uint32_t site = code >> 1;
-        if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
-        if (got < np) {
-            if (code != pref[got]) return -2;
-            ++got;
-            continue;
+    bool bad = false;
+    auto take = [&](uint32_t code) {
+        if (np > 0 && code <= last) {
+            bool in = false;
+            for (int j = 0; j < np; ++j) in |= pref[j] == code;
+            if (in) ++got; else bad = true;
+        } else {
+            next = min(next, code);
         }
-        return (long long)code;
+    };
+    for (uint32_t w = c.pw; w; w &= w - 1u) {
+        const int b = __ffs(w) - 1;
+        const uint32_t site = 2u * path_node(C.i, C.n, b >> 1) + (uint32_t)(b & 1);
+        if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+        take((site << 1) | ((C.enc == QRAM_QUTRIT && ((c.pwR >> b) & 1u)) ? 1u : 0u));
     }
+    if (c.pwB) {
+        const uint32_t iB = b_addr(c, C);
+        for (uint32_t w = c.pwB; w; w &= w - 1u) {
+            const int b = __ffs(w) - 1;
+            const uint32_t site = 2u * path_node(iB, C.n, b >> 1) + (uint32_t)(b & 1);
+            if ((candbits[site >> 5] >> (site & 31u)) & 1u) take(site << 1);
+        }
+    }
+    for (uint32_t q = 0; q < c.nexc; ++q) {
+        const uint32_t site = xs[q] >> 1;
+        if ((candbits[site >> 5] >> (site & 31u)) & 1u) take((uint32_t)xs[q]);
+    }
+    if (bad || got != np) return -2;
+    return next == 0xFFFFFFFFu ? -1 : (long long)next;
 }
 
 // first element (code) of the mask J(x) = C_s n X(x) and its size; the
@@ -1943,7 +1964,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         c1 = mask_first(c, nullptr, C, S.candbits, S.cl2, mcnt);
                         ce = c.e;
                         if (uni) {
-                            if (c.e >= 4096) capfail = true;             // the key holds 12 bits of e
+                            if (c.e >= 4096 || c.e >= H) capfail = true;  // the key holds 12 bits of e
                         } else {
                             const double ae = apow(S, c.e);
                             w = w2 * ae * ae;
@@ -1979,6 +2000,10 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             {
                 const uint32_t *sk0 = scr.selk + slot * NW * (size_t)scr.selseg;
                 const double *sw0 = scr.selw + slot * NW * (size_t)scr.selseg;
+                // block sum of the weights of the selected entries; equal
+                // magnitudes count their exponents in the integer histogram
+                // and fold its non-empty bins (FP64 work per bin, not per
+                // entry: a first jump can select tens of thousands)
                 auto Fsum = [&](uint32_t cmax, uint32_t ceq, bool eq_only_single, int *multi) {
                     double f = 0.0;
                     int mm = 0;
@@ -1991,23 +2016,33 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                             if (eq_only_single && code == ceq && !in) mm = 1;
                             if (in) {
                                 if (uni) {
-                                    const double ae = apow(S, (int)(kv >> 20));
-                                    f += w2u * ae * ae;
+                                    const uint32_t ex = kv >> 20;
+                                    if (ex < (uint32_t)H) atomicAdd(&hall[ex], 1u);
                                 } else {
                                     f += sw[e];
                                 }
                             }
                         }
                     }
+                    if (uni) {
+                        __syncthreads();
+                        for (int b = (int)threadIdx.x; b < H; b += NT) {
+                            const uint32_t cnt = hall[b];
+                            if (!cnt) continue;
+                            const double ae = apow(S, b);
+                            f += (double)cnt * (ae * ae);
+                            hall[b] = 0;
+                        }
+                    }
                     if (multi) *multi = mm;
-                    return f;
+                    return block_sum(f, S.redA, S) * (uni ? w2u : 1.0);
                 };
                 uint32_t lo = 0, hi = ncodes;
                 double Flo = 0.0;
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi) >> 1;
                     const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
-                    const double f = block_sum(Fsum(cmid, 0, false, nullptr), S.redA, S);
+                    const double f = Fsum(cmid, 0, false, nullptr);
                     if (O + f > tgt) hi = mid;
                     else { lo = mid + 1; Flo = f; }
                 }
@@ -2015,7 +2050,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     const uint32_t code = 2u * (cand[cb0 + (lo >> 1)] & 0xFFFFu) + (lo & 1u);
                     O += Flo;
                     int mm = 0;
-                    const double wex = block_sum(Fsum(0, code, true, &mm), S.redA, S);
+                    const double wex = Fsum(0, code, true, &mm);
                     const int multi = __syncthreads_or(mm);
                     if (threadIdx.x == 0) pref[0] = code;
                     __syncthreads();
