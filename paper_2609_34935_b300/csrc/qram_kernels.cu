@@ -1091,14 +1091,22 @@ __device__ __forceinline__ uint4 pack(const CompR &c, bool qubit, uint32_t col, 
     return v;
 }
 
+// A component's off-path list is a 64-byte slot (kXcap entries, 16-byte
+// aligned: the scratch base is 256-byte aligned), moved in 16-byte pieces;
+// xs must be 16-byte aligned.  Entries past nexc are don't-cares.
+static_assert(kXcap % 8 == 0, "off-path slots move in 16-byte pieces");
 __device__ __forceinline__ void load_exc(const Scratch &scr, size_t g, uint32_t nexc, uint16_t *xs) {
-    for (uint32_t q = 0; q < nexc; ++q) xs[q] = scr.exc[g * kXcap + q];
+    const uint4 *src = reinterpret_cast<const uint4 *>(scr.exc + g * kXcap);
+    uint4 *dst = reinterpret_cast<uint4 *>(xs);
+    for (uint32_t q = 0; q < (nexc + 7u) / 8u; ++q) dst[q] = src[q];
 }
 
 __device__ __forceinline__ void store_comp(const Scratch &scr, size_t g, const CompR &c, const uint16_t *xs,
                                            bool qubit, uint32_t col, uint32_t addr) {
     scr.cs[g] = pack(c, qubit, col, addr);
-    for (uint32_t q = 0; q < c.nexc; ++q) scr.exc[g * kXcap + q] = xs[q];
+    uint4 *dst = reinterpret_cast<uint4 *>(scr.exc + g * kXcap);
+    const uint4 *src = reinterpret_cast<const uint4 *>(xs);
+    for (uint32_t q = 0; q < (c.nexc + 7u) / 8u; ++q) dst[q] = src[q];
 }
 
 __device__ __forceinline__ double col_w2(const Params &P, uint32_t col) {
@@ -1717,7 +1725,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             const uint4 cur = nxt;
             if (r + NT < ncomp_pass) nxt = scr.cs[cbase + r + NT];
             CompR c;
-            uint16_t xs[kXcap];
+            alignas(16) uint16_t xs[kXcap];
             uint32_t lab = 0, addr = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
             double w = 0.0;
             uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | empty/ground << 2 | overlap sign + 1
@@ -2064,7 +2072,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 if (level > 0) {
                     double we = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
+                        CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
                         unpack(scr.cs[cbase + r], qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
@@ -2085,7 +2093,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
                     double f = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
+                        CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
                         unpack(scr.cs[cbase + r], qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
@@ -2104,7 +2112,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     // group with weight (the oracle's rule); descend on the largest code
                     uint32_t best = 0xFFFFFFFFu;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; uint16_t xs[kXcap]; uint32_t lab, addr;
+                        CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
                         unpack(scr.cs[cbase + r], qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
