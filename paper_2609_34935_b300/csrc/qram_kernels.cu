@@ -1542,7 +1542,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
 
     // ---- 4. epochs ----------------------------------------------------------
     // equal-magnitude inputs: weights are w2u * a^(2e), summed as integer
-    // histograms over e (all, empty mask / ground, signed overlap)
+    // histograms over e: all; the ground tree (final epoch) or, before it,
+    // the complement of the empty mask (the rarer case: one atomic less for
+    // most components); signed overlap
     const double w2u = P.w2u ? *P.w2u : 0.0;
     // (a qutrit phase w^m makes the overlap complex: those weights go through FP64)
     const bool uni = w2u > 0.0 && !(depol && P.enc == QRAM_QUTRIT);
@@ -1690,11 +1692,12 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     if (final_epoch) {                      // the orbit ends in the ground tree, Walsh coefficient +1
                         atomicAdd(&hemp[E], 1u);
                         atomicAdd(&hov[E], 1);
-                    } else if (!all && !tm) {
-                        atomicAdd(&hemp[E], 1u);
-                    } else if (!all) {
-                        const double ae = apow(S, E);
-                        wempty += ae * ae * qp;
+                    } else if (all || tm) {
+                        atomicAdd(&hemp[E], 1u);            // not wholly in the empty mask
+                        if (!all) {
+                            const double ae = apow(S, E);
+                            wempty += ae * ae * qp;
+                        }
                     }
                 } else {
                     const double w2 = col_w2(P, b);
@@ -1728,7 +1731,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             alignas(16) uint16_t xs[kXcap];
             uint32_t lab = 0, addr = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
             double w = 0.0;
-            uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | empty/ground << 2 | overlap sign + 1
+            uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | ground (final) or non-empty mask << 2 | overlap sign + 1
             Ctx C;
             if (alive) {
                 unpack(cur, qubit, c, lab, addr);
@@ -1775,7 +1778,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         wsum += w;
                         if (mcnt == 0) wempty += w;
                     } else {
-                        if (c.e < H) hkey = ((uint32_t)c.e << 3) | ((mcnt == 0 ? 1u : 0u) << 2) | 1u;
+                        if (c.e < H) hkey = ((uint32_t)c.e << 3) | ((mcnt != 0 ? 1u : 0u) << 2) | 1u;
                     }
                 } else {
                     const double ae = apow(S, c.e);
@@ -1870,7 +1873,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 if (!ca) continue;
                 const double ae = apow(S, b), a2 = ae * ae;
                 wsum += (double)ca * a2;
-                const uint32_t ce = hemp[b];
+                const uint32_t ce = final_epoch ? hemp[b] : ca - hemp[b];   // ground / empty mask
                 if (ce) wempty += (double)ce * a2;
                 const int co = hov[b];
                 if (co) ovl += (double)co * ae;
