@@ -1566,10 +1566,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         // every component is on a noiseless orbit, so a candidate on a position
         // no orbit can excite leaves J empty and needs no draw; after it, only
         // candidates in the subtree a jump damaged (and on the path to it)
-        int s1 = s_prev + 1;
+        int s1 = T;
         {
+            // first set bit at or after s_prev + 1 of the 128-slice mask
             const uint32_t *m = jumped ? S.syncmask + 4 : S.syncmask;
-            while (s1 < T && !((m[s1 >> 5] >> (s1 & 31)) & 1u)) ++s1;
+            const int s0 = s_prev + 1;
+            for (int wd = s0 >> 5; wd < 4; ++wd) {
+                const uint32_t bits = m[wd] & (wd == (s0 >> 5) ? (0xFFFFFFFFu << (s0 & 31)) : 0xFFFFFFFFu);
+                if (bits) { s1 = min(T, 32 * wd + __ffs(bits) - 1); break; }
+            }
         }
         const bool final_epoch = s1 >= T;
         if (threadIdx.x == 0) {
@@ -2176,12 +2181,14 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 if (depol || tree_related(u, r)) atomicOr(&S.syncmask[4 + (sc >> 5)], 1u << (sc & 31u));
             }
         }
-        // clear the candidate bitmaps of s1
+        // clear the candidate bitmaps of s1 (the hit bitmap word by word: a
+        // candidate near the root covers most of it)
         for (uint32_t c = S.slice_off[s1] + threadIdx.x; c < S.slice_off[s1 + 1]; c += NT) {
             const uint32_t site = cand[c] & 0xFFFFu;
             atomicAnd(&S.candbits[site >> 5], ~(1u << (site & 31u)));
-            if (lazy_pre) mark_leaves(S.hitbits, n, site >> 1, false);
         }
+        if (lazy_pre)
+            for (uint32_t wd = threadIdx.x; wd < ((1u << n) + 31u) / 32u; wd += NT) S.hitbits[wd] = 0u;
         __syncthreads();
         s_prev = s1;
     }
