@@ -70,6 +70,9 @@ def world_throughput(t_local: float, steps: int, ntraj: int, dist=None) -> tuple
 # lookups and adds), the hit test and a histogram count; a component-epoch
 # is the pack/unpack, mask and histogram bookkeeping of an explicit pass
 OPS_PER_UNIT = {"draws": 140, "comp_slices": 12, "branch_epochs": 12, "comp_epochs": 30}
+# 32-bit integer add/logic lanes per SM per clock (the unified FP32/INT32
+# cores; qram_measure_peaks measures 92 % of SMs x 128 x 2032 MHz)
+INT32_LANES = 128
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traj_kernel_qubit_n12k4_traffic.json")
 
 
@@ -227,9 +230,15 @@ def main():
                     help="fidelity vs n (qubit, k=3, 500-branch random input, 200 trajectories per point)")
     ap.add_argument("--profile-case", type=float, default=None, metavar="GAMMA",
                     help="one launch of 296 trajectories (148 CTAs of 512 threads) at this gamma, for ncu")
+    ap.add_argument("--configs", action="store_true",
+                    help="the other workload configurations (qutrit n=3, qubit n=6, qutrit n=10): throughput, "
+                         "work and measured peaks")
+    ap.add_argument("--only", type=int, default=None, help="with --configs: run only this configuration index")
     args = ap.parse_args()
     if args.profile_case is not None:
         return run_profile_case(args.profile_case)
+    if args.configs:
+        return run_configs(args)
     if args.scan:
         return run_scan(args)
     if args.impl == "reference":
@@ -386,16 +395,25 @@ def main():
     ops = sum(work[k] * OPS_PER_UNIT[k] for k in OPS_PER_UNIT) / args.steps
     sm_mhz = cl.get("sm_mhz") or 2032.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_int = nsm * 64 * sm_mhz * 1e6 / 1e12          # Tops/s: 64 INT32 lanes/SM/clock
+    peak_int = nsm * INT32_LANES * sm_mhz * 1e6 / 1e12  # Tops/s
     launch_s = t_dev / args.steps
     achieved = ops / launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_int, "unit": "Tops/s (INT32)",
             "frac": achieved / peak_int, "traffic": _traffic_per_step(),
             "note": "algorithmic INT32 ops per step launch from the kernel's work counters x ops per unit "
-                    f"{OPS_PER_UNIT} / launch time from CUDA events; peak derived: SMs x 64 INT32 lanes/clock x "
-                    "median SM clock under load (not a measured peak); traffic: DRAM read+write bytes of one "
+                    f"{OPS_PER_UNIT} / launch time from CUDA events; peak derived: SMs x {INT32_LANES} INT32 "
+                    "lanes/clock x median SM clock under load (measured_peaks: the measured add/logic rate); "
+                    "traffic: DRAM read+write bytes of one "
                     "step launch from an ncu capture of the same kernel sources, else null",
             "work_per_step": {k: v / args.steps for k, v in work.items()}, "variant_threads": variant}
+    try:
+        from paper_2609_34935_b300 import measure_peaks
+        mp = measure_peaks(local)
+        roof["measured_peaks"] = {"int32_tops": mp["int32_ops"] / 1e12, "fp64_tflops": mp["fp64_flops"] / 1e12,
+                                  "frac_of_measured_int32": achieved / (mp["int32_ops"] / 1e12),
+                                  "how": "qram_measure_peaks (independent add+xor / FP64 FMA chains on every SM)"}
+    except Exception as e:               # pragma: no cover
+        roof["measured_peaks"] = {"error": str(e)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -458,6 +476,93 @@ def run_scan(args):
                               "of the same strength (eps = gamma, every tree site active; n <= 8, n <= 6 at 1e-3)",
                       "seconds": t1 - t0, "rows": rows,
                       "seconds_eps_eq_gamma": time.perf_counter() - t1, "rows_eps_eq_gamma": rows_eps}), flush=True)
+    return 0
+
+
+# The workload configurations besides the bench's own (qubit n=12, k=4):
+# (name, encoding, n, k, gammas, trajectories, seeds per gamma).  All use the
+# data-loading input (every address, equal weights, zero bus) and i.i.d.
+# random cell bits.
+CONFIGS = [
+    ("qutrit n=3 (8 cells), k=1, gamma 1e-3, 1000 trajectories", W.QUTRIT, 3, 1, [1e-3], 1000, [1001]),
+    ("qubit n=6 (64 cells), k=1, gamma 1e-4 / 1e-3 / 1e-2, 1e4 trajectories each", W.QUBIT, 6, 1,
+     [1e-4, 1e-3, 1e-2], 10_000, [2001, 2002, 2003]),
+    ("qutrit n=10 (1024 cells), k=1, gamma 1e-3, 1e5 trajectories in one graph-captured launch", W.QUTRIT, 10, 1,
+     [1e-3], 100_000, [3001]),
+]
+
+
+def run_configs(args):
+    """Each configuration at each of its gammas: one graph-captured pruned
+    launch over all its trajectories (best of three, CUDA events on the
+    simulator's stream), full mode on up to 2e4 of the same trajectories,
+    the kernel's work counters and the INT32 rate they give, against the
+    derived INT32 peak and the measured integer and FP64 peaks."""
+    import torch
+    from paper_2609_34935_b300 import QramSim, measure_peaks
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    peaks = measure_peaks(0)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    rows = []
+    for ci, (name, enc, n, k, gammas, ntraj, seeds) in enumerate(CONFIGS):
+        if args.only is not None and ci != args.only:
+            continue
+        for g, seed in zip(gammas, seeds):
+            stream = torch.cuda.Stream(device=dev)
+            sim = QramSim(W.data_loading(enc, n, k, seed=seed), seed=seed, device=0, stream=stream)
+            sim.set_gamma_bound(g)
+            with torch.cuda.stream(stream):
+                variant = sim.autotune("pruned", g, min(ntraj, 2000))
+            gam = torch.full((ntraj,), g, dtype=torch.float64, device=dev)
+            out = torch.empty((ntraj, 48), dtype=torch.uint8, device=dev)
+            traj0 = torch.zeros(1, dtype=torch.int64, device=dev)
+            graph = sim.graph("pruned", gam, out, traj0)
+
+            def timed(fn, reps):
+                with torch.cuda.stream(stream):
+                    fn()
+                    stream.synchronize()
+                    best = float("inf")
+                    for _ in range(reps):
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        fn()
+                        b.record(stream)
+                        b.synchronize()
+                        best = min(best, a.elapsed_time(b) / 1e3)
+                return best
+
+            sim.work_counters(reset=True)
+            t_p = timed(graph, 3)
+            work = {kk: v / 4 for kk, v in sim.work_counters(reset=True).items()}   # warm-up + 3 timed launches
+            rp = sim.results(out)
+            nf = min(ntraj, 20_000)
+            gf, of = gam[:nf], torch.empty((nf, 48), dtype=torch.uint8, device=dev)
+            t_f = timed(lambda: sim.run_full(0, gf, of), 1)
+            rf = sim.results(of)
+            graph.close()
+            sim.close()
+            ops = sum(work[kk] * OPS_PER_UNIT[kk] for kk in OPS_PER_UNIT)
+            achieved = ops / t_p
+            peak_derived = nsm * INT32_LANES * 2032e6
+            rows.append({
+                "config": name, "gamma": g, "trajectories": ntraj, "variant_threads": variant,
+                "pruned_traj_per_s": ntraj / t_p, "full_traj_per_s": nf / t_f, "speedup": (ntraj / t_p) / (nf / t_f),
+                "mean_fidelity": float(rp["fidelity"].mean()),
+                "bad_fraction_mean": float(np.mean(rp["bad"]) / (1 << n)),
+                "max_abs_fidelity_diff_full": float(np.max(np.abs(rp["fidelity"][:nf] - rf["fidelity"]))),
+                "status_ok": bool((rp["status"] == 0).all() and (rf["status"] == 0).all()),
+                "work_per_launch": work,
+                "int32": {"achieved_tops": achieved / 1e12, "frac_of_derived": achieved / peak_derived,
+                          "frac_of_measured": achieved / peaks["int32_ops"]},
+            })
+    print(json.dumps({"configs": rows, "measured_peaks": {
+        "fp64_tflops": peaks["fp64_flops"] / 1e12, "int32_tops": peaks["int32_ops"] / 1e12,
+        "how": "qram_measure_peaks: 8 independent FMA (FP64) or add+xor (INT32) chains per thread on every SM, "
+               "best of 5 launches"},
+        "int32_peak_derived_tops": nsm * INT32_LANES * 2032e6 / 1e12}))
     return 0
 
 

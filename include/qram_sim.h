@@ -343,6 +343,17 @@ int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k, int32_t nu
                     uint32_t ntraj, const double *gamma, double gamma_max, qram_result_t *out,
                     void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Roofline denominators (no paper counterpart: a measurement utility).
+ * Measures on `device` the throughput of FP64 fused multiply-adds
+ * (*fp64_flops, FLOP/s at 2 per FMA) and of 32-bit integer add and logic
+ * instructions (*int32_ops, ops/s), with kernels of eight independent
+ * dependency chains per thread on every SM; best of five launches after one
+ * untimed.  Synchronous; allocates and frees a small device buffer.  Returns
+ * QRAM_E_ARG for null pointers, QRAM_E_CUDA on a CUDA error.
+ * ------------------------------------------------------------------------- */
+int qram_measure_peaks(int device, double *fp64_flops, double *int32_ops);
+
 /* Static message for a QRAM_* code. */
 const char *qram_strerror(int code);
 

@@ -109,6 +109,7 @@ def load_library(build_if_missing: bool = True):
     L.qram_set_variant.argtypes = [vp, C.c_int]
     L.qram_get_variant.argtypes = [vp]
     L.qram_autotune.argtypes = [vp, C.c_int, f64, u32, u64, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    L.qram_measure_peaks.argtypes = [C.c_int, C.POINTER(f64), C.POINTER(f64)]
     L.qram_strerror.argtypes = [C.c_int]
     L.qram_strerror.restype = C.c_char_p
     _lib = L
@@ -339,6 +340,15 @@ class QramSim:
         o = np.zeros(4, np.uint64)
         _check(self.lib.qram_work_counters(self.h, o.ctypes.data, 1 if reset else 0), "qram_work_counters")
         return {"draws": int(o[0]), "comp_slices": int(o[1]), "branch_epochs": int(o[2]), "comp_epochs": int(o[3])}
+
+
+def measure_peaks(device: int = 0) -> dict:
+    """Measured FP64 FMA (FLOP/s) and 32-bit integer add/logic (ops/s)
+    throughput of the device (qram_measure_peaks): roofline denominators."""
+    L = load_library()
+    fp, it = C.c_double(), C.c_double()
+    _check(L.qram_measure_peaks(device, C.byref(fp), C.byref(it)), "qram_measure_peaks")
+    return {"fp64_flops": fp.value, "int32_ops": it.value}
 
 
 class QramServer:

@@ -6,7 +6,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["qram_kernels.cu", "qram_api.cu", "qram_server.cu", "qram_noalloc.cu"]
+SOURCES = ["qram_kernels.cu", "qram_api.cu", "qram_server.cu", "qram_noalloc.cu", "qram_peaks.cu"]
 LIB = os.path.join(HERE, "libqram_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
