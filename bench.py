@@ -118,7 +118,10 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}_{os.getpid()}.csv")
+        # the raw samples are kept in QRAM_CLOCKS_DIR (default: the system's temporary directory)
+        import tempfile
+        d = os.environ.get("QRAM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_bench_{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
