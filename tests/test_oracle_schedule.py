@@ -37,6 +37,27 @@ def test_event_times_eq4(n, k):
         sorted([2 * l + 1 for l in range(n)] + [T - 2 * l - 1 for l in range(n)])
 
 
+@pytest.mark.parametrize("n", range(1, 15))
+def test_data_qubits_never_meet_a_router_swap(n):
+    """No router/data swap of a layer fires while a data qubit is in that
+    layer.  Every item moves one layer per slice whatever its path, so this
+    holds on and off the path: a data qubit's value never reaches a router,
+    and its position depends on the routers alone (the schedule of Sec. II,
+    data windows of Eq. (5))."""
+    for k in range(1, n + 1):
+        sched = core.schedule(n, k)
+        layers = {}                                  # slice -> layers holding a data qubit after its gates
+        for t in range(k):
+            tin, tf, tout = cf.tau_in(n, t), cf.tau_fetch(n, t), cf.tau_out(n, t)
+            for s in range(tin, tout):
+                L = s - tin if s < tf else (n - 1 if s == tf else n - 1 - (s - tf))
+                layers.setdefault(s, set()).add(L)
+        swaps = [(s, L) for s, g, L in sched if g == "iswap"]
+        assert len(swaps) == 2 * n
+        for s, L in swaps:
+            assert L not in layers.get(s - 1, set()) and L not in layers.get(s, set()), (n, k, s, L)
+
+
 def test_injection_count_sec5b():
     g = GOLD["single_fault_injection"]
     p = W.data_loading(W.QUBIT, g["n"], g["k"], seed=3)
