@@ -42,7 +42,7 @@ class _Hist(C.Structure):
     _fields_ = [("ncand", C.c_int32), ("cand_slice", C.c_void_p), ("cand_site", C.c_void_p),
                 ("aux_u", C.c_void_p), ("final_u", C.c_double),
                 ("nflip", C.c_int32), ("flip_slice", C.c_void_p), ("flip_site", C.c_void_p),
-                ("eps", C.c_double)]
+                ("eps", C.c_double), ("stop_slice", C.c_int32)]
 
 
 TRAJ_DTYPE = np.dtype([("fidelity", "f8"), ("fidelity_unsampled", "f8"), ("p_ground", "f8"),
@@ -131,6 +131,7 @@ class History:
     aux_u: dict | None = None      # slice -> u
     final_u: float | None = None
     flips: list | None = None      # [(slice, site)] X flips (qubit)
+    stop_slice: int = 0            # > 0: return the state after this slice's damping layer
 
 
 @dataclass
@@ -165,6 +166,7 @@ def run_one(prob, seed: int, traj: int, gamma: float, hist: History | None = Non
                   _ptr(cq).value if len(cq) else None, _ptr(au).value,
                   math.nan if hist.final_u is None else hist.final_u,
                   len(fl), _ptr(fs).value if fl else None, _ptr(fq).value if fl else None)
+        h.stop_slice = int(hist.stop_slice)
         if len(cs) == 0:
             z = np.zeros(1, np.int32)
             keep.append(z)

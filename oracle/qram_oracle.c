@@ -113,6 +113,9 @@ typedef struct {
     int32_t nflip;
     const int32_t *flip_slice, *flip_site;   /* X flips after the gates (qubit) */
     double eps;                              /* depolarizing strength (sampled events) */
+    int32_t stop_slice;                      /* > 0: stop after this slice's damping layer and
+                                              * return that state (an observation point for tests;
+                                              * the outputs then describe the partial query) */
 } ohist;
 
 typedef struct {
@@ -861,6 +864,7 @@ static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t 
             out->jumps++;
             out->jump_sites += (uint32_t)J.n;
         }
+        if (H && H->stop_slice == s) break;
     }
 
     /* final tree measurement (S5) and fidelity (S6) */

@@ -1,0 +1,52 @@
+"""After a fired router jump, the data qubits stay in product form.
+
+Every item moves one layer per slice whatever its path, and no router/data
+swap of a layer fires while a data qubit is in that layer, so a data qubit's
+value never reaches a router.  After a jump that resets a router, a
+surviving branch's 2^k data configurations (the first Hadamard wall's
+components) therefore share one address part and one set of (perturbed)
+data-qubit paths, and each data qubit t with value 1 is damped on every
+slice it spends in the tree: the window of Eq. (5), whatever its path.  Between the
+walls the configuration weights of a branch are then C_i * prod_t a^(2 m_t c_t),
+m_t = the slices of that window up to the observation point.  The oracle
+evolves every configuration explicitly; this checks its state against that
+form."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import core
+
+
+def _window(n, t, s_stop):
+    """Damping layers data qubit t has spent in the tree after slice s_stop."""
+    lo, hi = cf.tau_in(n, t), min(s_stop, cf.tau_out(n, t) - 1)
+    return max(0, hi - lo + 1)
+
+
+@pytest.mark.parametrize("n,k,s_stop", [(3, 2, 12), (3, 2, 14), (4, 3, 17)])
+def test_post_jump_configuration_weights_factorise(n, k, s_stop):
+    gamma = 0.1
+    a2 = 1.0 - gamma
+    p = W.data_loading(W.QUBIT, n, k, seed=7)
+    # a candidate on the root router (site 0) while it holds the routed
+    # address bit, drawn so that the jump fires: the survivors are the
+    # branches whose top address bit is 1, and the root then routes left
+    s_jump = 5
+    assert s_stop < 4 * n + 2 * k - 1                # observed before the second wall
+    h = core.History(cand_slice=[s_jump], cand_site=[0], aux_u={s_jump: 0.999}, final_u=0.5, stop_slice=s_stop)
+    out, d = core.run_one(p, 7, 0, gamma, hist=h)
+    assert out["jumps"] == 1 and out["first_jump_slice"] == s_jump
+    m = [_window(n, t, s_stop) for t in range(k)]
+    # expected weights relative to the heaviest configuration, one per value word c
+    expect = sorted((a2 ** sum(m[t] for t in range(k) if (c >> t) & 1) for c in range(1 << k)), reverse=True)
+    by = {}
+    for i, amp in zip(d.addr, d.amp):
+        by.setdefault(int(i), []).append(abs(amp) ** 2)
+    assert sorted(by) == list(range(1 << (n - 1), 1 << n))      # top address bit 1
+    for i, w in by.items():
+        assert len(w) == 1 << k, (i, len(w))
+        w = sorted(w, reverse=True)
+        rel = [x / w[0] for x in w]
+        assert np.allclose(rel, expect, rtol=1e-12, atol=0), (i, rel, expect)
