@@ -50,3 +50,26 @@ def test_post_jump_configuration_weights_factorise(n, k, s_stop):
         w = sorted(w, reverse=True)
         rel = [x / w[0] for x in w]
         assert np.allclose(rel, expect, rtol=1e-12, atol=0), (i, rel, expect)
+
+
+@pytest.mark.parametrize("s_stop", [12, 14])
+def test_jump_on_a_data_site_fixes_that_qubit(s_stop):
+    """A jump that fires on the site of data qubit 0 keeps the configurations
+    with c_0 = 1 and leaves that qubit at 0: each surviving branch keeps
+    2^(k-1) configurations, weighted by the other qubits' windows alone."""
+    n, k, gamma = 3, 2, 0.1
+    a2 = 1.0 - gamma
+    p = W.data_loading(W.QUBIT, n, k, seed=7)
+    t0 = cf.tau_in(n, 0)                 # data qubit 0 has just entered d_0 (site 1)
+    h = core.History(cand_slice=[5, t0], cand_site=[0, 1], aux_u={5: 0.999, t0: 0.999}, final_u=0.5,
+                     stop_slice=s_stop)
+    out, d = core.run_one(p, 7, 0, gamma, hist=h)
+    assert out["jumps"] == 2 and out["jump_sites"] == 2
+    by = {}
+    for i, amp in zip(d.addr, d.amp):
+        by.setdefault(int(i), []).append(abs(amp) ** 2)
+    assert sorted(by) == list(range(1 << (n - 1), 1 << n))
+    for i, w in by.items():
+        assert len(w) == 2, (i, len(w))
+        w = sorted(w, reverse=True)
+        assert abs(w[1] / w[0] - a2 ** _window(n, 1, s_stop)) < 1e-12, (i, w)
