@@ -11,6 +11,8 @@ walls the configuration weights of a branch are then C_i * prod_t a^(2 m_t c_t),
 m_t = the slices of that window up to the observation point.  The oracle
 evolves every configuration explicitly; this checks its state against that
 form."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -73,3 +75,31 @@ def test_jump_on_a_data_site_fixes_that_qubit(s_stop):
         assert len(w) == 2, (i, len(w))
         w = sorted(w, reverse=True)
         assert abs(w[1] / w[0] - a2 ** _window(n, 1, s_stop)) < 1e-12, (i, w)
+
+
+def test_data_qubit_positions_are_shared_by_the_configurations():
+    """After the router jump, with every data qubit in the tree, the excited
+    sites of a branch's 2^k configurations are one address part plus exactly
+    the subsets of k data-slot sites (the data qubits' positions, the same in
+    every configuration): the masks of the product form."""
+    n, k, gamma, s_stop = 4, 3, 0.1, 15
+    assert max(cf.tau_in(n, t) for t in range(k)) <= s_stop < min(cf.tau_out(n, t) for t in range(k))
+    p = W.data_loading(W.QUBIT, n, k, seed=7)
+    h = core.History(cand_slice=[5], cand_site=[0], aux_u={5: 0.999}, final_u=0.5, stop_slice=s_stop)
+    _, d = core.run_one(p, 7, 0, gamma, hist=h)
+    by = {}
+    for i, b, c in zip(d.addr, d.bus, d.configs):
+        by.setdefault(int(i), []).append((int(b), frozenset(c)))
+    assert len(by) == 1 << (n - 1)
+    positions = set()
+    for i, comps in by.items():
+        assert len(comps) == 1 << k and all(b == 0 for b, _ in comps)     # every data qubit is out of the bus
+        sets = [c for _, c in comps]
+        common = frozenset.intersection(*sets)
+        extras = [c - common for c in sets]
+        sites = frozenset().union(*extras)
+        assert len(sites) == k and all(site % 2 == 1 and lvl == 1 for site, lvl in sites)   # data slots
+        subsets = {frozenset(x) for r in range(k + 1) for x in itertools.combinations(sites, r)}
+        assert set(extras) == subsets, (i, extras)
+        positions.add(sites)
+    assert len(positions) > 1          # the positions depend on the branch's address bits
