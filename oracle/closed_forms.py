@@ -1,7 +1,7 @@
 """Closed forms of the paper, written out directly (test infrastructure only).
 
 Each function restates one formula; the tests compare the C oracle's explicit
-evolution against them.  Address bit "t" of Eq. (12) is the bit routed at
+evolution against them.  Address bit "t" of Eq. (14) is the bit routed at
 tree layer t, i.e. bit n-1-t of the address (most significant bit at the
 root, the leaf ordering of Eq. (7)).
 """
@@ -16,17 +16,17 @@ def slices(n: int, k: int) -> int:
 
 
 def tau_in(n: int, i: int) -> int:
-    """Eq. (4): CopyIn slice of data qubit i."""
+    """Eq. (3): CopyIn slice of data qubit i."""
     return 2 * n + 2 * i + 1
 
 
 def tau_fetch(n: int, i: int) -> int:
-    """Eq. (4): fetch slice of data qubit i."""
+    """Eq. (3): fetch slice of data qubit i."""
     return 3 * n + 2 * i + 1
 
 
 def tau_out(n: int, i: int) -> int:
-    """Eq. (4): CopyOut slice of data qubit i."""
+    """Eq. (3): CopyOut slice of data qubit i."""
     return 4 * n + 2 * i + 1
 
 
@@ -36,14 +36,14 @@ def routed_bit(i: int, n: int, t: int) -> int:
 
 
 def c_addr(i: int, n: int, k: int) -> int:
-    """Eq. (12): address exposure count of the qubit encoding."""
+    """Eq. (14): address exposure count of the qubit encoding."""
     T = slices(n, k)
     return sum(T - 2 * (2 * t + 1) for t in range(n) if routed_bit(i, n, t))
 
 
 def c_qutrit(i: int, j: int, d: int, n: int, k: int) -> int:
     """Exposure count c(i, j) of Prop. 1 under the qutrit reading: every
-    address item is excited (L or R) over the same T-4t-2 layers as Eq. (12);
+    address item is excited (L or R) over the same T-4t-2 layers as Eq. (14);
     a data slot is excited (R) while it carries a 1, for n layers before the
     fetch with the input bit and n layers after it with the output bit."""
     T = slices(n, k)
@@ -63,13 +63,13 @@ def beta(a: float, d: int) -> float:
 
 
 def hamming_amplitude(c: int, b_out: int, k: int, a: float, n: int) -> float:
-    """Eq. (11): A(c) = alpha_2n^(k-w) beta_2n^w, w = Ham(c xor b_out)."""
+    """Eq. (13): A(c) = alpha_2n^(k-w) beta_2n^w, w = Ham(c xor b_out)."""
     w = bin(c ^ b_out).count("1")
     return alpha(a, 2 * n) ** (k - w) * beta(a, 2 * n) ** w
 
 
 def good_branch_qubit(i: int, j: int, d: int, n: int, k: int, gamma: float) -> dict:
-    """Eq. (14): unnormalised no-jump end state of good branch (i, j),
+    """Eq. (16): unnormalised no-jump end state of good branch (i, j),
     word -> amplitude (times the input amplitude)."""
     a = math.sqrt(1.0 - gamma)
     pre = a ** c_addr(i, n, k)
@@ -89,19 +89,19 @@ def no_jump_norm_per_qubit(a: float, n: int) -> float:
 
 
 def leakage(gamma: float, n: int) -> float:
-    """Eq. (20): beta^2 / (alpha^2 + beta^2) with d = 2n (exact)."""
+    """Eq. (23): beta^2 / (alpha^2 + beta^2) with d = 2n (exact)."""
     a = math.sqrt(1.0 - gamma)
     al, be = alpha(a, 2 * n), beta(a, 2 * n)
     return be * be / (al * al + be * be)
 
 
 def leakage_asymptote(gamma: float, n: int) -> float:
-    """Eq. (20): leading term n^2 gamma^2 / 4."""
+    """Eq. (23): leading term n^2 gamma^2 / 4."""
     return n * n * gamma * gamma / 4.0
 
 
 def channel_error_split(gamma: float, n: int):
-    """Eq. (21): (1-a^2n)/2 = (1-a^4n)/4 + (1-a^2n)^2/4, returned as (lhs, rhs)."""
+    """Eq. (24): (1-a^2n)/2 = (1-a^4n)/4 + (1-a^2n)^2/4, returned as (lhs, rhs)."""
     a = math.sqrt(1.0 - gamma)
     lhs = (1.0 - a ** (2 * n)) / 2.0
     rhs = (1.0 - a ** (4 * n)) / 4.0 + (1.0 - a ** (2 * n)) ** 2 / 4.0
@@ -109,7 +109,7 @@ def channel_error_split(gamma: float, n: int):
 
 
 def mark_sources_total(n: int) -> float:
-    """Eq. (22): sum_v |bad(v)| / 2^n = n + (n-1)(n-2)/4."""
+    """Eq. (25): sum_v |bad(v)| / 2^n = n + (n-1)(n-2)/4."""
     return n + (n - 1) * (n - 2) / 4.0
 
 
@@ -122,7 +122,7 @@ def p_good(count_sources: int, gamma: float, n: int, k: int) -> float:
 
 def no_jump_fidelity(encoding: int, n: int, k: int, gamma: float, addr, bus, amp, memory) -> float:
     """Fidelity of a trajectory in which no jump fires: every branch follows
-    its closed form (Eq. (8) or Eq. (14)); F = |<psi_id|psi>|^2 / <psi|psi>."""
+    its closed form (Eq. (8) or Eq. (16)); F = |<psi_id|psi>|^2 / <psi|psi>."""
     a = math.sqrt(1.0 - gamma)
     ov = 0.0
     nrm = 0.0

@@ -18,6 +18,7 @@ _SRC = os.path.join(_HERE, "qram_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 
 OK, E_ARG, E_OOM, E_SCHED, E_CAP = 0, 1, 2, 3, 4
+DAMPING, DEPHASING = 0, 1      # the per-slice channel (amplitude damping; the phase-damping channel)
 G_LOAD, G_UNLOAD, G_BUS, G_ISWAP, G_CSWAP, G_FETCH = 1, 2, 3, 4, 5, 6
 GATE_NAMES = {1: "load", 2: "unload", 3: "bus", 4: "iswap", 5: "cswap", 6: "fetch"}
 
@@ -42,7 +43,7 @@ class _Hist(C.Structure):
     _fields_ = [("ncand", C.c_int32), ("cand_slice", C.c_void_p), ("cand_site", C.c_void_p),
                 ("aux_u", C.c_void_p), ("final_u", C.c_double),
                 ("nflip", C.c_int32), ("flip_slice", C.c_void_p), ("flip_site", C.c_void_p),
-                ("eps", C.c_double), ("stop_slice", C.c_int32)]
+                ("eps", C.c_double), ("stop_slice", C.c_int32), ("channel", C.c_int32)]
 
 
 TRAJ_DTYPE = np.dtype([("fidelity", "f8"), ("fidelity_unsampled", "f8"), ("p_ground", "f8"),
@@ -60,12 +61,13 @@ def lib():
         vp, i32, u64, f64 = C.c_void_p, C.c_int32, C.c_uint64, C.c_double
         L.oracle_run.argtypes = [vp, u64, u64, i32, vp, i32, vp]
         L.oracle_run_eps.argtypes = [vp, u64, u64, i32, vp, f64, i32, vp]
+        L.oracle_run_ch.argtypes = [vp, u64, u64, i32, vp, f64, i32, i32, vp]
         L.oracle_sample_paulis.argtypes = [vp, u64, u64, f64, vp, vp, vp, i32, vp]
         L.oracle_run_one.argtypes = [vp, u64, u64, f64, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_sample_faults.argtypes = [vp, u64, u64, f64, vp, vp, i32, vp, vp, vp, vp]
         L.oracle_schedule.argtypes = [i32, i32, vp, vp, vp, i32, vp]
         L.oracle_occupancy.argtypes = [vp, vp]
-        L.oracle_joint_layer.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp]
+        L.oracle_joint_layer.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp, i32]
         L.oracle_bad_range.argtypes = [i32, i32, C.c_uint32, vp, vp]
         L.oracle_bad_range.restype = None
         L.oracle_philox.argtypes = [vp, u64, vp]
@@ -111,14 +113,17 @@ def _check(rc, what):
         raise OracleError(f"{what}: oracle error {rc}")
 
 
-def run(prob, seed: int, traj0: int, gammas, nthreads: int | None = None, eps: float = 0.0) -> np.ndarray:
+def run(prob, seed: int, traj0: int, gammas, nthreads: int | None = None, eps: float = 0.0,
+        channel: int = DAMPING) -> np.ndarray:
     """Full evolution of trajectories traj0 .. traj0+len(gammas)-1; eps is the
-    depolarizing strength per (slice, site), eps < 0 meaning eps = gamma."""
+    depolarizing strength per (slice, site), eps < 0 meaning eps = gamma;
+    channel: DAMPING (amplitude damping) or DEPHASING (phase damping)."""
     g = np.ascontiguousarray(gammas, dtype=np.float64)
     out = np.zeros(len(g), dtype=TRAJ_DTYPE)
     b = _Bound(prob)
     nt = nthreads or os.cpu_count() or 1
-    _check(lib().oracle_run_eps(b.ref, seed, traj0, len(g), _ptr(g), float(eps), nt, _ptr(out)), "oracle_run")
+    _check(lib().oracle_run_ch(b.ref, seed, traj0, len(g), _ptr(g), float(eps), int(channel), nt, _ptr(out)),
+           "oracle_run")
     return out
 
 
@@ -143,13 +148,14 @@ class Dump:
 
 
 def run_one(prob, seed: int, traj: int, gamma: float, hist: History | None = None, cap: int = 1 << 20,
-            eps: float = 0.0):
+            eps: float = 0.0, channel: int = DAMPING):
     b = _Bound(prob)
     T = 6 * prob.n + 2 * prob.k
     keep = []
     hp = None
-    if hist is None and eps != 0.0:                # sampled history with depolarizing events
+    if hist is None and (eps != 0.0 or channel != DAMPING):   # sampled history, options set
         h = _Hist(0, None, None, None, math.nan, 0, None, None, float(eps))
+        h.channel = int(channel)
         keep.append(h)
         hp = C.byref(h)
     if hist is not None:
@@ -167,6 +173,8 @@ def run_one(prob, seed: int, traj: int, gamma: float, hist: History | None = Non
                   math.nan if hist.final_u is None else hist.final_u,
                   len(fl), _ptr(fs).value if fl else None, _ptr(fq).value if fl else None)
         h.stop_slice = int(hist.stop_slice)
+        h.eps = float(eps)
+        h.channel = int(channel)
         if len(cs) == 0:
             z = np.zeros(1, np.int32)
             keep.append(z)
@@ -266,8 +274,8 @@ def occupancy(prob) -> np.ndarray:
     return occ.reshape(T, M)
 
 
-def joint_layer(comps, cand, gamma: float, u: float):
-    """One joint damping layer on an explicit state.
+def joint_layer(comps, cand, gamma: float, u: float, channel: int = DAMPING):
+    """One joint layer (amplitude damping, or dephasing) on an explicit state.
 
     comps: list of (addr, bus, config, amp) with config a tuple of (site, level).
     Returns (new comps, J as tuple of (site, level))."""
@@ -292,7 +300,7 @@ def joint_layer(comps, cand, gamma: float, u: float):
     jl = np.zeros(maxe, np.uint8)
     _check(L.oracle_joint_layer(m, _ptr(addr), _ptr(bus), _ptr(ne), _ptr(sites), _ptr(lvls), _ptr(re),
                                 _ptr(im), C.byref(nout), _ptr(cnd), len(cand), gamma, u,
-                                C.byref(jn), _ptr(js), _ptr(jl)), "joint_layer")
+                                C.byref(jn), _ptr(js), _ptr(jl), int(channel)), "joint_layer")
     out = []
     for r in range(nout.value):
         cfg = tuple((int(sites[r * maxe + e]), int(lvls[r * maxe + e])) for e in range(int(ne[r])))

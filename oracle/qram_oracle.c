@@ -11,11 +11,11 @@
  *     brigade schedule of Sec. II.A (T = 6n + 2k slices, Eqs. (2)-(4));
  *   - after the gates of every slice 1..T-1, one joint damping layer on all
  *     M = 2(2^n - 1) tree sites (Sec. II.B, Eqs. (5)-(6)), resolved by the
- *     joint sampler of Sec. IV.D (Eqs. (15)-(18)): candidate set drawn in
+ *     joint sampler of Sec. IV.D (Eqs. (17)-(21)): candidate set drawn in
  *     advance, one auxiliary draw over the mask weights, K_J applied to the
  *     coherent state, normalisation once per layer;
  *   - a full evolution of EVERY input branch: the state is the unnormalised
- *     sparse dictionary {(i, j, Q) -> c} of App. A, Eq. (24), and every gate
+ *     sparse dictionary {(i, j, Q) -> c} of App. A, Eq. (27), and every gate
  *     acts entry by entry;
  *   - the bad-address union R of Algorithm 1 (subtree rule Eq. (7) for the
  *     qutrit encoding, family-divergence rule Eq. (9) for the qubit
@@ -29,7 +29,7 @@
  *      slice 2l+1, descends one layer per slice through the controlled swaps
  *      of layers 0..l-1 at slices 2l+1+m (m = 1..l), is swapped into the
  *      router of layer l at slice 3l+2, and leaves along the mirror image
- *      (slice s -> T - s).  Data qubit t enters d_0 at 2n+2t+1 (Eq. (4)),
+ *      (slice s -> T - s).  Data qubit t enters d_0 at 2n+2t+1 (Eq. (3)),
  *      descends through layers 0..n-2 at 2n+2t+1+m, is fetched at the leaf
  *      layer at 3n+2t+1, climbs at 3n+2t+1+m and leaves at 4n+2t+1.  This
  *      reading reproduces the damping rows of Tab. IV exactly.
@@ -80,6 +80,15 @@
  *   S6 fidelity: F = |<psi_id, 0_tree | psi>|^2 / <psi_Q|psi_Q> when the
  *      sampled Q is the ground configuration, else 0; its trajectory mean is
  *      the density-matrix fidelity of App. C.
+ *   S7 channel: amplitude damping (Eqs. (5)-(6)) by default.  The outlook
+ *      (Sec. VII) names dephasing as a further channel with a diagonal
+ *      no-jump operator; it is taken here as the phase-damping channel with
+ *      the same no-jump operator K0 = diag(1, a) (qutrit diag(1, a, a)) and
+ *      the jump K1 = sqrt(gamma)|1><1| (qutrit sqrt(gamma)|L><L|,
+ *      sqrt(gamma)|R><R|), so that K_J^dagger K_J is the same diagonal as
+ *      for damping and the joint sampler of Sec. IV.D applies unchanged
+ *      (Theorem 3's argument only uses that diagonal); a jump projects onto
+ *      the components holding the site excited instead of lowering it.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -94,6 +103,7 @@ enum { OR_OK = 0, OR_E_ARG = 1, OR_E_OOM = 2, OR_E_SCHED = 3, OR_E_CAP = 4 };
 enum { G_LOAD = 1, G_UNLOAD, G_BUS, G_ISWAP, G_CSWAP, G_FETCH };
 enum { ENC_QUTRIT = 0, ENC_QUBIT = 1 };
 enum { LV_W = 0, LV_L = 1, LV_R = 2 };   /* qubit: 0 / 1 use LV_W / LV_L */
+enum { CH_DAMPING = 0, CH_DEPHASING = 1 };  /* the per-slice channel (S7) */
 
 typedef struct {
     int32_t encoding, n, k;
@@ -103,7 +113,7 @@ typedef struct {
     const double *amp_re, *amp_im;
 } oproblem;
 
-/* optional fixed history for one trajectory (tests; Sec. V.A "fixed noise
+/* optional fixed history for one trajectory (tests; Sec. VI.A "fixed noise
  * histories").  Arrays may be NULL. */
 typedef struct {
     int32_t ncand;
@@ -116,6 +126,7 @@ typedef struct {
     int32_t stop_slice;                      /* > 0: stop after this slice's damping layer and
                                               * return that state (an observation point for tests;
                                               * the outputs then describe the partial query) */
+    int32_t channel;                         /* CH_DAMPING (0) or CH_DEPHASING (1), S7 */
 } ohist;
 
 typedef struct {
@@ -232,7 +243,7 @@ static int build_schedule(int n, int k, osched *S)
         for (int m = 1; m <= l; m++) add_gate(S, T - 2 * l - 1 - m, G_CSWAP, m - 1);
         add_gate(S, T - 2 * l - 1, G_UNLOAD, l);
     }
-    for (int t = 0; t < k; t++) {                 /* data qubit t, Eq. (4) */
+    for (int t = 0; t < k; t++) {                 /* data qubit t, Eq. (3) */
         add_gate(S, 2 * n + 2 * t + 1, G_BUS, t);
         for (int m = 1; m <= n - 1; m++) add_gate(S, 2 * n + 2 * t + 1 + m, G_CSWAP, m - 1);
         add_gate(S, 3 * n + 2 * t + 1, G_FETCH, t);
@@ -489,7 +500,7 @@ static int cmp_omw(const void *pa, const void *pb)
     return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
 }
 
-/* mask J(x) = C intersect X(x) with the levels of x (Eq. (18)) */
+/* mask J(x) = C intersect X(x) with the levels of x (Eq. (21)) */
 static void mask_of(const ocomp *x, const int32_t *cand, int nc, omask *m)
 {
     m->n = 0;
@@ -502,9 +513,9 @@ static void mask_of(const ocomp *x, const int32_t *cand, int nc, omask *m)
 }
 
 /* One joint layer on the state: candidate set cand[0..nc) (sorted),
- * auxiliary uniform u.  Selects J (written to Jout), applies K_J of Eq. (15)
+ * auxiliary uniform u.  Selects J (written to Jout), applies K_J of Eq. (17)
  * and normalises.  Returns 0 on success. */
-static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, double u, omask *Jout)
+static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, double u, int channel, omask *Jout)
 {
     double a = sqrt(1.0 - gamma), sg = sqrt(gamma);
     Jout->n = 0;
@@ -541,7 +552,13 @@ static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, do
         if (chosen) *Jout = list[pick].m;
         free(list);
     }
-    /* apply K_J: K1 (or K2) on the sites of J, K0 elsewhere */
+    /* apply K_J: the jump operator on the sites of J, K0 elsewhere.  Amplitude
+     * damping (S7): K1 = sqrt(g)|0><1| (qutrit: K1, K2 = sqrt(g)|W><L|,
+     * sqrt(g)|W><R|) lowers the site to the ground level.  Dephasing (S7):
+     * K1 = sqrt(g)|1><1| (qutrit: sqrt(g)|L><L|, sqrt(g)|R><R|) keeps it.
+     * Either way a component that does not hold every site of J at its
+     * level is annihilated, and K0 = diag(1, a) (diag(1, a, a)) gives a
+     * factor a per excited site outside J. */
     size_t w = 0;
     for (size_t r = 0; r < st->n; r++) {
         ocomp x = st->c[r];
@@ -550,8 +567,12 @@ static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, do
             if (get_lvl(&x, Jout->site[j]) != Jout->lvl[j]) { alive = 0; break; }
         if (!alive) continue;
         double f = 1.0;
-        for (int j = 0; j < Jout->n; j++) { f *= sg; set_lvl(&x, Jout->site[j], LV_W); }
-        for (int e = 0; e < x.ne; e++) f *= a;      /* K0: factor a per excited site */
+        for (int j = 0; j < Jout->n; j++) {
+            f *= sg;
+            if (channel == CH_DAMPING) set_lvl(&x, Jout->site[j], LV_W);
+        }
+        const int outside = channel == CH_DAMPING ? x.ne : x.ne - Jout->n;
+        for (int e = 0; e < outside; e++) f *= a;   /* K0 on the excited sites outside J */
         x.re *= f; x.im *= f;
         st->c[w++] = x;
     }
@@ -569,8 +590,9 @@ static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, do
 int oracle_joint_layer(int32_t ncomp, uint32_t *addr, uint32_t *bus, int32_t *ne, uint32_t *sites,
                        uint8_t *lvls, double *re, double *im, int32_t *ncomp_out,
                        const int32_t *cand, int32_t nc, double gamma, double u,
-                       int32_t *jn, uint32_t *jsite, uint8_t *jlvl)
+                       int32_t *jn, uint32_t *jsite, uint8_t *jlvl, int32_t channel)
 {
+    if (channel != CH_DAMPING && channel != CH_DEPHASING) return OR_E_ARG;
     ostate st = { 0 };
     for (int r = 0; r < ncomp; r++) {
         ocomp x; memset(&x, 0, sizeof(x));
@@ -581,7 +603,7 @@ int oracle_joint_layer(int32_t ncomp, uint32_t *addr, uint32_t *bus, int32_t *ne
         if (push(&st, &x)) { free(st.c); return OR_E_OOM; }
     }
     omask J;
-    int rc = joint_layer(&st, cand, nc, gamma, u, &J);
+    int rc = joint_layer(&st, cand, nc, gamma, u, channel, &J);
     if (rc) { free(st.c); return rc; }
     *jn = J.n;
     for (int j = 0; j < J.n; j++) { jsite[j] = J.site[j]; jlvl[j] = J.lvl[j]; }
@@ -787,7 +809,7 @@ static int apply_weyl(ocomp *x, uint32_t site, int qubit, int t)
 }
 
 static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t traj, double gamma,
-                    double eps, const ohist *H, otraj_out *out, ostate *dump, uint8_t *occupancy)
+                    double eps, int channel, const ohist *H, otraj_out *out, ostate *dump, uint8_t *occupancy)
 {
     int n = S->n, k = S->k, T = S->T, qubit = P->encoding == ENC_QUBIT;
     memset(out, 0, sizeof(*out));
@@ -858,7 +880,7 @@ static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t 
             else { uint32_t o[4]; draw(seed, 0, (uint32_t)s, 2u, traj, o); u = uniform53(o[0], o[1]); }
         }
         omask J;
-        if ((rc = joint_layer(&st, cand, ncs, gamma, u, &J))) goto fail;
+        if ((rc = joint_layer(&st, cand, ncs, gamma, u, channel, &J))) goto fail;
         if (J.n > 0) {
             if (out->jumps == 0) out->first_jump_slice = (uint32_t)s;
             out->jumps++;
@@ -914,7 +936,7 @@ fail:
 
 typedef struct {
     const oproblem *P; const osched *S; uint64_t seed, traj0; int ntraj;
-    const double *gamma; double eps; otraj_out *out; int next; int rc;
+    const double *gamma; double eps; int channel; otraj_out *out; int next; int rc;
     pthread_mutex_t mu;
 } ojob;
 
@@ -927,19 +949,20 @@ static void *worker(void *arg)
         pthread_mutex_unlock(&J->mu);
         if (t >= J->ntraj) break;
         const double e = J->eps < 0.0 ? J->gamma[t] : J->eps;       /* eps < 0: eps = gamma */
-        int rc = run_traj(J->P, J->S, J->seed, J->traj0 + (uint64_t)t, J->gamma[t], e, NULL, &J->out[t], NULL, NULL);
+        int rc = run_traj(J->P, J->S, J->seed, J->traj0 + (uint64_t)t, J->gamma[t], e, J->channel, NULL, &J->out[t],
+                          NULL, NULL);
         if (rc) { pthread_mutex_lock(&J->mu); J->rc = rc; pthread_mutex_unlock(&J->mu); }
     }
     return NULL;
 }
 
-int oracle_run_eps(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj, const double *gamma,
-                   double eps, int32_t nthreads, otraj_out *out);
+int oracle_run_ch(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj, const double *gamma,
+                  double eps, int32_t channel, int32_t nthreads, otraj_out *out);
 
 int oracle_run(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj,
                const double *gamma, int32_t nthreads, otraj_out *out)
 {
-    return oracle_run_eps(P, seed, traj0, ntraj, gamma, 0.0, nthreads, out);
+    return oracle_run_ch(P, seed, traj0, ntraj, gamma, 0.0, CH_DAMPING, nthreads, out);
 }
 
 /* eps: depolarizing strength per (slice, site); eps < 0 takes eps = gamma
@@ -947,6 +970,14 @@ int oracle_run(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj,
 int oracle_run_eps(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj, const double *gamma,
                    double eps, int32_t nthreads, otraj_out *out)
 {
+    return oracle_run_ch(P, seed, traj0, ntraj, gamma, eps, CH_DAMPING, nthreads, out);
+}
+
+/* channel: CH_DAMPING or CH_DEPHASING (S7) */
+int oracle_run_ch(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj, const double *gamma,
+                  double eps, int32_t channel, int32_t nthreads, otraj_out *out)
+{
+    if (channel != CH_DAMPING && channel != CH_DEPHASING) return OR_E_ARG;
     int rc = check_problem(P);
     if (rc) return rc;
     osched *S = malloc(sizeof(osched));
@@ -957,6 +988,7 @@ int oracle_run_eps(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntr
     memset(&J, 0, sizeof(J));
     if (!(eps < 1.0)) { free(S); return OR_E_ARG; }
     J.P = P; J.S = S; J.seed = seed; J.traj0 = traj0; J.ntraj = ntraj; J.gamma = gamma; J.eps = eps; J.out = out;
+    J.channel = channel;
     pthread_mutex_init(&J.mu, NULL);
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
@@ -981,7 +1013,8 @@ int oracle_run_one(const oproblem *P, uint64_t seed, uint64_t traj, double gamma
     if (!S) return OR_E_OOM;
     if ((rc = build_schedule(P->n, P->k, S))) { free(S); return rc; }
     ostate st = { 0 };
-    rc = run_traj(P, S, seed, traj, gamma, H ? H->eps : 0.0, H, out, &st, NULL);
+    if (H && H->channel != CH_DAMPING && H->channel != CH_DEPHASING) { free(S); return OR_E_ARG; }
+    rc = run_traj(P, S, seed, traj, gamma, H ? H->eps : 0.0, H ? H->channel : CH_DAMPING, H, out, &st, NULL);
     free(S);
     if (rc) return rc;
     double W = 0.0;
@@ -999,7 +1032,7 @@ int oracle_run_one(const oproblem *P, uint64_t seed, uint64_t traj, double gamma
 
 /* noiseless occupancy: occ[s*M + site] = 1 when some component holds the
  * site excited after the gates of slice s (used for the vacuous-case count
- * of Sec. V.B) */
+ * of Sec. VI.B) */
 int oracle_occupancy(const oproblem *P, uint8_t *occ)
 {
     int rc = check_problem(P);
@@ -1012,7 +1045,7 @@ int oracle_occupancy(const oproblem *P, uint8_t *occ)
     int32_t dummy = 0;
     H.cand_slice = &dummy; H.cand_site = &dummy; H.ncand = 0; H.final_u = 0.0;
     otraj_out o;
-    rc = run_traj(P, S, 0, 0, 0.0, 0.0, &H, &o, NULL, occ);
+    rc = run_traj(P, S, 0, 0, 0.0, 0.0, CH_DAMPING, &H, &o, NULL, occ);
     free(S);
     return rc;
 }

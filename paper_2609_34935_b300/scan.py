@@ -2,7 +2,7 @@
 faults of the same strength).
 
 For each (n, gamma) point: one simulator on the scan input (min(D, 2^n)
-distinct addresses, random bus words, equal weights; Sec. V.A restricted to
+distinct addresses, random bus words, equal weights; Sec. VI restricted to
 one bus column per address), ``ntraj`` pruned trajectories in one launch,
 and the trajectory mean of the fidelity with its standard error from the
 library's fixed-order reduction (qram_fidelity).  Every step runs in the

@@ -1,5 +1,5 @@
-"""Oracle pins against the closed forms: Prop. 1 (Eq. (8)), Lemma 1 (Eq. (10)),
-Theorems 1-2 (Eqs. (11), (14)), Eqs. (19)-(21), and the no-jump fidelity."""
+"""Oracle pins against the closed forms: Prop. 1 (Eq. (8)), Lemma 1 (Eq. (12)),
+Theorems 1-2 (Eqs. (13), (16)), Eqs. (22)-(24), and the no-jump fidelity."""
 import math
 
 import numpy as np
@@ -20,7 +20,7 @@ def _final(p, gamma):
 @pytest.mark.parametrize("n,k", [(2, 1), (2, 2), (3, 3), (4, 2), (5, 4), (6, 1), (8, 3)])
 @pytest.mark.parametrize("gamma", [1e-5, 1e-3, 3e-2])
 def test_qubit_good_branch_theorem2(n, k, gamma):
-    """No jump: every branch ends as Eq. (14), exactly (to rounding)."""
+    """No jump: every branch ends as Eq. (16), exactly (to rounding)."""
     p = W.random_columns(W.QUBIT, n, k, D=min(1 << n, 7), seed=n * 31 + k)
     d = _final(p, gamma)
     want = {}
@@ -86,7 +86,7 @@ def test_lemma1_limits():
 def test_leakage_law_eq20(n):
     """Per-qubit wrong-bit probability of a no-jump branch, read off the
     oracle's evolved state, equals beta^2/(alpha^2+beta^2) and approaches
-    n^2 gamma^2 / 4 with log-log slope 2 (Fig. 6(a))."""
+    n^2 gamma^2 / 4 with log-log slope 2 (Fig. 5(a))."""
     pts = []
     for gamma in [1e-5, 1e-4, 1e-3]:
         p = W.Problem(W.QUBIT, n, 1, W.memory_bits(n, 1, 8), np.array([3 % (1 << n)], np.uint32),
@@ -123,10 +123,10 @@ def test_no_jump_trajectories_equal_F0(enc, n, k, gamma):
 
 @pytest.mark.parametrize("n,k,gamma,wmax", [(6, 4, 1e-3, 0), (8, 3, 1e-4, 1), (10, 8, 1e-3, 2), (4, 2, 1e-2, 0)])
 def test_low_weight_truncation_bound(n, k, gamma, wmax):
-    """Sec. IV cost discussion: each unit of Hamming weight costs beta/alpha
+    """Sec. V cost discussion: each unit of Hamming weight costs beta/alpha
     = O(n gamma) in amplitude, so the words dropped at weight > w_max carry
     relative amplitudes at most (n gamma)^(w_max + 1), and the kept words'
-    norm deficit is the binomial tail of the Eq. (11) amplitudes."""
+    norm deficit is the binomial tail of the Eq. (13) amplitudes."""
     a = math.sqrt(1 - gamma)
     al, be = cf.alpha(a, 2 * n), cf.beta(a, 2 * n)
     assert be / al <= n * gamma

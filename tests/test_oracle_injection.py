@@ -1,4 +1,4 @@
-"""Oracle pins from single-fault injection (Sec. III.B, Sec. V.B) and from the
+"""Oracle pins from single-fault injection (Sec. III.B, Sec. VI.B) and from the
 density-matrix cross-check of App. C (ensemble means)."""
 import math
 

@@ -1,4 +1,4 @@
-"""Oracle pin for the joint damping sampler (Theorem 3, Eqs. (15)-(18)):
+"""Oracle pin for the joint damping sampler (Theorem 3, Eqs. (17)-(21)):
 averaged over the candidate draw and the auxiliary draw, one layer of the
 oracle reproduces the amplitude damping channel on every site exactly."""
 import itertools
@@ -10,8 +10,12 @@ import pytest
 from oracle import core
 
 
-def _kraus(qubit, gamma):
+def _kraus(qubit, gamma, channel=core.DAMPING):
     a, s = math.sqrt(1 - gamma), math.sqrt(gamma)
+    if channel == core.DEPHASING:              # phase damping: same no-jump operator, diagonal jumps
+        if qubit:
+            return [np.diag([1, a]), np.diag([0, s])]
+        return [np.diag([1, a, a]), np.diag([0, s, 0]), np.diag([0, 0, s])]
     if qubit:
         return [np.array([[1, 0], [0, a]]), np.array([[0, s], [0, 0]])]
     return [np.diag([1, a, a]), np.array([[0, s, 0], [0, 0, 0], [0, 0, 0]]),
@@ -63,9 +67,14 @@ def _interval_mids(comps, cand):
     return mids
 
 
+@pytest.mark.parametrize("channel", [core.DAMPING, core.DEPHASING])
 @pytest.mark.parametrize("qubit", [True, False])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_theorem3_single_layer(qubit, seed):
+def test_theorem3_single_layer(qubit, seed, channel):
+    """Theorem 3 for amplitude damping, and its argument carried to the
+    dephasing channel of the outlook: it needs only that K_J^dagger K_J is
+    diagonal with the damping values, which holds for the phase-damping
+    Kraus set with the same no-jump operator."""
     rng = np.random.default_rng(seed)
     base = 2 if qubit else 3
     sites = [1, 4, 5, 8]
@@ -85,13 +94,13 @@ def test_theorem3_single_layer(qubit, seed):
     comps = [(a, b, c, v / nrm) for a, b, c, v in comps]
     psi = _vec(comps, sites, base, nlab)
     rho_in = np.outer(psi, psi.conj())
-    want = _channel(rho_in, sites, base, nlab, _kraus(qubit, gamma))
+    want = _channel(rho_in, sites, base, nlab, _kraus(qubit, gamma, channel))
     got = np.zeros_like(rho_in)
     for mask in itertools.product([0, 1], repeat=len(sites)):
         cand = [q for q, m in zip(sites, mask) if m]
         pc = gamma ** len(cand) * (1 - gamma) ** (len(sites) - len(cand))
         for J, u, pj in _interval_mids(comps, set(cand)):
-            out, Jo = core.joint_layer(comps, cand, gamma, u)
+            out, Jo = core.joint_layer(comps, cand, gamma, u, channel)
             assert Jo == J
             v = _vec(out, sites, base, nlab)
             assert np.linalg.norm(v) == pytest.approx(1.0, abs=1e-12)

@@ -6,7 +6,7 @@ value never reaches a router.  After a jump that resets a router, a
 surviving branch's 2^k data configurations (the first Hadamard wall's
 components) therefore share one address part and one set of (perturbed)
 data-qubit paths, and each data qubit t with value 1 is damped on every
-slice it spends in the tree: the window of Eq. (5), whatever its path.  Between the
+slice it spends in the tree: the window of Eq. (4), whatever its path.  Between the
 walls the configuration weights of a branch are then C_i * prod_t a^(2 m_t c_t),
 m_t = the slices of that window up to the observation point.  The oracle
 evolves every configuration explicitly; this checks its state against that

@@ -1,7 +1,7 @@
 """Oracle pins for the noise sampler and the classifier: Philox4x32-10
 against an independent implementation, the geometric gaps of the fault
 stream against the inverse CDF, the candidate rate, Eq. (7), Eq. (9),
-Eq. (22), and the probability that an address stays good."""
+Eq. (25), and the probability that an address stays good."""
 import math
 import os
 import subprocess

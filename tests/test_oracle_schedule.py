@@ -1,5 +1,5 @@
-"""Oracle pins for the time-sliced schedule (Sec. II.A, Eqs. (2)-(4), Eq. (12),
-Sec. V.B injection count, App. C Tab. IV)."""
+"""Oracle pins for the time-sliced schedule (Sec. II.A, Eqs. (2)-(4), Eq. (14),
+Sec. VI.B injection count, App. C Tab. IV)."""
 import json
 import math
 import os
@@ -31,7 +31,7 @@ def test_event_times_eq4(n, k):
     for t in range(k):
         assert (cf.tau_in(n, t), t) in bus and (cf.tau_out(n, t), t) in bus
         assert (cf.tau_fetch(n, t), "fetch", t) in sched
-        assert cf.tau_out(n, t) - cf.tau_in(n, t) == 2 * n                       # Eq. (5) window
+        assert cf.tau_out(n, t) - cf.tau_in(n, t) == 2 * n                       # Eq. (4) window
         assert cf.tau_out(n, t) == T - cf.tau_in(n, k - 1 - t)                   # mirror
     assert sorted(s for s, g, _ in sched if g in ("load", "unload")) == \
         sorted([2 * l + 1 for l in range(n)] + [T - 2 * l - 1 for l in range(n)])
@@ -43,7 +43,7 @@ def test_data_qubits_never_meet_a_router_swap(n):
     layer.  Every item moves one layer per slice whatever its path, so this
     holds on and off the path: a data qubit's value never reaches a router,
     and its position depends on the routers alone (the schedule of Sec. II,
-    data windows of Eq. (5))."""
+    data windows of Eq. (4))."""
     for k in range(1, n + 1):
         sched = core.schedule(n, k)
         layers = {}                                  # slice -> layers holding a data qubit after its gates
@@ -98,7 +98,7 @@ def test_noise_free_equals_ideal():
 def test_address_window_eq12(n, k):
     """A single qubit-encoding branch with no candidates ends with norm
     a^(2 c_addr(i)) ((1+a^4n)/2)^k: address bit t damped for T-4t-2 layers
-    (Eq. (12)), every data qubit for exactly 2n (Eq. (5))."""
+    (Eq. (14)), every data qubit for exactly 2n (Eq. (4))."""
     gamma = 0.013
     a = math.sqrt(1 - gamma)
     for i in [0, 1, (1 << n) - 1, (1 << n) // 3]:

@@ -1,4 +1,4 @@
-"""The fidelity-scan input (Sec. V.A, restricted to one bus column per
+"""The fidelity-scan input (Sec. VI, restricted to one bus column per
 address): min(D, 2^n) distinct addresses, bus words below 2^k, equal weights
 with unit norm, reproducible from the seed."""
 import numpy as np

@@ -5,7 +5,7 @@ classical memory, the input columns and the per-batch damping rates that a
 query simulation takes as inputs.  Everything is generated with numpy's
 PCG64 from an explicit seed, so both sides see identical inputs.
 
-Workloads (paper Sec. V: data-loading input of one branch per address with
+Workloads (paper Sec. VI: data-loading input of one branch per address with
 zero bus input; memory with i.i.d. uniform bits):
   - ``data_loading(n, k, seed)``: D = 2^n columns, c_i = 2^{-n/2}, bus 0.
   - ``random_columns(n, k, D, seed)``: D distinct addresses, random bus
@@ -65,7 +65,7 @@ def random_columns(encoding: int, n: int, k: int, D: int, seed: int) -> Problem:
 
 
 def uniform_random_input(encoding: int, n: int, k: int, D: int, seed: int) -> Problem:
-    """The scan input of Sec. V.A restricted to one bus column per address:
+    """The scan input of Sec. VI restricted to one bus column per address:
     min(D, 2^n) distinct addresses drawn without replacement, a uniform random
     bus word each, equal weights (the paper draws D of the 2^(n+k)
     address-bus components; several columns per address are outside the
