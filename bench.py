@@ -90,14 +90,18 @@ def _kernel_sources_hash() -> str:
 
 
 def _traffic_per_step():
-    """DRAM bytes of one step launch from the committed ncu record, only if it
-    was taken on the kernel sources of this tree."""
+    """DRAM bytes of one step launch: the committed ncu record of the small
+    mix case (--profile-mix: 296 trajectories with the bench's mix of damping
+    rates, one launch) scaled per trajectory to the 1e5 trajectories of a
+    step; only if it was taken on the kernel sources of this tree."""
     try:
         with open(TRAFFIC_RECORD) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    return rec.get("dram_bytes_per_step_launch") if rec.get("sources_sha256") == _kernel_sources_hash() else None
+    if rec.get("sources_sha256") != _kernel_sources_hash() or "dram_bytes_per_trajectory" not in rec:
+        return None
+    return rec["dram_bytes_per_trajectory"] * NTRAJ
 
 
 def _problem():
@@ -226,19 +230,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--full-per-batch", type=int, default=20, help="full-mode trajectories per gamma batch")
     ap.add_argument("--serving", action="store_true", help="run the serving-stream benchmark instead")
-    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--requests", type=int, default=2000, help="--serving: number of requests")
+    ap.add_argument("--traj-lo", type=float, default=1e3, help="--serving: trajectories per request, log-uniform from")
+    ap.add_argument("--traj-hi", type=float, default=1e5, help="--serving: ... to")
     ap.add_argument("--scan", action="store_true",
                     help="fidelity vs n (qubit, k=3, 500-branch random input, 200 trajectories per point)")
     ap.add_argument("--profile-case", type=float, default=None, metavar="GAMMA",
                     help="one launch of 296 trajectories (148 CTAs of 512 threads) at this gamma, for ncu")
+    ap.add_argument("--profile-mix", action="store_true",
+                    help="one launch of 296 trajectories of the bench workload (every 337th index, with its gamma; "
+                         "148 CTAs of 512 threads), for ncu: the small case whose traffic scales to a step")
     ap.add_argument("--configs", action="store_true",
                     help="the other workload configurations (qutrit n=3, qubit n=6, qutrit n=10): throughput, "
                          "work and measured peaks")
     ap.add_argument("--only", type=int, default=None, help="with --configs: run only this configuration index")
     args = ap.parse_args()
-    if args.profile_case is not None:
+    if args.profile_case is not None or args.profile_mix:
         return run_profile_case(args.profile_case)
     if args.configs:
         return run_configs(args)
@@ -309,11 +317,6 @@ def main():
     res = sim.results(out)
     value, t_dev = world_throughput(sum(ms) / 1e3, args.steps, NTRAJ, dist)
 
-    # ---- pruned vs full on the same stratified subset --------------------
-    sub = np.concatenate([np.arange(b, b + args.full_per_batch) for b in range(0, NTRAJ, BATCH)])
-    gsub = torch.tensor(gam_h[sub], dtype=torch.float64, device=dev)
-    osub = torch.empty((len(sub), 48), dtype=torch.uint8, device=dev)
-
     def timed(fn, reps=1):
         with torch.cuda.stream(stream):
             fn()
@@ -327,15 +330,45 @@ def main():
         b.synchronize()
         return a.elapsed_time(b) / 1e3 / reps
 
-    t_full = timed(lambda: sim.run_full(base + 7_000_000, gsub, osub))
-    full_res = sim.results(osub)
-    t_psub = timed(lambda: sim.run_pruned(base + 7_000_000, gsub, osub), reps=3)
-    pr_res = sim.results(osub)
+    # ---- full evolution on the whole workload, same trajectories ------------
+    # One graph-captured full-mode launch per step over the same 1e5
+    # trajectories as the pruned steps (the same trajectory indices, damping
+    # rates and noise histories), timed like them; then the pruned step of
+    # the last index range is replayed to compare the two modes trajectory by
+    # trajectory.
+    out_f = torch.empty((NTRAJ, 48), dtype=torch.uint8, device=dev)
+    graph_f = sim.graph("full", gam, out_f, traj0)
+    full_steps = max(2, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        traj0.fill_(base + args.warmup * NTRAJ)
+        graph_f()
+    barrier()
+    evf = []
+    for j in range(full_steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(j & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            traj0.fill_(base + (args.warmup + j) * NTRAJ)
+            a.record(stream)
+            graph_f()
+            b.record(stream)
+        evf.append((a, b))
+    barrier()
+    t_full_step = sum(a.elapsed_time(b) for a, b in evf) / 1e3 / full_steps
+    full_res = sim.results(out_f)
+    with torch.cuda.stream(stream):
+        graph()                                   # pruned, same traj0 as the last full step
+    barrier()
+    pr_res = sim.results(out)
     agree = float(np.max(np.abs(full_res["fidelity"] - pr_res["fidelity"])))
+    same_int = bool(all(np.array_equal(full_res[f], pr_res[f]) for f in ("ncand", "bad", "ref", "jumps",
+                                                                           "first_jump_slice", "q_ground")))
+    graph_f.close()
 
     # ---- pruned vs full per gamma decade (the shape of the paper's Tab. V) ---
     per_decade = {}
-    nd = 4000
+    nd = 20_000
     gd = torch.empty(nd, dtype=torch.float64, device=dev)
     od = torch.empty((nd, 48), dtype=torch.uint8, device=dev)
     for dg in (1e-5, 1e-4, 1e-3, 1e-2):
@@ -346,13 +379,15 @@ def main():
         rf = sim.results(od)
         per_decade[f"{dg:g}"] = {"pruned_traj_per_s": nd / tp, "full_traj_per_s": nd / tf, "speedup": tf / tp,
                                  "evolved_fraction": float(np.mean(rp["explicit_comps"]) / np.mean(rf["explicit_comps"])),
-                                 "max_abs_fidelity_diff": float(np.max(np.abs(rp["fidelity"] - rf["fidelity"])))}
+                                 "max_abs_fidelity_diff": float(np.max(np.abs(rp["fidelity"] - rf["fidelity"]))),
+                                 "trajectories": nd}
 
     # ---- the paper's mixed setting, depolarizing faults with eps = gamma ------
-    # Every branch is explicit in both modes, and every tree site takes faults,
-    # so stray excitations pile up in every component: measured on qubit n=8,
-    # k=3 (data-loading input) where they stay within the per-component
-    # capacity for eps <= 1e-3.
+    # Every branch is explicit in both modes and every tree site takes faults
+    # (the placement the paper leaves open), so stray excitations pile up in
+    # every component; a trajectory whose strays exceed the per-component
+    # capacity (32 off-path sites) reports QRAM_E_CAP.  The mean fidelity and
+    # the rate are over the completed trajectories, with the failed count.
     mixed = {}
     nm = 2000
     pm = W.data_loading(W.QUBIT, 8, 3, seed=SEED + 8)
@@ -365,9 +400,15 @@ def main():
         gm.fill_(dg)
         tm_ = timed(lambda: simm.run_pruned(base + 6_000_000, gm, om))
         rm = QramSim.results(om)
-        mixed[f"{dg:g}"] = {"traj_per_s": nm / tm_, "mean_fidelity": float(rm["fidelity"].mean()),
-                            "status_ok_fraction": float(np.mean(rm["status"] == 0))}
+        okm = rm["status"] == 0
+        mixed[f"{dg:g}"] = {"completed_traj_per_s": int(okm.sum()) / tm_,
+                            "mean_fidelity_completed": float(rm["fidelity"][okm].mean()) if okm.any() else None,
+                            "completed": int(okm.sum()), "failed_capacity": int(np.sum(rm["status"] == 6)),
+                            "failed_other": int(np.sum(~okm & (rm["status"] != 6)))}
     simm.close()
+
+    # ---- mixed persistent launch: three workloads in one graph launch -------
+    mixed_launch = _mixed_launch_row(dev, stream, variant)
 
     # ---- per-query latency: one gamma batch (1000 trajectories) alone -----
     lat = []
@@ -406,8 +447,8 @@ def main():
             "note": "algorithmic INT32 ops per step launch from the kernel's work counters x ops per unit "
                     f"{OPS_PER_UNIT} / launch time from CUDA events; peak derived: SMs x {INT32_LANES} INT32 "
                     "lanes/clock x median SM clock under load (measured_peaks: the measured add/logic rate); "
-                    "traffic: DRAM read+write bytes of one "
-                    "step launch from an ncu capture of the same kernel sources, else null",
+                    "traffic: DRAM read+write bytes per trajectory of the small mix case (ncu, one launch of 296 "
+                    "trajectories, same kernel sources) x the trajectories of a step, else null",
             "work_per_step": {k: v / args.steps for k, v in work.items()}, "variant_threads": variant}
     try:
         from paper_2609_34935_b300 import measure_peaks
@@ -433,15 +474,19 @@ def main():
             "config": {"workload": WORKLOAD, "mode": "pruned", "trajectories_per_step": NTRAJ,
                        "l2": "256 MiB buffer written between timed steps",
                        "parallelism": f"replicas x{world} (trajectory ranges)"},
-            "full": {"value": len(sub) / t_full, "unit": "trajectories/s",
-                     "pruned_same_subset": len(sub) / t_psub, "speedup_pruned_over_full": t_full / t_psub,
-                     "subset": f"{args.full_per_batch} trajectories per gamma batch ({len(sub)} total)",
-                     "max_abs_fidelity_diff_pruned_vs_full": agree},
+            "full": {"value": world * NTRAJ / t_full_step, "unit": "trajectories/s",
+                     "ms_per_step": 1e3 * t_full_step, "steps": full_steps,
+                     "speedup_pruned_over_full": t_full_step / (t_dev / args.steps),
+                     "trajectories": f"the same {NTRAJ} trajectories per step as the pruned steps (same indices, "
+                                     "damping rates and noise histories), one graph-captured launch per step",
+                     "max_abs_fidelity_diff_pruned_vs_full": agree, "integer_outputs_equal": same_int},
             "per_gamma_decade": per_decade,
             "eps_eq_gamma_per_decade": {"note": "depolarizing faults of strength eps = gamma on top of the damping "
-                                                "(the paper's benchmark setting, every tree site active), every "
-                                                "branch explicit; qubit n=8, k=3, data-loading input, 2000 "
-                                                "trajectories per decade", **mixed},
+                                                "(the paper's benchmark setting; every tree site active, a reading "
+                                                "the paper's Tab. IV does not pin), every branch explicit; qubit "
+                                                "n=8, k=3, data-loading input, 2000 trajectories per decade; rate "
+                                                "and mean fidelity over the completed trajectories", **mixed},
+            "mixed_launch": mixed_launch,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "query": "one gamma batch of 1000 trajectories launched alone", "n": int(len(lat))},
             "mean_fidelity": float(res["fidelity"].mean()), "status_ok": bool(np.all(res["status"] == 0)),
@@ -458,6 +503,66 @@ def main():
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _mixed_launch_row(dev, stream, threads):
+    """Qubit n=6 (3e4 trajectories, gamma cycling through 1e-4, 1e-3, 1e-2),
+    qutrit n=10 (1e5 at 1e-3) and the bench workload (qubit n=12, k=4, 1e5)
+    in one persistent graph-captured launch (qram_batch_create), against the
+    three launched one after the other as their own graphs in the same
+    variant; both timed with CUDA events, best of three."""
+    import torch
+    from paper_2609_34935_b300 import QramBatch, QramSim
+    parts = [(W.data_loading(W.QUBIT, 6, 1, seed=2001), 2001, np.tile([1e-4, 1e-3, 1e-2], 10_000)),
+             (W.data_loading(W.QUTRIT, 10, 1, seed=3001), 3001, np.full(NTRAJ, 1e-3)),
+             (_problem(), SEED, _gammas())]
+    sims, gams, outs, graphs, t0s = [], [], [], [], []
+    for p, seed, g in parts:
+        sim = QramSim(p, seed=seed, device=dev.index or 0, stream=stream)
+        sim.set_gamma_bound(float(g.max()))
+        sim.set_variant(threads)
+        gams.append(torch.tensor(g, dtype=torch.float64, device=dev))
+        outs.append(torch.empty((len(g), 48), dtype=torch.uint8, device=dev))
+        t0s.append(torch.zeros(1, dtype=torch.int64, device=dev))
+        sims.append(sim)
+    for sim, g, o, t0 in zip(sims, gams, outs, t0s):
+        graphs.append(sim.graph("pruned", g, o, t0))
+    batch = QramBatch(sims, "pruned", [0, 0, 0], gams, outs, threads=threads)
+
+    def best(fn):
+        with torch.cuda.stream(stream):
+            fn()
+            stream.synchronize()
+            b = float("inf")
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                b = min(b, e0.elapsed_time(e1) / 1e3)
+        return b
+
+    def separate():
+        for gr in graphs:
+            gr()
+    t_sep = best(separate)
+    sep = [sim.results(o).copy() for sim, o in zip(sims, outs)]
+    t_mix = best(batch)
+    same = all(np.array_equal(QramSim.results(o), r) for o, r in zip(outs, sep))
+    ntot = sum(len(g) for _, _, g in parts)
+    row = {"workloads": "qubit n=6 k=1 (3e4, gamma 1e-4/1e-3/1e-2), qutrit n=10 k=1 (1e5, gamma 1e-3), "
+                        "qubit n=12 k=4 (1e5, the bench's gamma mix)",
+           "threads": threads, "ctas": batch.grid, "trajectories": ntot,
+           "mixed_traj_per_s": ntot / t_mix, "separate_graphs_traj_per_s": ntot / t_sep,
+           "mixed_ms": 1e3 * t_mix, "separate_ms": 1e3 * t_sep, "results_equal_to_separate": bool(same)}
+    batch.close()
+    for gr in graphs:
+        gr.close()
+    for sim in sims:
+        sim.close()
+    return row
 
 
 def run_scan(args):
@@ -569,21 +674,37 @@ def run_configs(args):
     return 0
 
 
-def run_profile_case(gamma: float):
+PROFILE_TRAJ = 296          # two per CTA of a 148-CTA launch
+PROFILE_STRIDE = 337        # the mix case: trajectory indices 0, 337, ... (spans the 100 gamma batches)
+
+
+def run_profile_case(gamma):
     """Small case of the bench kernel for a profiler capture: the bench
-    problem, one launch, one CTA per SM, two trajectories per CTA."""
+    problem, one launch, one CTA per SM, two trajectories per CTA.  With a
+    gamma, every trajectory has that rate.  Without (the mix case),
+    trajectories 0..295 take the rates of every PROFILE_STRIDE-th index of
+    the bench workload: about three per gamma batch, the bench's own mix of
+    rates, so per-trajectory counters (DRAM bytes, work) scale to a step."""
     import torch
     from paper_2609_34935_b300 import QramSim
     sim = QramSim(_problem(), seed=SEED, device=0)
     sim.set_variant(512)
     sim.set_launch_ctas(148)
     sim.set_gamma_bound(G_HI)
-    g = torch.full((296,), gamma, dtype=torch.float64, device="cuda:0")
+    if gamma is None:
+        idx = np.arange(PROFILE_TRAJ) * PROFILE_STRIDE
+        gh = _gammas()[idx]
+    else:
+        gh = np.full(PROFILE_TRAJ, gamma)
+    g = torch.tensor(gh, dtype=torch.float64, device="cuda:0")
+    sim.work_counters(reset=True)
     raw = sim.run_pruned(0, g)
     torch.cuda.synchronize()
     r = sim.results(raw)
-    print(json.dumps({"profile_case": gamma, "status_max": int(r["status"].max()),
-                      "mean_fidelity": float(r["fidelity"].mean()), "jumps": float(r["jumps"].mean())}))
+    w = sim.work_counters(reset=True)
+    print(json.dumps({"profile_case": gamma if gamma is not None else "mix", "trajectories": PROFILE_TRAJ,
+                      "status_max": int(r["status"].max()), "mean_fidelity": float(r["fidelity"].mean()),
+                      "jumps": float(r["jumps"].mean()), "work": w}))
     sim.close()
     return 0
 
@@ -602,7 +723,7 @@ def run_serving(args):
         return
     torch.cuda.set_device(local)
     rng = np.random.default_rng(5001)
-    lo, hi = 1e2, 1e4
+    lo, hi = args.traj_lo, args.traj_hi
     reqs = []
     for i in range(args.requests):
         enc = int(rng.integers(0, 2))
@@ -633,6 +754,8 @@ def run_serving(args):
         ntot = sum(c["ntraj"] for c in comps)
         return wall, lat, ok, ntot
 
+    clocks = Clocks(local)
+    clocks.start()
     wall0, _, ok0, ntot = run(0.0)                     # capacity: everything submitted at once
     cap_rps = len(reqs) / wall0
     lines = []
@@ -641,9 +764,10 @@ def run_serving(args):
         lines.append({"load": frac, "rate_req_per_s": frac * cap_rps, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                       "p99_ms": 1e3 * float(np.percentile(lat, 99)), "trajectories_per_s": ntot / wall,
                       "status_ok": bool(ok)})
+    cl = clocks.stop()
     print(json.dumps({"metric": "serving stream: p50/p99 query latency and trajectories/s", "unit": "ms",
                       "requests": len(reqs), "capacity_req_per_s": cap_rps, "capacity_traj_per_s": ntot / wall0,
-                      "runs": lines, "data": "synthetic",
+                      "runs": lines, "data": "synthetic", "clocks": cl, "capacity_status_ok": bool(ok0),
                       "config": {"workload": f"Poisson arrivals of {len(reqs)} requests; encoding 50/50, n in 4..14, "
                                              f"k in 1..min(n,4), gamma log-uniform [1e-5,1e-2], trajectories "
                                              f"log-uniform [{lo:g},{hi:g}], data-loading input, pruned mode",

@@ -64,6 +64,10 @@ enum {
 
 enum { QRAM_QUTRIT = 0, QRAM_QUBIT = 1 };
 
+/* Noise channel of the layer that follows every slice's gates (see
+ * qram_set_channel). */
+enum { QRAM_CHANNEL_DAMPING = 0, QRAM_CHANNEL_DEPHASING = 1 };
+
 /* One QRAM query problem (Sec. II.A; input class of Sec. IV.D: a coherent
  * superposition over addresses with one bus column per address). */
 typedef struct {
@@ -125,19 +129,27 @@ int qram_sample_faults(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const do
 
 /* Pruned simulation (Algorithm 1): bad branches plus the reference branch
  * are evolved explicitly with the joint damping sampler of Sec. IV.D; the
- * good branches enter the mask weights (Eq. (18)) and the final state
- * through their closed forms (Prop. 1, Eq. (8); Theorem 2, Eq. (14)), and
- * are annihilated once a non-empty jump fires (Sec. V.A).  gamma: device,
- * ntraj values in [0, 1); out: device, ntraj results. */
+ * good branches enter the mask weights (Eq. (21)) and the final state
+ * through their closed forms (Prop. 1, Eq. (8); Theorem 2, Eq. (16)), and
+ * are annihilated once a non-empty jump fires (Sec. VI.A).  gamma: device,
+ * ntraj values in [0, gamma_lim); out: device, ntraj results.
+ *
+ * Damping-rate limit.  Amplitudes are carried unnormalised as a^e with an
+ * integer count e of K0 factors (a = sqrt(1 - gamma)); normalisation happens
+ * only in ratios.  The weights a^(2e) must stay in the normal FP64 range:
+ * gamma_lim = 1 - exp(-650 / ((2n + k)(T - 1))), i.e. 0.255 at n = 12, k = 4
+ * and 0.20 at n = 14, k = 4 (the oracle renormalises every layer and has no
+ * such limit).  A trajectory whose rate is outside [0, gamma_lim) reports
+ * status QRAM_E_ARG; nothing is computed for it. */
 int qram_run_pruned(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double *gamma,
                     qram_result_t *out);
 
 /* Full simulation: every branch evolved explicitly from the same noise
- * history (the comparison mode of Sec. V.A).  Same arguments. */
+ * history (the comparison mode of Sec. VI.A).  Same arguments. */
 int qram_run_full(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double *gamma,
                   qram_result_t *out);
 
-/* Test hook (fixed noise histories of Sec. V.A): while set, trajectory
+/* Test hook (fixed noise histories of Sec. VI.A): while set, trajectory
  * traj0 + t of the next runs takes its candidate set from
  * cand[off[t] .. off[t+1]) (device, packed as in qram_sample_faults, sorted)
  * instead of the FAULT stream, for t < nhist; the auxiliary and final draws
@@ -145,7 +157,8 @@ int qram_run_full(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double 
  * must stay valid while the hook is set. */
 int qram_set_fault_history(qram_sim_t *sim, uint32_t nhist, const uint32_t *cand, const uint32_t *off);
 
-/* Upper bound on the damping rates of the next runs (0 < gmax < 1), used to
+/* Upper bound on the damping rates of the next runs (0 < gmax < gamma_lim of
+ * qram_run_pruned, else QRAM_E_ARG), used to
  * size the per-trajectory candidate scratch without reading the rates back
  * to the host; 0 clears it (each run then reduces gamma on the device and
  * synchronises once).  A trajectory whose candidates overflow the sized
@@ -174,6 +187,36 @@ int qram_graph_create(qram_sim_t *sim, int mode, uint32_t ntraj, const double *g
 int qram_graph_launch(qram_graph_t *graph);
 void qram_graph_destroy(qram_graph_t *graph);
 
+/* Mixed persistent launch (spec batching pattern; no paper counterpart:
+ * the paper runs one query at a time).  One work-stealing launch, captured
+ * in a CUDA graph, over the trajectories of several problems of different
+ * encodings, address widths n and data widths k: problem q contributes
+ * trajectories traj0[q] .. traj0[q] + ntraj[q] - 1 with damping rates
+ * gamma[q] (device, ntraj[q]) and results out[q] (device, ntraj[q]); mode 0
+ * pruned, 1 full for all.  The global counter runs over the concatenated
+ * ranges, so problems with uneven per-trajectory cost share the SMs; each
+ * CTA runs Algorithm 1 for one trajectory of one problem at a time, and
+ * every trajectory's result is bitwise the one that problem's own launch in
+ * the same variant gives.
+ *   sims: 1 .. 16 simulators on one device, each with a damping-rate bound
+ *         (qram_set_gamma_bound, else QRAM_E_STATE) and no depolarizing
+ *         faults (else QRAM_E_ARG);
+ *   threads: the launch variant for all problems (128, 256 or 512; 0 = that
+ *         of sims[0]).  Each simulator is switched to it (qram_set_variant,
+ *         which invalidates that simulator's graphs) and its scratch sized;
+ *         the dynamic shared memory is the largest problem's.
+ * The pointers and counts are bound when the batch is created.
+ * qram_batch_launch replays the graph on the stream of sims[0]; work of the
+ * other simulators' streams must be ordered before it by the caller.
+ * qram_batch_grid returns the number of CTAs of the launch. */
+typedef struct qram_batch qram_batch_t;
+int qram_batch_create(qram_sim_t *const *sims, uint32_t nsims, int mode, int threads, const uint64_t *traj0,
+                      const uint32_t *ntraj, const double *const *gamma, qram_result_t *const *out,
+                      qram_batch_t **batch);
+int qram_batch_launch(qram_batch_t *batch);
+int qram_batch_grid(const qram_batch_t *batch);
+void qram_batch_destroy(qram_batch_t *batch);
+
 /* Launch variant: threads per CTA of the trajectory kernel (128, 256 or
  * 512; default 256).  Results do not depend on it except through the order
  * of floating-point block reductions (rounding).  qram_get_variant returns
@@ -188,16 +231,25 @@ int qram_get_variant(const qram_sim_t *sim);
 int qram_autotune(qram_sim_t *sim, int mode, double gamma, uint32_t ntraj, uint64_t traj0, int *best_threads,
                   float *best_ms);
 
-/* Ensemble mean and standard error of results[0 .. ntraj).fidelity
- * (device array), reduced on the device in a fixed order; blocks until the
- * two host doubles are written. */
+/* Trajectory-averaged fidelity (Sec. VI.A: the ensemble mean over sampled
+ * noise histories that App. C compares with the density-matrix F_rho) and
+ * its Monte Carlo standard error (Fig. 2 error bars: standard error of the
+ * mean over trajectories), of results[0 .. ntraj).fidelity (device array).
+ * Reduced on the device by one CTA in a fixed order (deterministic); the
+ * variance is the unbiased sample variance.  Blocks until the two host
+ * doubles are written.  QRAM_E_ARG for null pointers; ntraj = 0 gives 0, 0. */
 int qram_fidelity(qram_sim_t *sim, const qram_result_t *results, uint32_t ntraj, double *mean,
                   double *stderr_out);
 
-/* Final normalised state of one trajectory (parity checks, Sec. V.A
- * "matching their complete complex amplitudes"): every explicitly evolved
- * component after the second Hadamard wall plus, in pruned mode, the
- * predicted good branches.  Host outputs, capacity cap entries:
+/* Final normalised state of one trajectory (the exactness check of Sec. VI.A:
+ * the pruned and full end states compared amplitude by amplitude): every
+ * explicitly evolved component after the second Hadamard wall plus, in
+ * pruned mode, the branches held in closed form.  Pruned mode runs the same
+ * lazy form as qram_run_pruned: while no jump has fired every branch is in
+ * closed form (Prop. 1, Theorem 2), so a jump-free trajectory is emitted
+ * entirely from the closed forms; after a jump only the materialised
+ * configurations survive (the others are annihilated by K_J).  gamma must be
+ * in [0, gamma_lim) (see qram_run_pruned), else QRAM_E_ARG.  Host outputs, capacity cap entries:
  * addr[c], bus[c], config_hash[c] (64-bit hash of the sorted excited-site
  * list, 0 for the ground configuration), re[c], im[c]; *count receives the
  * number of entries (QRAM_E_CAP if it exceeds cap).  mode: 0 pruned, 1 full.
@@ -219,11 +271,24 @@ int qram_dump_state(qram_sim_t *sim, int mode, uint64_t traj, double gamma, uint
  * path do not describe).  0 <= eps < 1, else QRAM_E_ARG.  Default 0. */
 int qram_set_depolarizing(qram_sim_t *sim, double eps, int eps_equals_gamma);
 
+/* Noise channel of the per-slice layer (default QRAM_CHANNEL_DAMPING, the
+ * amplitude damping of Eqs. (5)-(6)).  QRAM_CHANNEL_DEPHASING is the
+ * dephasing channel that the outlook (Sec. VII) names as a further channel
+ * with a diagonal no-jump operator: phase damping of strength gamma with the
+ * same no-jump operator K0 = diag(1, a) (qutrit diag(1, a, a)) and the jump
+ * sqrt(gamma)|1><1| (qutrit sqrt(gamma)|L><L|, sqrt(gamma)|R><R|).  Its
+ * K_J^dagger K_J is the damping one, so the candidate sampling, the marking,
+ * the joint draw of Sec. IV.D and the good-branch closed forms (Prop. 1,
+ * Theorem 2) are unchanged; a fired jump projects onto the components that
+ * hold its sites excited and leaves their configuration as it is.  Applies
+ * to both modes and to qram_dump_state; QRAM_E_ARG for another value. */
+int qram_set_channel(qram_sim_t *sim, int channel);
+
 /* Low-weight truncation of the predicted good branches in qram_dump_state
- * (Sec. IV, cost discussion after Eq. (22)): each good branch ends in a
+ * (Sec. V, cost discussion after Eq. (26)): each good branch ends in a
  * superposition over all 2^k output words whose amplitude falls by
  * beta/alpha = O(n gamma) per unit of Hamming distance from the ideal word
- * (Eq. (14)); with w_max >= 0 only the words within distance w_max are
+ * (Eq. (13)); with w_max >= 0 only the words within distance w_max are
  * emitted, the dropped amplitudes being O((n gamma)^(w_max + 1)).
  * w_max = -1 (the default) emits all 2^k words.  Qubit encoding only (the
  * qutrit good branch is a single word); returns QRAM_E_ARG for w_max < -1. */
@@ -238,12 +303,21 @@ uint64_t qram_launch_count(const qram_sim_t *sim);
 
 /* Work done by this simulator's trajectory launches since creation or the
  * last reset.  No counterpart in the paper: instrumentation for the
- * roofline of the trajectory kernel.  out (host, 4 entries):
+ * roofline of the trajectory kernel, and evidence of which evolution forms
+ * a launch took.  out (host, 8 entries):
  *   out[0] fault-stream draws (one 64-bit word per geometric gap),
  *   out[1] explicit component-slices (gate slices applied to explicit
  *          components, pruned and full mode),
- *   out[2] branch-epochs of the closed-form weights before the first jump,
- *   out[3] component-epochs of the explicit passes.
+ *   out[2] branch-epochs of the closed-form weights before the first jump
+ *          (nonzero only when the lazy pruned form ran),
+ *   out[3] component-epochs of the explicit passes,
+ *   out[4] component-slices on the path words of a component with two paths
+ *          (a misaligned router sent items off its address path),
+ *   out[5] component-slices through the register generic form (path B or
+ *          off-path items, at most 8 sites off the address path),
+ *   out[6] component-slices through the memory generic form (sorted site
+ *          list, up to 32 off-path sites),
+ *   out[7] component-epochs that began with off-path items.
  * Each trajectory adds its counts when it finishes.  Waits for the
  * simulator's stream; reset != 0 zeroes the counters afterwards.  Returns
  * QRAM_E_ARG for null pointers, QRAM_E_CUDA on a CUDA error. */
@@ -266,7 +340,7 @@ typedef struct {
     qram_problem_t problem;    /* copied at submit */
     uint64_t traj0;            /* first trajectory index */
     uint32_t ntraj;            /* >= 1 */
-    const double *gamma;       /* host, ntraj damping rates in [0, 1) (copied) */
+    const double *gamma;       /* host, ntraj damping rates in [0, gamma_lim) (copied) */
     int32_t mode;              /* 0 pruned, 1 full */
 } qram_request_t;
 
@@ -284,7 +358,8 @@ typedef struct {
 int qram_server_create(size_t mem_budget, int device, uint32_t max_active, qram_server_t **out);
 
 /* Queue a request; *id receives its identifier.  QRAM_E_ARG for a malformed
- * request (same checks as qram_sim_create, gamma outside [0,1)), QRAM_E_OOM
+ * request (same checks as qram_sim_create, a gamma outside [0, gamma_lim)
+ * of qram_run_pruned), QRAM_E_OOM
  * if it could never fit the budget, QRAM_E_BUSY if 65536 requests wait. */
 int qram_server_submit(qram_server_t *srv, const qram_request_t *req, uint64_t *id);
 
@@ -320,7 +395,7 @@ void qram_server_destroy(qram_server_t *srv);
  * kernel as qram_run_pruned (mode 0) or qram_run_full (mode 1) on one
  * problem held entirely in caller-owned DEVICE memory:
  *   memory[2^n], addr[D], bus[D], amp_re[D], amp_im[D]  (as in qram_problem_t)
- *   gamma[ntraj] in [0, 1), out[ntraj]  (as in qram_run_pruned)
+ *   gamma[ntraj] in [0, gamma_lim), out[ntraj]  (as in qram_run_pruned)
  * gamma_max (host) bounds the damping rates (sizes the candidate scratch; a
  * trajectory above it that overflows is reported QRAM_E_CAP).  The inputs
  * are validated on the device; invalid ones make every trajectory report
@@ -342,6 +417,11 @@ int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k, int32_t nu
                     const double *amp_re, const double *amp_im, uint64_t seed, uint64_t traj0,
                     uint32_t ntraj, const double *gamma, double gamma_max, qram_result_t *out,
                     void *cuda_stream);
+/* (qram_run_static: gamma_max must be below gamma_lim of qram_run_pruned,
+ * else QRAM_E_ARG; a trajectory whose own rate reaches gamma_lim reports
+ * QRAM_E_ARG.  The static array's device address is cached per device and
+ * per CUDA context: after a device reset, or under another context, the
+ * next call looks it up again.) */
 
 /* ---------------------------------------------------------------------------
  * Roofline denominators (no paper counterpart: a measurement utility).

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["QramSim", "QramServer", "RESULT_DTYPE", "QramError", "load_library", "QUTRIT", "QUBIT"]
+__all__ = ["QramSim", "QramServer", "QramBatch", "RESULT_DTYPE", "QramError", "load_library", "QUTRIT", "QUBIT"]
 
 QUTRIT, QUBIT = 0, 1
 OK = 0
@@ -93,6 +93,7 @@ def load_library(build_if_missing: bool = True):
     L.qram_work_counters.argtypes = [vp, vp, C.c_int]
     L.qram_set_dump_weight.argtypes = [vp, C.c_int]
     L.qram_set_depolarizing.argtypes = [vp, C.c_double, C.c_int]
+    L.qram_set_channel.argtypes = [vp, C.c_int]
     L.qram_server_create.argtypes = [C.c_size_t, C.c_int, u32, C.POINTER(vp)]
     L.qram_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
     L.qram_server_estimate.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
@@ -106,6 +107,11 @@ def load_library(build_if_missing: bool = True):
     L.qram_graph_launch.argtypes = [vp]
     L.qram_graph_destroy.argtypes = [vp]
     L.qram_graph_destroy.restype = None
+    L.qram_batch_create.argtypes = [vp, u32, C.c_int, C.c_int, vp, vp, vp, vp, C.POINTER(vp)]
+    L.qram_batch_launch.argtypes = [vp]
+    L.qram_batch_grid.argtypes = [vp]
+    L.qram_batch_destroy.argtypes = [vp]
+    L.qram_batch_destroy.restype = None
     L.qram_set_variant.argtypes = [vp, C.c_int]
     L.qram_get_variant.argtypes = [vp]
     L.qram_autotune.argtypes = [vp, C.c_int, f64, u32, u64, C.POINTER(C.c_int), C.POINTER(C.c_float)]
@@ -258,6 +264,11 @@ class QramSim:
         _check(self.lib.qram_set_depolarizing(self.h, float(eps), 1 if eps_equals_gamma else 0),
                "qram_set_depolarizing")
 
+    def set_channel(self, channel: str):
+        """The per-slice channel: "damping" (amplitude damping, the default)
+        or "dephasing" (phase damping with the same no-jump operator)."""
+        _check(self.lib.qram_set_channel(self.h, {"damping": 0, "dephasing": 1}[channel]), "qram_set_channel")
+
     def set_gamma_bound(self, gmax: float):
         _check(self.lib.qram_set_gamma_bound(self.h, gmax), "qram_set_gamma_bound")
 
@@ -336,10 +347,56 @@ class QramSim:
     def work_counters(self, reset: bool = False) -> dict:
         """Work of the trajectory launches since creation or the last reset:
         fault-stream draws, explicit component-slices, closed-form
-        branch-epochs, explicit component-epochs (waits for the stream)."""
-        o = np.zeros(4, np.uint64)
+        branch-epochs, explicit component-epochs, and the component-slices
+        (epochs) taken by the two-path, register generic, memory generic
+        (off-path) forms (waits for the stream)."""
+        o = np.zeros(8, np.uint64)
         _check(self.lib.qram_work_counters(self.h, o.ctypes.data, 1 if reset else 0), "qram_work_counters")
-        return {"draws": int(o[0]), "comp_slices": int(o[1]), "branch_epochs": int(o[2]), "comp_epochs": int(o[3])}
+        names = ("draws", "comp_slices", "branch_epochs", "comp_epochs", "two_path_slices", "reg_generic_slices",
+                 "mem_generic_slices", "offpath_comp_epochs")
+        return {nm: int(v) for nm, v in zip(names, o)}
+
+
+class QramBatch:
+    """One persistent launch over several problems (qram_batch_create): a
+    CUDA graph replayed by calling the object.  ``sims``: QramSim objects on
+    one device, each with a damping-rate bound; ``gammas``/``outs``: device
+    tensors per problem (float64 rates; uint8 [ntraj, 48] results);
+    ``traj0s``: first trajectory index per problem."""
+
+    def __init__(self, sims, mode: str, traj0s, gammas, outs, threads: int = 0):
+        self.lib = load_library()
+        n = len(sims)
+        hs = (C.c_void_p * n)(*[s.h for s in sims])
+        t0 = (C.c_uint64 * n)(*[int(t) for t in traj0s])
+        nt = (C.c_uint32 * n)(*[int(g.numel()) for g in gammas])
+        gp = (C.c_void_p * n)(*[_dptr(g) for g in gammas])
+        op = (C.c_void_p * n)(*[_dptr(o) for o in outs])
+        for g, o in zip(gammas, outs):
+            assert o.shape[0] == g.numel() and o.shape[1] == RESULT_DTYPE.itemsize
+        h = C.c_void_p()
+        _check(self.lib.qram_batch_create(hs, n, 0 if mode == "pruned" else 1, int(threads), t0, nt, gp, op,
+                                          C.byref(h)), "qram_batch_create")
+        self.h = h
+        self._keep = (list(sims), list(gammas), list(outs))
+
+    @property
+    def grid(self) -> int:
+        return int(self.lib.qram_batch_grid(self.h))
+
+    def __call__(self):
+        _check(self.lib.qram_batch_launch(self.h), "qram_batch_launch")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qram_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def measure_peaks(device: int = 0) -> dict:

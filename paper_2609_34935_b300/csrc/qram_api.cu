@@ -50,6 +50,7 @@ struct qram_sim {
     int dump_wmax = -1;         // low-weight truncation of the dumped good branches
     double eps = 0.0;           // depolarizing strength
     int eps_gamma = 0;          // the strength of each trajectory is its damping rate
+    int channel = QRAM_CHANNEL_DAMPING;
 };
 
 namespace {
@@ -239,6 +240,8 @@ Params base_params(qram_sim *S) {
     P.eps = S->eps;
     P.eps_gamma = S->eps_gamma;
     P.ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(S->d_work) + 32);
+    P.gamma_lim = gamma_limit(S->n, S->k);
+    P.channel = S->channel;
     std::memcpy(P.ops, S->ops, sizeof(P.ops));
     std::memcpy(P.occ2, S->occ2, sizeof(P.occ2));
     P.orbit = S->orbit;
@@ -284,6 +287,11 @@ int run_mode(qram_sim *S, int mode, uint64_t traj0, uint32_t ntraj, const double
 namespace qram {
 
 int build_ops(int n, int k, SliceOps *ops) { return build_ops_impl(n, k, ops); }
+
+double gamma_limit(int n, int k) {
+    const double emax = (double)(2 * n + k) * (double)(6 * n + 2 * k - 1);
+    return -std::expm1(-kLnBudget / emax);                 // 1 - exp(-budget / emax)
+}
 
 // Noiseless orbit with every item excited (all address bits 1, all data bits
 // 1): its path word after each slice marks every position an item can hold.
@@ -465,7 +473,7 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
     cudaStream_t st = S->stream;
     if (!ok(cudaMallocAsync((void **)&S->d_mem, N, st)) || !ok(cudaMallocAsync((void **)&S->d_addr, D * 4, st)) ||
         !ok(cudaMallocAsync((void **)&S->d_bus, D * 4, st)) || !ok(cudaMallocAsync((void **)&S->d_re, D * 8, st)) ||
-        !ok(cudaMallocAsync((void **)&S->d_im, D * 8, st)) || !ok(cudaMallocAsync((void **)&S->d_work, 64, st)) ||
+        !ok(cudaMallocAsync((void **)&S->d_im, D * 8, st)) || !ok(cudaMallocAsync((void **)&S->d_work, 128, st)) ||
         !ok(cudaMallocAsync((void **)&S->d_fid2, 16, st)) || !ok(cudaMallocAsync((void **)&S->d_gmax, 8, st)) ||
         !ok(cudaMallocAsync((void **)&S->d_w2u, 8, st))) {
         cudaGetLastError();
@@ -479,7 +487,7 @@ int qram_sim_create(const qram_problem_t *p, int device, void *cuda_stream, qram
         !ok(cudaMemcpyAsync(S->d_re, p->amp_re, D * 8, cudaMemcpyHostToDevice, st)) ||
         !ok(cudaMemcpyAsync(S->d_im, p->amp_im, D * 8, cudaMemcpyHostToDevice, st)))
         rc = QRAM_E_CUDA;
-    if (!rc && !ok(cudaMemsetAsync(S->d_work, 0, 64, st))) rc = QRAM_E_CUDA;     // counter + work counters
+    if (!rc && !ok(cudaMemsetAsync(S->d_work, 0, 128, st))) rc = QRAM_E_CUDA;    // counter + 8 work counters at +32
     // every address present (qubit): the closed-form weights factorise over the address bits
     if (!rc && S->enc == QRAM_QUBIT && D == N) {
         std::vector<uint32_t> col(N);
@@ -598,6 +606,125 @@ void qram_graph_destroy(qram_graph_t *G) {
     delete G;
 }
 
+struct qram_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;           // the first simulator's stream
+    std::vector<qram_sim *> sims;
+    Params *d_params = nullptr;
+    uint32_t *d_work = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int threads = 0, grid = 0;
+};
+
+int qram_batch_create(qram_sim_t *const *sims, uint32_t nsims, int mode, int threads, const uint64_t *traj0,
+                      const uint32_t *ntraj, const double *const *gamma, qram_result_t *const *out,
+                      qram_batch_t **bout) {
+    if (!sims || !traj0 || !ntraj || !gamma || !out || !bout || nsims < 1 || nsims > (uint32_t)kMaxBatch ||
+        (mode != 0 && mode != 1))
+        return QRAM_E_ARG;
+    *bout = nullptr;
+    uint64_t total = 0;
+    for (uint32_t q = 0; q < nsims; ++q) {
+        const qram_sim *S = sims[q];
+        if (!S || !gamma[q] || !out[q] || ntraj[q] == 0) return QRAM_E_ARG;
+        if (S->device != sims[0]->device) return QRAM_E_ARG;
+        if (S->eps > 0.0 || S->eps_gamma) return QRAM_E_ARG;             // damping only
+        if (!(S->gamma_bound > 0.0)) return QRAM_E_STATE;                // no host read-back inside a capture
+        total += ntraj[q];
+    }
+    if (total >= 0x7FFFFFFFull) return QRAM_E_ARG;
+    if (threads == 0) threads = sims[0]->threads;
+    if (!valid_threads(threads)) return QRAM_E_ARG;
+    DeviceGuard g(sims[0]->device);
+    qram_batch *B = new (std::nothrow) qram_batch();
+    if (!B) return QRAM_E_OOM;
+    B->device = sims[0]->device;
+    B->stream = sims[0]->stream;
+    B->threads = threads;
+    B->sims.assign(sims, sims + nsims);
+    size_t dyn = 0;
+    int slots = 0x7FFFFFFF;
+    int rc = QRAM_OK;
+    std::vector<Params> host(nsims);
+    MultiParams MP;
+    std::memset(&MP, 0, sizeof(MP));
+    for (uint32_t q = 0; q < nsims && !rc; ++q) {
+        qram_sim *S = sims[q];
+        // every problem runs in the batch's variant: scratch laid out for it
+        if ((rc = qram_set_variant(S, threads))) break;
+        if ((rc = ensure_scratch(S, S->gamma_bound))) break;
+        dyn = std::max(dyn, S->dyn);
+        slots = std::min(slots, S->slots);
+        Params &P = host[q];
+        P = base_params(S);
+        P.traj0 = traj0[q]; P.ntraj = ntraj[q]; P.gamma = gamma[q]; P.mode = mode == 0 ? kPruned : kFull; P.out = out[q];
+        MP.start[q + 1] = MP.start[q] + ntraj[q];
+    }
+    if (!rc) {
+        const int b = kernel_blocks_per_sm_multi(threads, dyn);
+        if (b < 1) rc = QRAM_E_CUDA;
+        else B->grid = (int)std::min<uint64_t>((uint64_t)std::min(slots, sims[0]->sms * b), total);
+    }
+    cudaStream_t st = B->stream;
+    if (!rc && (!ok(cudaMallocAsync((void **)&B->d_params, sizeof(Params) * nsims, st)) ||
+                !ok(cudaMallocAsync((void **)&B->d_work, 256, st)))) {
+        cudaGetLastError();
+        rc = QRAM_E_OOM;
+    }
+    if (!rc && (!ok(cudaMemcpyAsync(B->d_params, host.data(), sizeof(Params) * nsims, cudaMemcpyHostToDevice, st)) ||
+                !ok(cudaStreamSynchronize(st))))          // the host table goes out of scope
+        rc = QRAM_E_CUDA;
+    if (!rc) {
+        MP.probs = B->d_params;
+        MP.work = B->d_work;
+        MP.nprob = nsims;
+        MP.dyn_words = (uint32_t)(dyn / sizeof(uint32_t));
+        cudaStream_t cap = nullptr;
+        if (!ok(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) rc = QRAM_E_CUDA;
+        else {
+            if (!ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) rc = QRAM_E_CUDA;
+            else {
+                if (!ok(cudaMemsetAsync(B->d_work, 0, sizeof(uint32_t), cap)) ||
+                    !ok(launch_trajectories_multi(MP, B->grid, threads, dyn, cap)))
+                    rc = QRAM_E_CUDA;
+                cudaGraph_t graph = nullptr;
+                if (!ok(cudaStreamEndCapture(cap, &graph))) rc = QRAM_E_CUDA;
+                B->graph = graph;
+                if (!rc && !ok(cudaGraphInstantiate(&B->exec, B->graph, 0))) rc = QRAM_E_CUDA;
+            }
+            cudaStreamDestroy(cap);
+        }
+    }
+    if (rc) { cudaGetLastError(); qram_batch_destroy(B); return rc; }
+    *bout = B;
+    return QRAM_OK;
+}
+
+int qram_batch_launch(qram_batch_t *B) {
+    if (!B || !B->exec) return QRAM_E_ARG;
+    DeviceGuard g(B->device);
+    if (!ok(cudaGraphLaunch(B->exec, B->stream))) return QRAM_E_CUDA;
+    for (qram_sim *S : B->sims) S->launches++;
+    return QRAM_OK;
+}
+
+int qram_batch_grid(const qram_batch_t *B) { return B ? B->grid : 0; }
+
+void qram_batch_destroy(qram_batch_t *B) {
+    if (!B) return;
+    {
+        DeviceGuard g(B->device);
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        if (B->graph) cudaGraphDestroy(B->graph);
+        if (B->d_params) cudaFreeAsync(B->d_params, B->stream);
+        if (B->d_work) cudaFreeAsync(B->d_work, B->stream);
+        cudaStreamSynchronize(B->stream);
+        cudaGetLastError();
+    }
+    delete B;
+}
+
 int qram_set_launch_ctas(qram_sim_t *S, uint32_t nctas) {
     if (!S) return QRAM_E_ARG;
     const int full = S->sms * S->blocks_per_sm;
@@ -628,7 +755,9 @@ int qram_get_variant(const qram_sim_t *S) { return S ? S->threads : 0; }
 
 int qram_autotune(qram_sim_t *S, int mode, double gamma, uint32_t ntraj, uint64_t traj0, int *best_threads,
                   float *best_ms) {
-    if (!S || !best_threads || ntraj == 0 || (mode != 0 && mode != 1) || !(gamma >= 0.0 && gamma < 1.0)) return QRAM_E_ARG;
+    if (!S || !best_threads || ntraj == 0 || (mode != 0 && mode != 1) ||
+        !(gamma >= 0.0 && gamma < gamma_limit(S->n, S->k)))
+        return QRAM_E_ARG;
     DeviceGuard g(S->device);
     double *dg = nullptr;
     qram_result_t *dr = nullptr;
@@ -669,7 +798,7 @@ int qram_autotune(qram_sim_t *S, int mode, double gamma, uint32_t ntraj, uint64_
 }
 
 int qram_set_gamma_bound(qram_sim_t *S, double gmax) {
-    if (!S || !(gmax >= 0.0 && gmax < 1.0)) return QRAM_E_ARG;
+    if (!S || !(gmax >= 0.0 && gmax < gamma_limit(S->n, S->k))) return QRAM_E_ARG;
     S->gamma_bound = gmax;
     return QRAM_OK;
 }
@@ -689,7 +818,8 @@ int qram_fidelity(qram_sim_t *S, const qram_result_t *res, uint32_t ntraj, doubl
 
 int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32_t cap, uint32_t *addr,
                     uint32_t *bus, uint64_t *hash, double *re, double *im, uint32_t *count) {
-    if (!S || !count || (mode != 0 && mode != 1) || !(gamma >= 0.0 && gamma < 1.0)) return QRAM_E_ARG;
+    if (!S || !count || (mode != 0 && mode != 1) || !(gamma >= 0.0 && gamma < gamma_limit(S->n, S->k)))
+        return QRAM_E_ARG;
     if (cap && (!addr || !bus || !hash || !re || !im)) return QRAM_E_ARG;
     DeviceGuard g(S->device);
     int rc = ensure_scratch(S, gamma);
@@ -769,6 +899,12 @@ int qram_set_depolarizing(qram_sim_t *S, double eps, int eps_equals_gamma) {
     return QRAM_OK;
 }
 
+int qram_set_channel(qram_sim_t *S, int channel) {
+    if (!S || (channel != QRAM_CHANNEL_DAMPING && channel != QRAM_CHANNEL_DEPHASING)) return QRAM_E_ARG;
+    S->channel = channel;
+    return QRAM_OK;
+}
+
 int qram_set_dump_weight(qram_sim_t *S, int w_max) {
     if (!S || w_max < -1) return QRAM_E_ARG;
     S->dump_wmax = w_max;
@@ -779,8 +915,8 @@ int qram_work_counters(qram_sim_t *S, uint64_t *out, int reset) {
     if (!S || !out) return QRAM_E_ARG;
     DeviceGuard g(S->device);
     char *c = reinterpret_cast<char *>(S->d_work) + 32;
-    if (!ok(cudaMemcpyAsync(out, c, 32, cudaMemcpyDeviceToHost, S->stream))) return QRAM_E_CUDA;
-    if (reset && !ok(cudaMemsetAsync(c, 0, 32, S->stream))) return QRAM_E_CUDA;
+    if (!ok(cudaMemcpyAsync(out, c, 64, cudaMemcpyDeviceToHost, S->stream))) return QRAM_E_CUDA;
+    if (reset && !ok(cudaMemsetAsync(c, 0, 64, S->stream))) return QRAM_E_CUDA;
     if (!ok(cudaStreamSynchronize(S->stream))) return QRAM_E_CUDA;
     return QRAM_OK;
 }

@@ -20,6 +20,11 @@ constexpr int kGapBits = 13;
 // Damping exponents are bounded by (2n+k)(T-1) (at most 2n+k excited sites
 // per slice); histograms over them need (2n+k)(T-1)+1 <= 3565 bins.
 constexpr int kHistMax = 3584;
+// Amplitudes are kept unnormalised as a^e (a = sqrt(1 - gamma)), so the
+// weights a^(2e) <= (1 - gamma)^((2n+k)(T-1)) must stay in the normal FP64
+// range with room for the input weights (>= 2^-22): (2n+k)(T-1) (-ln(1 - gamma))
+// is kept below this budget (ln DBL_MIN = -708.4).
+constexpr double kLnBudget = 650.0;
 
 enum Mode : int { kPruned = 0, kFull = 1, kSampleOnly = 2 };
 
@@ -73,7 +78,7 @@ struct DumpOut {
     double *re, *im;
     uint32_t cap;
     uint32_t *count;
-    double *scal;        // [4]: W, jump fired, good scale flag
+    double *scal;        // [4]: W, jump fired, every branch explicit (depolarizing), lazy form
 };
 
 struct Params {
@@ -104,21 +109,39 @@ struct Params {
     const uint32_t *col_of;        // qubit input over every address (D = 2^n): column of each address, else null
     double eps;                    // depolarizing strength per (slice, site)
     int eps_gamma;                 // nonzero: the strength of each trajectory is its damping rate
-    unsigned long long *ctr;       // if non-null: work counters (draws, explicit comp-slices, lazy branch-epochs,
-                                   // explicit comp-epochs), added once per trajectory
+    unsigned long long *ctr;       // if non-null: 8 work counters (see qram_work_counters), added once per trajectory
     int hist_pad;                  // bins per exponent histogram (dynamic shared memory: 3 of them)
+    double gamma_lim;              // damping rates at or above this are rejected per trajectory (QRAM_E_ARG)
+    int channel;                   // QRAM_CHANNEL_DAMPING or QRAM_CHANNEL_DEPHASING (the jump keeps its sites)
     SliceOps ops[kMaxT];
     uint32_t occ2[kMaxT];  // per slice: path-word positions any noiseless orbit can hold excited
     Orbit orbit;
 };
 
+// One persistent launch over several problems (different encodings, n, k):
+// the work-stealing counter runs over the concatenated trajectory ranges
+// [start[p], start[p + 1]) of problems p = 0 .. nprob - 1, whose Params sit
+// in device memory.
+constexpr int kMaxBatch = 16;
+struct MultiParams {
+    const Params *probs;          // device, nprob entries
+    uint32_t *work;               // work-stealing counter over all trajectories
+    uint32_t nprob;
+    uint32_t dyn_words;           // dynamic shared memory (32-bit words): the largest problem's
+    uint32_t start[kMaxBatch + 1];
+};
+
 cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_trajectories_multi(const MultiParams &mp, int grid, int block, size_t smem, cudaStream_t s);
+int kernel_blocks_per_sm_multi(int threads, size_t dyn);
 cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s);
 cudaError_t launch_uniform_weight(const double *re, const double *im, int D, int qubit_k, double *out, cudaStream_t s);
 cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n, uint32_t cap,
                                  uint32_t *o_addr, uint32_t *o_bus, uint64_t *o_hash, double *o_re,
                                  double *o_im, cudaStream_t s);
 // host-side helpers shared by the API and the serving loop
+// largest damping rate (exclusive) whose unnormalised weights stay in range (kLnBudget)
+double gamma_limit(int n, int k);
 size_t estimate_sim_bytes(int enc, int n, int k, int D, int slots, double gmax, int threads);
 int build_ops(int n, int k, SliceOps *ops);
 // occ2[s] = (layer, slot) positions, as path-word bits, that an item can

@@ -18,7 +18,7 @@
 //      slot on the address path) plus a short list of off-path excitations;
 //      gates on the path word are a few bit operations, anything else takes
 //      a generic slow path.  K0 is applied lazily as an integer exponent.
-//   5. at a slice with candidates: mask weights (Eq. (18)), including the
+//   5. at a slice with candidates: mask weights (Eq. (21)), including the
 //      closed-form weight of the predicted good branches before the first
 //      jump; one auxiliary draw picks J in the canonical order (empty mask
 //      first, then sorted (site, level) lists lexicographically, a proper
@@ -165,7 +165,7 @@ struct Smem {
     uint32_t region;               // after a jump: root of the subtree that can hold excitations
     uint64_t gq[kGapBits];         // fault stream: 64-bit fixed-point (1 - gamma)^(2^m)
     uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
-    uint32_t wk[4];                // work of this trajectory (see Params::ctr)
+    uint32_t wk[8];                // work of this trajectory (see Params::ctr)
     double fprod2[kMaxT];          // product-form lazy weights: prod_l (1 + a^(2 ov_l(s))) per slice s
     double fprod1;                 // prod_l (1 + a^(ov_l(T-1))): the final overlap
     int16_t etab[4][16];           // lazy epochs: address exposure by nibble of the address
@@ -838,9 +838,13 @@ __device__ __forceinline__ bool slice_touches(const SliceOps &op, uint32_t LX, i
     return ((op.iswap | op.cswap | (op.cswap << 1)) & LX) != 0u || (op.fetch >= 0 && ((LX >> (n - 1)) & 1u));
 }
 
-// One slice of gates.  LX = xs_layers(c, xs), kept current here.
-__device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16_t *xs, const Ctx &C, uint32_t &LX) {
-    if (fast_slice(op, c, C)) return true;
+// One slice of gates.  LX = xs_layers(c, xs), kept current here.  Returns
+// the form that evolved it: kPathFast (path words), kPathReg (register
+// generic slice), kPathMem (memory generic slice), or 0 when a capacity was
+// exceeded.
+enum : int { kPathFast = 1, kPathReg = 2, kPathMem = 3 };
+__device__ __forceinline__ int apply_slice(const SliceOps &op, CompR &c, uint16_t *xs, const Ctx &C, uint32_t &LX) {
+    if (fast_slice(op, c, C)) return kPathFast;
     if (c.nexc && !slice_touches(op, LX, C.n)) {
         // the off-path items sit this slice out: path A alone, as long as no
         // item leaves it (an off-path list never coexists with a path B)
@@ -849,7 +853,7 @@ __device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16
         if (fast_slice(op, a, C) && a.ldiv < 0) {
             a.nexc = c.nexc;
             c = a;
-            return true;
+            return kPathFast;
         }
     }
     int okv;
@@ -857,11 +861,11 @@ __device__ __forceinline__ bool apply_slice(const SliceOps &op, CompR &c, uint16
     if (okv) {
         c = h;
         LX = xs_layers(c, xs);
-        return true;
+        return kPathReg;
     }
     c = slow_slice(op, c, xs, C, &okv);
     LX = xs_layers(c, xs);
-    return okv != 0;
+    return okv ? kPathMem : 0;
 }
 
 __device__ __forceinline__ int excited_count(const CompR &c) {
@@ -1119,7 +1123,7 @@ __device__ __forceinline__ int ov(int lo, int hi, int s) {   // |[lo,hi] n [1,s]
     return top >= lo ? top - lo + 1 : 0;
 }
 
-// closed-form exposure of a good branch after damping layers 1..s (Eq. (12);
+// closed-form exposure of a good branch after damping layers 1..s (Eq. (14);
 // Prop. 1 for the qutrit data slots)
 __device__ int good_exposure(const Params &P, uint32_t col, int s) {
     const uint32_t i = __ldg(P.addr + col);
@@ -1140,7 +1144,7 @@ __device__ int good_exposure(const Params &P, uint32_t col, int s) {
 
 // ---- lazy branches --------------------------------------------------------
 // Before the first fired jump every configuration is still on its noiseless
-// orbit: K0 only scales it (Eq. (12)).  Its path word at any slice follows
+// orbit: K0 only scales it (Eq. (14)).  Its path word at any slice follows
 // from the orbit table, its weight from the closed-form exposure; explicit
 // state is only needed once a jump fires, and only for the configurations
 // whose mask at that slice is non-empty (the others are annihilated).
@@ -1331,7 +1335,10 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     const size_t slot = blockIdx.x;
     const Scratch &scr = P.scr;
     uint32_t *cand = scr.cand + slot * scr.cand_cap;
-    const bool valid = gamma >= 0.0 && gamma < 1.0 && !(P.input_error && *P.input_error);
+    // rates at or above gamma_lim would underflow the unnormalised weights
+    // (sampling alone does not form them)
+    const bool valid = gamma >= 0.0 && gamma < 1.0 && (P.mode == kSampleOnly || gamma < P.gamma_lim) &&
+                       !(P.input_error && *P.input_error);
 
     if (P.input_error && *P.input_error) {          // inputs failed validation: touch nothing else
         if (threadIdx.x == 0 && P.out) {
@@ -1345,7 +1352,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     }
     if (threadIdx.x == 0) {
         S.status = valid ? QRAM_OK : QRAM_E_ARG; S.refcol = -1; S.nbad = 0; S.nJ = 0;
-        S.wk[0] = S.wk[1] = S.wk[2] = S.wk[3] = 0;
+        for (int q = 0; q < 8; ++q) S.wk[q] = 0;
     }
     for (int w = threadIdx.x; w < 512; w += NT) { S.badbits[w] = 0; S.hitbits[w] = 0; }
     for (int w = threadIdx.x; w < 1024; w += NT) S.candbits[w] = 0;
@@ -1455,8 +1462,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     }
 
     // pruned mode keeps every branch implicit until a jump fires (the state
-    // dump reads the explicit set at the end, so it keeps the eager form)
-    const bool lazy = P.mode == kPruned && P.orbit.ok && !P.dump_mode && !depol;
+    // dump takes the same form: a jump-free trajectory is emitted from the
+    // closed forms of every branch, a jumped one from its explicit survivors)
+    const bool lazy = P.mode == kPruned && P.orbit.ok && !depol;
     // lazy epochs in product form: qubit input over every address, equal weights
     const bool factored = lazy && P.col_of != nullptr && P.w2u != nullptr && *P.w2u > 0.0;
 
@@ -1489,7 +1497,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     }
     for (int sw = (int)threadIdx.x; factored && sw < T; sw += NT) {
         // sum over every address of a^(2E) after damping slices 1..s: the
-        // address bits enter independently (Eq. (12))
+        // address bits enter independently (Eq. (14))
         double p2 = 1.0, p1 = 1.0;
         for (int l = 0; l < n; ++l) {
             const double x = apow(S, ov(2 * l + 1, T - 2 * l - 2, sw));
@@ -1594,7 +1602,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             S.fO = lp ? w2c * al : (uni ? w2u : 1.0);
         }
         if (lazy && !jumped && threadIdx.x < 128) {
-            // exposure tables of the closed form (Eq. (12); Prop. 1 for the
+            // exposure tables of the closed form (Eq. (14); Prop. 1 for the
             // qutrit data slots) after damping slices 1..sw
             const int sw = final_epoch ? T - 1 : s1 - 1;
             const int g = (threadIdx.x >> 4) & 3, v = threadIdx.x & 15;
@@ -1639,7 +1647,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         double wsum = 0.0, wempty = 0.0, ovl = 0.0, ovi = 0.0;
         bool capfail_lazy = false;
         if (lazy_pre) {
-            // closed-form weights of every branch (Eq. (12), Lemma 1): the
+            // closed-form weights of every branch (Eq. (14), Lemma 1): the
             // configurations of a branch share its address exposure E and
             // differ only in their data qubits, whose factors are per-epoch
             // scalars.  Equal-magnitude inputs are counted in the integer
@@ -1727,6 +1735,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
         if (threadIdx.x < ncomp_pass) nxt = scr.cs[cbase + threadIdx.x];
         uint32_t nsl = 0;                                  // component-slices evolved by this thread
+        uint32_t n2p = 0, nreg = 0, nmem = 0, noff = 0;    // by form: two paths, register / memory generic, off-path
         for (uint32_t r0 = 0; r0 < ncomp_pass; r0 += NT) {
             const uint32_t r = r0 + threadIdx.x;
             bool alive = r < ncomp_pass;
@@ -1743,24 +1752,34 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                 C = make_ctx(P.enc, n, P.mem, addr);
                 if (s_prev > 0) {                           // pending K_J of slice s_prev
+                    // damping lowers the sites of J; dephasing keeps them
+                    // excited (a projection), and K0 then acts only on the
+                    // excited sites outside J
+                    int keep = 0;
                     if (nJ > 0) {
                         alive = holds_all(c, xs, C, S.J, nJ);
-                        if (alive)
+                        if (alive && P.channel == QRAM_CHANNEL_DAMPING)
                             for (int j = 0; j < nJ; ++j) {
                                 int okc;
                                 c = clear_site(c, xs, C, S.J[j] >> 1, &okc);
                                 if (!okc) capfail = true;
                             }
+                        else keep = nJ;
                     }
-                    if (alive) c.e += excited_count(c);
+                    if (alive) c.e += excited_count(c) - keep;
                 }
             }
             if (alive) {
                 const int slast = final_epoch ? T - 1 : s1;
                 nsl += (uint32_t)(slast - s_prev);
                 uint32_t LX = xs_layers(c, xs);
+                noff += c.nexc ? 1u : 0u;
                 for (int s = s_prev + 1; s <= slast; ++s) {
-                    if (!apply_slice(P.ops[s], c, xs, C, LX)) { capfail = true; break; }
+                    const int form = apply_slice(P.ops[s], c, xs, C, LX);
+                    if (!form) { capfail = true; break; }
+                    n2p += (form == kPathFast && c.pwB) ? 1u : 0u;
+                    nreg += form == kPathReg ? 1u : 0u;
+                    nmem += form == kPathMem ? 1u : 0u;
                     if (npev) {                             // depolarizing faults of slice s
                         bool okall = true;
                         for (uint32_t e = S.pslice_off[s]; e < S.pslice_off[s + 1]; ++e) {
@@ -1863,6 +1882,16 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         if (lane == 0) S.segn[warp] = wcur;
         nsl = __reduce_add_sync(0xFFFFFFFFu, nsl);
         if (lane == 0 && nsl) atomicAdd(&S.wk[1], nsl);
+        if (__any_sync(0xFFFFFFFFu, (n2p | nreg | nmem | noff) != 0u)) {
+            n2p = __reduce_add_sync(0xFFFFFFFFu, n2p);
+            nreg = __reduce_add_sync(0xFFFFFFFFu, nreg);
+            nmem = __reduce_add_sync(0xFFFFFFFFu, nmem);
+            noff = __reduce_add_sync(0xFFFFFFFFu, noff);
+            if (lane == 0) {
+                atomicAdd(&S.wk[4], n2p); atomicAdd(&S.wk[5], nreg);
+                atomicAdd(&S.wk[6], nmem); atomicAdd(&S.wk[7], noff);
+            }
+        }
         if (threadIdx.x == 0) {
             if (lazy_pre) S.wk[2] += (uint32_t)P.D;
             else S.wk[3] += ncomp_pass;
@@ -1887,7 +1916,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         }
         block_sum3(wsum, wempty, ovl, S, S.fW, S.fW, S.fO);
         // good branches of the eager form: closed-form weights before the
-        // first jump (Eq. (18))
+        // first jump (Eq. (21))
         double wgs = 0.0, ogs = 0.0;
         if (P.mode == kPruned && !jumped && !lazy && !depol) {
             const int sw = final_epoch ? T - 1 : s1 - 1;
@@ -1929,17 +1958,18 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 R.status = (uint8_t)S.status;
                 if (P.out) P.out[t] = R;
                 if (P.ctr)
-                    for (int q = 0; q < 4; ++q) atomicAdd(P.ctr + q, (unsigned long long)S.wk[q]);
+                    for (int q = 0; q < 8; ++q) atomicAdd(P.ctr + q, (unsigned long long)S.wk[q]);
                 if (P.dump_mode) {
                     P.dump.scal[0] = Wtot;
                     P.dump.scal[1] = jumped ? 1.0 : 0.0;
                     P.dump.scal[2] = depol ? 1.0 : 0.0;           // every branch explicit: nothing to predict
+                    P.dump.scal[3] = lazy ? 1.0 : 0.0;            // no branch explicit before a jump
                 }
             }
             __syncthreads();
             return;
         }
-        // ---- 5. joint draw at slice s1 (Theorem 3 with Eq. (18) weights) ----
+        // ---- 5. joint draw at slice s1 (Theorem 3 with Eq. (21) weights) ----
         const double u = uniform53(P.seed, (uint32_t)s1, 2u, traj);
         double tgt = u * Wtot;
         int nsel = 0;
@@ -2216,6 +2246,75 @@ __global__ void __launch_bounds__(NT, MINB) traj_kernel(const __grid_constant__ 
     }
 }
 
+// Mixed persistent launch: one work-stealing loop over the trajectories of
+// several problems.  A CTA maps the global trajectory index to its problem,
+// copies that problem's Params from device memory into shared memory when
+// the problem changes, and runs the same per-trajectory code as traj_kernel
+// (damping only: the depolarizing variant is not instantiated here).  Every
+// problem's scratch holds at least gridDim.x slots.
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) traj_kernel_multi(const __grid_constant__ MultiParams MP) {
+    __shared__ Smem<NT> S;
+    __shared__ __align__(16) Params Ps;
+    extern __shared__ __align__(16) uint32_t dyn_hist[];
+    for (uint32_t b = threadIdx.x; b < MP.dyn_words; b += NT) dyn_hist[b] = 0;
+    if (threadIdx.x == 0) S.part = reinterpret_cast<double *>(dyn_hist);
+    __syncthreads();
+    const uint32_t total = MP.start[MP.nprob];
+    int cur = -1;                                   // problem whose Params are in Ps (same in every thread)
+    for (;;) {
+        if (threadIdx.x == 0) S.t = (int)atomicAdd(MP.work, 1u);
+        __syncthreads();
+        const uint32_t t = (uint32_t)S.t;
+        __syncthreads();
+        if (t >= total) break;
+        int p = 0;
+        while (p + 1 < (int)MP.nprob && t >= MP.start[p + 1]) ++p;
+        if (p != cur) {
+            static_assert(sizeof(Params) % 8 == 0, "Params copy in 8-byte words");
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(MP.probs + p);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(&Ps);
+            for (uint32_t w = threadIdx.x; w < sizeof(Params) / 8; w += NT) dst[w] = src[w];
+            cur = p;
+            __syncthreads();
+        }
+        run_one<NT, false>(Ps, S, t - MP.start[p], dyn_hist);
+        __syncthreads();
+    }
+}
+
+template <int NT, int MINB>
+static cudaError_t launch_multi_variant(const MultiParams &mp, int grid, size_t dyn, cudaStream_t s,
+                                        bool occupancy_only, int *blocks) {
+    cudaError_t e = cudaFuncSetAttribute(traj_kernel_multi<NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(3 * kHistMax * sizeof(uint32_t)));
+    if (e != cudaSuccess) return e;
+    if (occupancy_only)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, traj_kernel_multi<NT, MINB>, NT, dyn);
+    traj_kernel_multi<NT, MINB><<<grid, NT, dyn, s>>>(mp);
+    return cudaGetLastError();
+}
+
+static cudaError_t dispatch_multi(int threads, const MultiParams &mp, int grid, size_t dyn, cudaStream_t s, bool occ,
+                                  int *blocks) {
+    switch (threads) {
+    case 128: return launch_multi_variant<128, 8>(mp, grid, dyn, s, occ, blocks);
+    case 256: return launch_multi_variant<256, 4>(mp, grid, dyn, s, occ, blocks);
+    case 512: return launch_multi_variant<512, 2>(mp, grid, dyn, s, occ, blocks);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_trajectories_multi(const MultiParams &mp, int grid, int threads, size_t dyn, cudaStream_t s) {
+    return dispatch_multi(threads, mp, grid, dyn, s, false, nullptr);
+}
+
+int kernel_blocks_per_sm_multi(int threads, size_t dyn) {
+    int b = 0;
+    if (dispatch_multi(threads, MultiParams{}, 0, dyn, nullptr, true, &b) != cudaSuccess) { cudaGetLastError(); return 0; }
+    return b;
+}
+
 // launch variants (threads per CTA, minimum resident CTAs for the register cap)
 template <int NT, int MINB, bool DEPOL>
 static cudaError_t launch_variant(const Params &p, int grid, size_t dyn, cudaStream_t s, bool occupancy_only, int *blocks) {
@@ -2343,15 +2442,19 @@ __global__ void dump_finalize_kernel(const Params P, uint32_t n_in, uint32_t *ou
             }
         }
     }
-    // predicted good branches (pruned mode, no jump fired)
+    // branches in closed form (pruned mode, no jump fired): the good ones of
+    // the eager form, or every branch of the lazy form
     if (P.mode != kPruned || d.scal[1] != 0.0 || d.scal[2] != 0.0) return;
+    const bool all_closed = d.scal[3] != 0.0;
     const double g = P.gamma[0];
     const double a = sqrt(1.0 - g);
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < (uint32_t)P.D; b += gridDim.x * blockDim.x) {
         const uint32_t i = __ldg(P.addr + b);
-        // the reference and the bad branches were explicit
-        if (P.o_badbits && ((P.o_badbits[i >> 5] >> (i & 31u)) & 1u)) continue;
-        if ((int)b == *P.o_ref) continue;
+        // eager form: the reference and the bad branches were explicit
+        if (!all_closed) {
+            if (P.o_badbits && ((P.o_badbits[i >> 5] >> (i & 31u)) & 1u)) continue;
+            if ((int)b == *P.o_ref) continue;
+        }
         int E = 0;
         const int n = P.n, T = P.T;
         for (int l = 0; l < n; ++l)

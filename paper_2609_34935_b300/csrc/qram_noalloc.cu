@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>            // driver types only: the two driver calls are looked up at run time
 #include <cuda_runtime.h>
 
 #include "qram_internal.h"
@@ -33,18 +34,60 @@ static __device__ __align__(256) unsigned char g_qram_static_scratch[kStaticByte
 namespace {
 
 std::mutex g_mu;
+// Per device: the context the array's address was looked up in, and that
+// address.  A device reset (or any teardown of the context) reloads the
+// module at a new address, so the cached one is only valid in its context.
+unsigned long long g_ctx[kMaxDevices] = {};
 void *g_base[kMaxDevices] = {};
 
-// Once per device, with that device current: the device address of the
-// static array (the host-side symbol is only a stand-in, not an address).
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// Unique id of the context current on this thread (0 on failure).  The
+// driver calls come through the runtime's entry-point query, so the library
+// does not link the driver library itself.
+unsigned long long current_ctx_id() {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return 0;
+        }
+        get_current = (PfnCtxGetCurrent)f1;
+        get_id = (PfnCtxGetId)f2;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Once per device and context, with that device current: the device address
+// of the static array (the host-side symbol is only a stand-in, not an
+// address).  Looked up again when the current context is not the one of the
+// cached address (after a device reset, or under another context).
 int static_setup(int device, size_t dyn, void **base, int *resident_slots) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (device < 0 || device >= kMaxDevices) return QRAM_E_ARG;
-    if (!g_base[device]) {
+    unsigned long long ctx = current_ctx_id();
+    if (ctx == 0) {
+        // no context current yet: make the device's primary context current
+        // (this initialises it); a context the caller made current is kept
+        if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return QRAM_E_CUDA; }
+        ctx = current_ctx_id();
+        if (ctx == 0) return QRAM_E_CUDA;
+    }
+    if (!g_base[device] || g_ctx[device] != ctx) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_qram_static_scratch);
         if (e != cudaSuccess || !p) { cudaGetLastError(); return QRAM_E_CUDA; }
         g_base[device] = p;
+        g_ctx[device] = ctx;
     }
     *base = g_base[device];
     *resident_slots = resident_slots_per_device(device, kernel_threads(), dyn);
@@ -95,7 +138,7 @@ extern "C" int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k,
     if (n < 1 || n > kMaxN || k < 1 || k > kMaxK || k > n) return QRAM_E_ARG;
     if (num_branches < 1 || num_branches > (1 << n)) return QRAM_E_ARG;
     if (!memory || !addr || !bus || !amp_re || !amp_im || !gamma || !out) return QRAM_E_ARG;
-    if (!(gamma_max >= 0.0 && gamma_max < 1.0)) return QRAM_E_ARG;
+    if (!(gamma_max >= 0.0 && gamma_max < gamma_limit(n, k))) return QRAM_E_ARG;
     if (ntraj == 0) return QRAM_OK;
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return QRAM_E_CUDA;
@@ -118,6 +161,7 @@ extern "C" int qram_run_static(int mode, int32_t encoding, int32_t n, int32_t k,
     build_orbit(n, k, P.ops, &P.orbit);
     P.enc = encoding; P.n = n; P.k = k; P.T = 6 * n + 2 * k; P.D = num_branches;
     P.nodes = (1 << n) - 1; P.M = 2 * P.nodes; P.nthreads = threads; P.hist_pad = hist_pad(n, k);
+    P.gamma_lim = gamma_limit(n, k);
     P.mem = memory; P.addr = addr; P.bus = bus; P.amp_re = amp_re; P.amp_im = amp_im;
     P.seed = seed; P.traj0 = traj0; P.ntraj = ntraj; P.gamma = gamma;
     P.mode = mode == 0 ? kPruned : kFull;

@@ -197,8 +197,9 @@ bool valid_request(const qram_request_t *q) {
     if (p.num_branches < 1 || p.num_branches > (1 << p.n)) return false;
     if (!p.memory || !p.addr || !p.bus || !p.amp_re || !p.amp_im) return false;
     if (q->ntraj < 1 || !q->gamma || (q->mode != 0 && q->mode != 1)) return false;
+    const double lim = qram::gamma_limit(p.n, p.k);
     for (uint32_t t = 0; t < q->ntraj; ++t)
-        if (!(q->gamma[t] >= 0.0 && q->gamma[t] < 1.0)) return false;
+        if (!(q->gamma[t] >= 0.0 && q->gamma[t] < lim)) return false;
     return true;
 }
 

@@ -10,12 +10,16 @@ import workloads as W
 
 
 def test_traffic_record_needs_matching_sources(tmp_path, monkeypatch):
+    """The small-case record's bytes per trajectory scale to the step's
+    trajectories, and only while the kernel sources are the recorded ones."""
     rec = tmp_path / "traffic.json"
     h = bench._kernel_sources_hash()
-    rec.write_text(json.dumps({"dram_bytes_per_step_launch": 123, "sources_sha256": h}))
+    rec.write_text(json.dumps({"dram_bytes_per_trajectory": 123.0, "sources_sha256": h}))
     monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(rec))
-    assert bench._traffic_per_step() == 123
-    rec.write_text(json.dumps({"dram_bytes_per_step_launch": 123, "sources_sha256": "0" * 64}))
+    assert bench._traffic_per_step() == 123.0 * bench.NTRAJ
+    rec.write_text(json.dumps({"dram_bytes_per_trajectory": 123.0, "sources_sha256": "0" * 64}))
+    assert bench._traffic_per_step() is None
+    rec.write_text(json.dumps({"dram_bytes_per_step_launch": 123, "sources_sha256": h}))   # full-size record: unused
     assert bench._traffic_per_step() is None
     rec.write_text("not json")
     assert bench._traffic_per_step() is None

@@ -1,0 +1,169 @@
+"""GPU parity at the workload sizes, in the launch configurations that the
+benchmark times, against the CPU oracle.
+
+- qubit n=12, k=4, data-loading input, 1e5 trajectories with damping rates
+  log-uniform in [1e-5, 1e-2] per batch of 1000: one graph-captured launch of
+  512-thread CTAs under the benchmark's damping-rate bound, sampled across
+  the gamma range with the jumped trajectories of the upper decades first;
+  the compared trajectories are shown (work counters) to run the post-jump
+  two-path and generic forms;
+- qutrit n=10, k=1, gamma = 1e-3, 1e5 trajectories in one graph-captured
+  launch: every 50th trajectory;
+- qubit n=6, k=1, gamma in {1e-4, 1e-3, 1e-2}, 1e4 trajectories each: every
+  trajectory (so every one with a fired jump), and the jump-free ones against
+  the closed-form no-jump fidelity;
+- the damping-rate limit of the unnormalised amplitudes: just below it the
+  oracle's answer (or a capacity status), at it QRAM_E_ARG, never a silent
+  mismatch.
+
+Integer outputs bit-exact, floating point within 1e-12 absolute."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import core
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+QRAM_E_ARG, QRAM_E_CAP = 1, 6
+
+
+def _sim(p, seed):
+    from paper_2609_34935_b300 import QramSim
+    return QramSim(p, seed=seed, device=0)
+
+
+def _cmp(got, ref):
+    assert np.all(got["status"] == 0), np.unique(got["status"])
+    for f in ("bad", "ref", "ncand", "jumps", "first_jump_slice", "jump_sites", "q_ground"):
+        assert np.array_equal(got[f].astype(np.int64), ref[f].astype(np.int64)), f
+    for f in ("fidelity", "fidelity_unsampled", "p_ground"):
+        d = np.abs(got[f] - ref[f])
+        assert np.max(d) < TOL, (f, float(np.max(d)), int(np.argmax(d)))
+
+
+def _oracle_at(p, seed, idx, gam_h):
+    """The oracle on scattered trajectory indices, one per host thread."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        parts = list(ex.map(lambda t: core.run(p, seed, int(t), gam_h[t:t + 1], nthreads=1), idx))
+    return np.concatenate(parts)
+
+
+def _graph_run(sim, gam_h, gamma_bound, threads):
+    """One persistent launch over every trajectory, captured in a CUDA graph
+    and replayed (the benchmark's step)."""
+    from paper_2609_34935_b300 import QramSim
+    sim.set_gamma_bound(gamma_bound)
+    sim.set_variant(threads)
+    gam = torch.tensor(gam_h, dtype=torch.float64, device="cuda:0")
+    out = torch.empty((len(gam_h), 48), dtype=torch.uint8, device="cuda:0")
+    t0 = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    graph = sim.graph("pruned", gam, out, t0)
+    graph()
+    torch.cuda.synchronize()
+    raw = out.cpu().numpy().copy()
+    graph.close()
+    return raw, QramSim.results(torch.from_numpy(raw))
+
+
+def test_bench_launch_configuration_matches_oracle():
+    n, k, ntraj, seed = 12, 4, 100_000, 4001
+    p = W.data_loading(W.QUBIT, n, k, seed=seed)
+    gam_h = W.gamma_batches(ntraj, 1000, 1e-5, 1e-2, seed=seed)
+    sim = _sim(p, seed)
+    raw, res = _graph_run(sim, gam_h, 1e-2, 512)
+    assert np.all(res["status"] == 0)
+    # sample: 24 trajectories below 1e-4, then the trajectories with the most
+    # jump sites in [1e-4, 1e-3), [1e-3, 5e-3) and [5e-3, 1e-2]
+    pick = []
+    bins = [(0.0, 1e-4, 24), (1e-4, 1e-3, 32), (1e-3, 5e-3, 48), (5e-3, 1.0, 48)]
+    for lo, hi, m in bins:
+        idx = np.nonzero((gam_h >= lo) & (gam_h < hi))[0]
+        if lo == 0.0:
+            sel = idx[:: max(1, len(idx) // m)][:m]
+        else:
+            order = np.argsort(-res["jump_sites"][idx].astype(np.int64), kind="stable")
+            sel = idx[order[:m]]
+            assert np.all(res["jumps"][sel] > 0)
+        pick.extend(int(t) for t in sel)
+    pick = np.array(sorted(set(pick)))
+    assert np.sum(gam_h[pick] >= 5e-3) >= 8
+    # the same trajectories launched one by one (bitwise equal to the graph's
+    # rows) with the work counters reset: they take the post-jump forms
+    sim.work_counters(reset=True)
+    for t in pick:
+        one = sim.run_pruned(int(t), torch.tensor(gam_h[t:t + 1], device="cuda:0")).cpu().numpy()
+        assert np.array_equal(one[0], raw[t])
+    w = sim.work_counters(reset=True)
+    sim.close()
+    assert w["two_path_slices"] > 0 and w["reg_generic_slices"] > 0 and w["offpath_comp_epochs"] > 0, w
+    _cmp(res[pick], _oracle_at(p, seed, pick, gam_h))
+
+
+def test_qutrit_n10_graph_launch_matches_oracle():
+    n, k, ntraj, seed, gamma = 10, 1, 100_000, 3001, 1e-3
+    p = W.data_loading(W.QUTRIT, n, k, seed=seed)
+    gam_h = np.full(ntraj, gamma)
+    sim = _sim(p, seed)
+    _, res = _graph_run(sim, gam_h, gamma, 256)
+    sim.close()
+    pick = np.arange(0, ntraj, 50)
+    ref = _oracle_at(p, seed, pick, gam_h)
+    _cmp(res[pick], ref)
+    assert np.sum(ref["jumps"] > 0) > 100
+
+
+@pytest.mark.parametrize("gamma,seed", [(1e-4, 2001), (1e-3, 2002), (1e-2, 2003)])
+def test_qubit_n6_every_trajectory(gamma, seed):
+    n, k, ntraj = 6, 1, 10_000
+    p = W.data_loading(W.QUBIT, n, k, seed=seed)
+    g = np.full(ntraj, gamma)
+    sim = _sim(p, seed)
+    got = sim.results(sim.run_pruned(0, torch.tensor(g, device="cuda:0")))
+    full = sim.results(sim.run_full(0, torch.tensor(g, device="cuda:0")))
+    sim.close()
+    ref = core.run(p, seed, 0, g)
+    _cmp(got, ref)
+    _cmp(full, ref)
+    assert np.sum(ref["jumps"] > 0) > 0
+    nj = got["jumps"] == 0
+    F0 = cf.no_jump_fidelity(W.QUBIT, n, k, gamma, p.addr, p.bus, p.amp, p.memory)
+    assert np.max(np.abs(got["fidelity"][nj & (got["q_ground"] == 1)] - F0)) < TOL
+
+
+def _gamma_limit(n, k):
+    # 1 - exp(-650 / ((2n + k)(T - 1))): the limit the library documents
+    return -math.expm1(-650.0 / ((2 * n + k) * (6 * n + 2 * k - 1)))
+
+
+@pytest.mark.parametrize("n,k,below_parity", [(5, 3, True), (8, 2, True), (12, 4, False)])
+def test_gamma_limit_boundary(n, k, below_parity):
+    """Just below the limit: the oracle's answer (or a capacity status);
+    at and above it: QRAM_E_ARG per trajectory and for the rate bound.  At
+    n = 12, k = 4 the limit (0.255) puts about 2000 candidates in every
+    slice, so only the rejection side is run there."""
+    seed = 4001
+    p = W.data_loading(W.QUBIT, n, k, seed=seed)
+    lim = _gamma_limit(n, k)
+    sim = _sim(p, seed)
+    if below_parity:
+        below = np.full(6, lim * 0.98)
+        got = sim.results(sim.run_pruned(0, torch.tensor(below, device="cuda:0")))
+        ref = core.run(p, seed, 0, below)
+        ok = got["status"] == 0
+        assert np.all(ok | (got["status"] == QRAM_E_CAP))        # a capacity status, never a silent mismatch
+        assert np.sum(ok) >= 3
+        _cmp(got[ok], ref[ok])
+    above = np.array([lim * (1 + 1e-9), lim * 1.01, 0.999])
+    got = sim.results(sim.run_pruned(0, torch.tensor(above, device="cuda:0")))
+    assert np.all(got["status"] == QRAM_E_ARG)
+    with pytest.raises(Exception):
+        sim.set_gamma_bound(lim * 1.001)
+    sim.close()

@@ -128,15 +128,34 @@ def _hash_cfg(cfg):
     return h or 1
 
 
-@pytest.mark.parametrize("enc,n,k,gamma,kind", [(W.QUBIT, 4, 3, 6e-2, "load"), (W.QUTRIT, 4, 2, 4e-2, "rand"),
-                                               (W.QUBIT, 5, 2, 1e-2, "rand"), (W.QUBIT, 3, 3, 0.0, "load")])
+DUMP_CASES = [
+    # encoding, n, k, gamma, input, both jump-free and jumped trajectories among the 12
+    (W.QUBIT, 4, 3, 6e-2, "load", False), (W.QUTRIT, 4, 2, 4e-2, "rand", False),
+    (W.QUBIT, 5, 2, 1e-2, "rand", True), (W.QUBIT, 3, 3, 0.0, "load", False),
+    (W.QUBIT, 6, 2, 3e-3, "load", True),      # every address, equal weights: the product-form lazy epochs
+    (W.QUBIT, 8, 2, 1e-3, "load", True),
+    (W.QUBIT, 6, 3, 4e-3, "rand", True),      # unequal complex weights: FP64 lazy weights
+    (W.QUTRIT, 6, 1, 3e-3, "load", True),     # integer exponent histograms
+]
+
+
+@pytest.mark.parametrize("enc,n,k,gamma,kind,mix", DUMP_CASES)
 @pytest.mark.parametrize("mode", ["pruned", "full"])
-def test_final_state_amplitudes(enc, n, k, gamma, kind, mode):
+def test_final_state_amplitudes(enc, n, k, gamma, kind, mix, mode):
+    """Final amplitudes of every component, keyed by (address, bus word,
+    tree configuration), against the oracle's full evolution at 1e-12.  In
+    pruned mode the dump runs the lazy form that qram_run_pruned runs (the
+    closed-form branch-epoch counter moves): a jump-free trajectory comes
+    entirely from the closed forms, a jumped one from the configurations
+    materialised at its first jump."""
     seed = 555 + n
     p = _problem(enc, n, k, kind, seed)
     sim = _sim(p, seed)
-    for traj in range(8):
-        _, d = core.run_one(p, seed, traj, gamma, None, cap=1 << 14)
+    sim.work_counters(reset=True)
+    jumped = []
+    for traj in range(12):
+        r, d = core.run_one(p, seed, traj, gamma, None, cap=1 << 16)
+        jumped.append(int(r["jumps"]) > 0)
         want = {}
         for a, b, cfg, amp in zip(d.addr, d.bus, d.configs, d.amp):
             want[(int(a), int(b), _hash_cfg(cfg))] = amp
@@ -147,12 +166,17 @@ def test_final_state_amplitudes(enc, n, k, gamma, kind, mode):
             got[key] = got.get(key, 0) + z
         for key in set(want) | set(got):
             assert abs(want.get(key, 0) - got.get(key, 0)) < TOL, (traj, key)
+    w = sim.work_counters(reset=True)
+    if mode == "pruned":
+        assert w["branch_epochs"] > 0                 # the lazy form ran
+    if mix:
+        assert any(jumped) and not all(jumped)
     sim.close()
 
 
 def test_fixed_history_annihilation():
     """A fired jump on the reference's path annihilates every predicted good
-    group (Sec. V.A); fixed histories exercise it independently of the FAULT
+    group (Sec. VI.A); fixed histories exercise it independently of the FAULT
     stream."""
     n, k = 5, 2
     p = W.data_loading(W.QUBIT, n, k, seed=9)

@@ -73,17 +73,69 @@ def test_static_entry_point_matches_allocating_one(enc, n, k, gamma, mode):
         _same(QramSim.results(out), ref)
 
 
-def test_static_entry_point_rejects_oversize_and_bad_input():
+def test_static_entry_point_rejects_oversize():
     import workloads as W
-    from paper_2609_34935_b300 import QramSim
     L = _lib()
     big = W.data_loading(1, 14, 8, seed=1)                    # 16384 x 256 components: beyond 32 MiB
     g = torch.full((4,), 1e-3, dtype=torch.float64, device="cuda:0")
     rc, _ = _static(L, 0, big, 1, 0, g, 1e-2)
     assert rc == 8                                            # QRAM_E_TOOBIG
-    bad = W.data_loading(1, 4, 2, seed=2)
-    bad.addr = bad.addr.copy()
-    bad.addr[3] = bad.addr[2]                                 # duplicate address
+    p = W.data_loading(1, 6, 2, seed=1)
+    rc, _ = _static(L, 0, p, 1, 0, g, 0.9)                    # gamma_max beyond the damping-rate limit
+    assert rc == 1                                            # QRAM_E_ARG
+
+
+def _corrupt(p, kind):
+    p.addr, p.bus, p.memory, p.amp = p.addr.copy(), p.bus.copy(), p.memory.copy(), p.amp.copy()
+    if kind == "duplicate_address":
+        p.addr[3] = p.addr[2]
+    elif kind == "address_range":
+        p.addr[3] = 1 << p.n
+    elif kind == "bus_range":
+        p.bus[2] = 1 << p.k
+    elif kind == "memory_range":
+        p.memory[5] = 1 << p.k
+    elif kind == "norm":
+        p.amp *= 1.01
+    elif kind == "nan_amplitude":
+        p.amp[0] = complex(float("nan"), 0.0)
+    return p
+
+
+@pytest.mark.parametrize("kind", ["duplicate_address", "address_range", "bus_range", "memory_range", "norm",
+                                  "nan_amplitude"])
+def test_static_entry_point_rejects_bad_input(kind):
+    """Inputs live in device memory, so they are checked on the device before
+    the trajectory kernel reads them: every trajectory reports QRAM_E_ARG."""
+    import workloads as W
+    from paper_2609_34935_b300 import QramSim
+    L = _lib()
+    bad = _corrupt(W.data_loading(1, 4, 2, seed=2), kind)
+    g = torch.full((4,), 1e-2, dtype=torch.float64, device="cuda:0")
     rc, out = _static(L, 0, bad, 1, 0, g, 1e-2)
     assert rc == 0
     assert np.all(QramSim.results(out)["status"] == 1)        # QRAM_E_ARG on every trajectory
+
+
+def test_static_entry_point_reports_capacity_without_writing_past_out():
+    """A damping rate far above gamma_max overflows the candidate scratch
+    sized for gamma_max: the trajectory reports QRAM_E_CAP, the others are
+    unaffected, and nothing is written past the caller's output rows."""
+    import workloads as W
+    from paper_2609_34935_b300 import QramSim
+    L = _lib()
+    p = W.data_loading(1, 8, 2, seed=5)
+    mem, addr, bus, re, im = _dev(p)
+    nt, guard = 6, 4
+    g = torch.full((nt,), 1e-4, dtype=torch.float64, device="cuda:0")
+    g[2] = 0.3
+    buf = torch.full((nt + guard, 48), 0xAB, dtype=torch.uint8, device="cuda:0")
+    rc = L.qram_run_static(0, p.encoding, p.n, p.k, len(p.addr), mem.data_ptr(), addr.data_ptr(), bus.data_ptr(),
+                           re.data_ptr(), im.data_ptr(), 11, 0, nt, g.data_ptr(), 1e-4, buf.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert rc == 0
+    res = QramSim.results(buf[:nt])
+    assert res["status"][2] == 6                              # QRAM_E_CAP
+    assert np.all(np.delete(res["status"], 2) == 0)
+    assert bool(torch.all(buf[nt:] == 0xAB))
