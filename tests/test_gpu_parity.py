@@ -330,8 +330,10 @@ def test_work_counters_exact():
     sim.results(sim.run_full(0, g0))
     w = sim.work_counters(reset=True)
     assert w["draws"] == 0
-    assert w["comp_slices"] == ntraj * p.D * (1 << k) * (T - 1)
-    assert w["comp_epochs"] == ntraj * p.D * (1 << k)
+    # one merged component per branch through slices 1..2n (before the first
+    # wall its 2^k configurations share the tree), then every configuration
+    assert w["comp_slices"] == ntraj * p.D * (2 * n + (1 << k) * (T - 1 - 2 * n))
+    assert w["comp_epochs"] == ntraj * p.D * (1 + (1 << k))
     sim.results(sim.run_pruned(0, g0))
     w = sim.work_counters(reset=True)
     assert w["comp_slices"] == 0 and w["comp_epochs"] == 0
@@ -432,4 +434,46 @@ def test_depolarizing_final_state_amplitudes(enc, n, k, gamma, eps):
             got[key] = got.get(key, 0) + z
         for key in set(want) | set(got):
             assert abs(want.get(key, 0) - got.get(key, 0)) < TOL, (traj, key)
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", ["pruned", "full"])
+def test_merged_components_before_the_first_wall(mode):
+    """Jumps before the first Hadamard wall (slices <= 2n), while one merged
+    component per branch stands for its 2^k wall configurations, then
+    candidates in the data phase after the expansion: fixed histories
+    against the oracle, trajectory by trajectory and amplitude by
+    amplitude."""
+    n, k = 6, 3
+    p = W.random_columns(W.QUBIT, n, k, D=50, seed=17)
+    T = 6 * n + 2 * k
+    seed = 2718
+    rng = np.random.default_rng(5)
+    hists = []
+    for t in range(40):
+        early = sorted({(int(rng.integers(2, 2 * n + 1)), int(rng.integers(0, 2 * (2 ** n - 1))) % 8)
+                        for _ in range(3)})
+        late = sorted({(int(rng.integers(2 * n + 1, T)), int(rng.integers(0, 2 * (2 ** n - 1))))
+                       for _ in range(6)})
+        hists.append(sorted(set(early + late)))
+    cand, off = [], [0]
+    for h in hists:
+        cand += [(s << 16) | q for s, q in h]
+        off.append(len(cand))
+    sim = _sim(p, seed)
+    sim.set_fault_history(torch.tensor(np.array(cand, np.int64).astype(np.int32), device="cuda:0"),
+                          torch.tensor(np.array(off, np.int32), device="cuda:0"))
+    g = np.full(len(hists), 0.02)
+    got = sim.results(sim.run(mode, 0, torch.tensor(g, device="cuda:0")))
+    early_jumps = 0
+    for t, h in enumerate(hists):
+        r, _ = core.run_one(p, seed, t, 0.02, core.History([s for s, _ in h], [q for _, q in h]), cap=1 << 14)
+        assert got["status"][t] == 0
+        for f in ("jumps", "first_jump_slice", "jump_sites", "q_ground", "bad", "ref"):
+            assert int(got[f][t]) == int(r[f]), (t, f)
+        for f in ("fidelity", "fidelity_unsampled", "p_ground"):
+            assert abs(got[f][t] - r[f]) < TOL, (t, f)
+        early_jumps += int(0 < r["first_jump_slice"] <= 2 * n)
+    assert early_jumps >= 3
+    sim.set_fault_history()
     sim.close()
