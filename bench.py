@@ -91,7 +91,7 @@ def _kernel_sources_hash() -> str:
 
 def _traffic_per_step():
     """DRAM bytes of one step launch: the committed ncu record of the small
-    mix case (--profile-mix: 296 trajectories with the bench's mix of damping
+    mix case (--profile-mix: 592 trajectories with the bench's mix of damping
     rates, one launch) scaled per trajectory to the 1e5 trajectories of a
     step; only if it was taken on the kernel sources of this tree."""
     try:
@@ -237,10 +237,10 @@ def main():
     ap.add_argument("--scan", action="store_true",
                     help="fidelity vs n (qubit, k=3, 500-branch random input, 200 trajectories per point)")
     ap.add_argument("--profile-case", type=float, default=None, metavar="GAMMA",
-                    help="one launch of 296 trajectories (148 CTAs of 512 threads) at this gamma, for ncu")
+                    help="one launch of 592 trajectories (296 CTAs of 512 threads) at this gamma, for ncu")
     ap.add_argument("--profile-mix", action="store_true",
-                    help="one launch of 296 trajectories of the bench workload (every 337th index, with its gamma; "
-                         "148 CTAs of 512 threads), for ncu: the small case whose traffic scales to a step")
+                    help="one launch of 592 trajectories with the bench workload's rates (every 168th index; "
+                         "296 CTAs of 512 threads), for ncu: the small case whose traffic scales to a step")
     ap.add_argument("--configs", action="store_true",
                     help="the other workload configurations (qutrit n=3, qubit n=6, qutrit n=10): throughput, "
                          "work and measured peaks")
@@ -447,8 +447,8 @@ def main():
             "note": "algorithmic INT32 ops per step launch from the kernel's work counters x ops per unit "
                     f"{OPS_PER_UNIT} / launch time from CUDA events; peak derived: SMs x {INT32_LANES} INT32 "
                     "lanes/clock x median SM clock under load (measured_peaks: the measured add/logic rate); "
-                    "traffic: DRAM read+write bytes per trajectory of the small mix case (ncu, one launch of 296 "
-                    "trajectories, same kernel sources) x the trajectories of a step, else null",
+                    "traffic: DRAM read+write bytes per trajectory of the small mix case (ncu, one launch of 592 "
+                    "trajectories on the step's 296 CTAs, same kernel sources) x the trajectories of a step, else null",
             "work_per_step": {k: v / args.steps for k, v in work.items()}, "variant_threads": variant}
     try:
         from paper_2609_34935_b300 import measure_peaks
@@ -674,22 +674,24 @@ def run_configs(args):
     return 0
 
 
-PROFILE_TRAJ = 296          # two per CTA of a 148-CTA launch
-PROFILE_STRIDE = 337        # the mix case: trajectory indices 0, 337, ... (spans the 100 gamma batches)
+PROFILE_TRAJ = 592          # two per CTA of a launch with the bench's 296 CTAs (2 per SM)
+PROFILE_STRIDE = 168        # the mix case: trajectory indices 0, 168, ... (spans the 100 gamma batches)
 
 
 def run_profile_case(gamma):
     """Small case of the bench kernel for a profiler capture: the bench
-    problem, one launch, one CTA per SM, two trajectories per CTA.  With a
-    gamma, every trajectory has that rate.  Without (the mix case),
-    trajectories 0..295 take the rates of every PROFILE_STRIDE-th index of
-    the bench workload: about three per gamma batch, the bench's own mix of
-    rates, so per-trajectory counters (DRAM bytes, work) scale to a step."""
+    problem in the bench's launch shape (512-thread CTAs, two per SM), one
+    launch of two trajectories per CTA.  With a gamma, every trajectory has
+    that rate.  Without (the mix case), trajectories 0..591 take the rates
+    of every PROFILE_STRIDE-th index of the bench workload: about six per
+    gamma batch, the bench's own mix of rates, with as many CTAs sharing L2
+    as in a step, so per-trajectory counters (DRAM bytes, work) scale to a
+    step."""
     import torch
     from paper_2609_34935_b300 import QramSim
     sim = QramSim(_problem(), seed=SEED, device=0)
     sim.set_variant(512)
-    sim.set_launch_ctas(148)
+    sim.set_launch_ctas(PROFILE_TRAJ // 2)
     sim.set_gamma_bound(G_HI)
     if gamma is None:
         idx = np.arange(PROFILE_TRAJ) * PROFILE_STRIDE

@@ -160,6 +160,7 @@ struct Smem {
     double dn, al, qt[kMaxK];      // per-epoch data factors (qubit): norm^2, final overlap, 1/(1 + a^(2 m_t))
     double fdn[kMaxT];             // per trajectory: the norm^2 data factor dn after damping slices 1..s
     double fW, fO;                 // per-epoch scale of the weight sums and of the overlap sum
+    double bw, a2n;                // binomial groups: (1 + a^(4n))^k and a^(2n)
     double hdat[2 * kMaxN + 1];    // per trajectory: (1 + a^(2m)) / 2 and 1 / (1 + a^(2m)), m <= 2n
     double rdat[2 * kMaxN + 1];
     uint32_t region;               // after a jump: root of the subtree that can hold excitations
@@ -272,11 +273,37 @@ __device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem<NT> &S) {
 
 // Entry of a warp's compact selection list (components with a non-empty
 // mask at the slice being drawn): the mask's first element (16 bits), its
-// size capped at 15 (the descent only asks "one element or more"), and for
+// size capped at 7 (the descent only asks "one element or more"), whether
+// the component is a binomial group (bit 19, see kBinFlag), and for
 // equal-magnitude inputs the exponent e (12 bits), from which the descent
 // recomputes the weight w2u a^(2e) instead of the pass storing a double.
-__device__ __forceinline__ uint32_t sel_key(uint32_t c1, uint32_t mcnt, int e) {
-    return (c1 & 0xFFFFu) | (min(mcnt, 15u) << 16) | ((uint32_t)e & 0xFFFu) << 20;
+__device__ __forceinline__ uint32_t sel_key(uint32_t c1, uint32_t mcnt, int e, bool bin) {
+    return (c1 & 0xFFFFu) | (min(mcnt, 7u) << 16) | ((bin ? 1u : 0u) << 19) | ((uint32_t)e & 0xFFFu) << 20;
+}
+
+// Binomial groups (qubit).  After the gates of slice 4n+2k-1 every data
+// qubit is back in the bus.  A branch whose 2^k wall configurations c are
+// all alive, share one tree state, carry the exponents e0 + 2n |c| (every
+// data qubit excited for its whole window, Eq. (4)) and the signs
+// s0 + c.phi is held as one component: the tree state, e0, s0 and phi (in the
+// bus-word field), marked by bit 29 of the packed w word.  Later gates and
+// K_J act on the shared tree alike, so the group stays one: its weight is
+// sum_w C(k, w) a^(2 (e0 + 2n w)), its overlap with the ideal output
+// (-1)^s0 sum_w K_w(|phi ^ b_out|) a^(e0 + 2n w), K_w the Krawtchouk sums
+// sum_{|c| = w} (-1)^(c . psi).
+constexpr uint32_t kBinFlag = 1u << 29;
+
+__device__ __forceinline__ int binom(int k, int w) {
+    int r = 1;
+    for (int q = 1; q <= w; ++q) r = r * (k - w + q) / q;
+    return r;
+}
+// sum over c in {0,1}^k with |c| = w of (-1)^(|c & psi|), |psi| = m
+__device__ __forceinline__ int kraw(int k, int w, int m) {
+    int r = 0;
+    for (int j = 0; j <= w && j <= m; ++j)
+        if (w - j <= k - m) r += ((j & 1) ? -1 : 1) * binom(m, j) * binom(k - m, w - j);
+    return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -1534,18 +1561,25 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     if (ncomp0 > scr.ecap) { if (threadIdx.x == 0) S.status = QRAM_E_CAP; }
     __syncthreads();
     const size_t cbase = slot * (size_t)scr.ecap;
+    // Merged components (qubit).  Until the first Hadamard wall (slice 2n+1)
+    // no data qubit is in the tree, so the 2^k wall configurations of a
+    // branch have the same tree state, exponent and masks; they differ only
+    // in the bus word c and the wall sign (-1)^(j.c), which matter from the
+    // wall on.  Before it, one component per branch stands for all 2^k
+    // (multiplicity 2^mlog in every weight); at the epoch boundary forced at
+    // slice 2n they are expanded into the 2^k configurations.
+    int mlog = (qubit && !lazy) ? kb : 0;
     if (S.status == QRAM_OK && !lazy) {
-        for (uint32_t r = threadIdx.x; r < ncomp0; r += NT) {
-            const uint32_t col = expl[r >> kb], cw = r & ((1u << kb) - 1u);
+        for (uint32_t r = threadIdx.x; r < S.nexpl; r += NT) {
+            const uint32_t col = expl[r];
             CompR c;
             c.pw = 0; c.pwR = 0; c.pwB = 0; c.ldiv = -1; c.e = 0; c.nexc = 0;
-            const uint32_t j = __ldg(P.bus + col);
-            if (qubit) { c.cb = cw; c.sign = __popc(j & cw) & 1u; }   // first wall: (-1)^(j.c)
-            else { c.cb = j; c.sign = 0; }
+            c.cb = qubit ? 0u : __ldg(P.bus + col);                     // qubit: wall configurations at expansion
+            c.sign = 0;
             store_comp(scr, cbase + r, c, nullptr, qubit, col, __ldg(P.addr + col));
         }
     }
-    if (threadIdx.x == 0) S.ncomp = (S.status == QRAM_OK && !lazy) ? ncomp0 : 0;
+    if (threadIdx.x == 0) S.ncomp = (S.status == QRAM_OK && !lazy) ? S.nexpl : 0;
     __syncthreads();
 
     // ---- 4. epochs ----------------------------------------------------------
@@ -1568,8 +1602,129 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         double al = 1.0;                                  // (1 + a^(2n)) / 2 per fully exposed data qubit
         if (qubit) for (int q = 0; q < P.k; ++q) al *= S.hdat[n];
         S.al = al;
+        const double a2n = apow(S, 2 * n), a4n = apow(S, 4 * n);
+        double bw = 1.0;
+        for (int q = 0; q < P.k; ++q) bw *= 1.0 + a4n;
+        S.bw = bw;
+        S.a2n = a2n;
     }
+    // binomial groups from slice sU on (every data qubit back in the bus)
+    const int sU = 4 * n + 2 * P.k - 1;
+    const bool binok = qubit && !depol;
+    const uint32_t kmask = (1u << P.k) - 1u;
     for (;;) {
+        if (mlog > 0 && s_prev >= 2 * n) {
+            // expand the merged components into the 2^k wall configurations
+            // (the pending K_J of slice s_prev acts on each in the pass below).
+            // Top-down chunks: chunk [r0, r0 + NT) writes [r0 2^mlog, ...),
+            // where every component is already read.
+            const uint32_t nc = S.ncomp, m = 1u << mlog;
+            for (int r0 = ((int)nc - 1) / NT * NT; r0 >= 0; r0 -= NT) {
+                const uint32_t r = (uint32_t)r0 + threadIdx.x;
+                const bool have = r < nc;
+                CompR c;
+                alignas(16) uint16_t xs[kXcap];
+                uint32_t lab = 0, addr = 0;
+                if (have) {
+                    unpack(scr.cs[cbase + r], qubit, c, lab, addr);
+                    if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
+                }
+                __syncthreads();
+                if (have) {
+                    const uint32_t j = __ldg(P.bus + lab);
+                    for (uint32_t cw = 0; cw < m; ++cw) {
+                        CompR d = c;
+                        d.cb = cw;
+                        d.sign = c.sign ^ (__popc(j & cw) & 1u);            // first wall: (-1)^(j.c)
+                        store_comp(scr, cbase + (size_t)r * m + cw, d, xs, qubit, lab, addr);
+                    }
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) S.ncomp = nc << mlog;
+            mlog = 0;
+            __syncthreads();
+        }
+        if (binok && mlog == 0 && s_prev == sU && (!lazy || jumped)) {
+            // merge each branch's 2^k wall configurations into a binomial
+            // group where they qualify (see kBinFlag).  A branch's
+            // configurations are consecutive components.  1: the first slot
+            // of each run of one column decides, staging the group component
+            // per column (the selection lists are free here) and its slot in
+            // expl; 2: order-preserving compaction.
+            const uint32_t nc = S.ncomp, K = 1u << P.k;
+            uint4 *stg = reinterpret_cast<uint4 *>(scr.selw + slot * NW * (size_t)scr.selseg);
+            for (uint32_t r = threadIdx.x; r < nc; r += NT) {
+                const uint4 v = scr.cs[cbase + r];
+                const uint32_t col = v.w & 0x3FFFu;
+                if (r > 0 && (scr.cs[cbase + r - 1].w & 0x3FFFu) == col) continue;
+                bool ok = !(v.w & kBinFlag) && r + K <= nc && (scr.cs[cbase + r + K - 1].w & 0x3FFFu) == col &&
+                          (r + K == nc || (scr.cs[cbase + r + K].w & 0x3FFFu) != col);
+                int e0 = -1;
+                uint32_t s0 = 0, phi = 0, seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                const uint32_t nx = (v.z >> 21) & 0x3Fu;
+                for (uint32_t q = 0; ok && q < K; ++q) {
+                    const uint4 m = scr.cs[cbase + r + q];
+                    const uint32_t cb = (m.z >> 12) & 0xFFu;
+                    if (m.x != v.x || m.y != v.y || (m.z >> 21) != (v.z >> 21) || (m.w & kBinFlag) || cb > kmask ||
+                        ((seen[cb >> 5] >> (cb & 31u)) & 1u)) { ok = false; break; }
+                    seen[cb >> 5] |= 1u << (cb & 31u);
+                    for (uint32_t x = 0; x < nx && ok; ++x)
+                        if (scr.exc[(cbase + r + q) * kXcap + x] != scr.exc[(cbase + r) * kXcap + x]) ok = false;
+                    if (cb == 0) { e0 = (int)(m.z & 0xFFFu); s0 = (m.z >> 20) & 1u; }
+                }
+                for (uint32_t q = 0; ok && q < K; ++q) {             // phi from the one-qubit configurations
+                    const uint4 m = scr.cs[cbase + r + q];
+                    const uint32_t cb = (m.z >> 12) & 0xFFu;
+                    if (__popc(cb) == 1 && (((m.z >> 20) & 1u) ^ s0)) phi |= cb;
+                }
+                for (uint32_t q = 0; ok && q < K; ++q) {             // exponents e0 + 2n|c|, signs s0 + c.phi
+                    const uint4 m = scr.cs[cbase + r + q];
+                    const uint32_t cb = (m.z >> 12) & 0xFFu;
+                    if ((int)(m.z & 0xFFFu) != e0 + 2 * n * __popc(cb) ||
+                        ((m.z >> 20) & 1u) != ((s0 + __popc(cb & phi)) & 1u))
+                        ok = false;
+                }
+                uint4 g = make_uint4(0u, 0u, 0u, 0u);
+                if (ok) {
+                    g.x = v.x; g.y = v.y;
+                    g.z = ((uint32_t)e0 & 0xFFFu) | (phi << 12) | (s0 << 20) | (v.z & (0x3FFu << 21));
+                    g.w = (v.w & 0x0FFFFFFFu) | kBinFlag;
+                }
+                stg[col] = g;
+                expl[col] = r;
+            }
+            __syncthreads();
+            uint32_t wr = 0;
+            for (uint32_t r0 = 0; r0 < nc; r0 += NT) {
+                const uint32_t r = r0 + threadIdx.x;
+                bool keep = false;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                alignas(16) uint16_t xs[kXcap];
+                uint32_t nx = 0;
+                if (r < nc) {
+                    v = scr.cs[cbase + r];
+                    const uint32_t col = v.w & 0x3FFFu;
+                    const uint4 g = stg[col];
+                    if (g.w & kBinFlag) { keep = expl[col] == r; v = g; }
+                    else keep = true;
+                    nx = (v.z >> 21) & 0x3Fu;
+                    if (keep && nx) load_exc(scr, cbase + r, nx, xs);
+                }
+                uint32_t tot;
+                const uint32_t pre = block_scan_flag(keep, &tot, S);    // every read of the chunk is done
+                if (keep) {
+                    const size_t gdst = cbase + wr + pre;
+                    scr.cs[gdst] = v;
+                    uint4 *dst = reinterpret_cast<uint4 *>(scr.exc + gdst * kXcap);
+                    const uint4 *src = reinterpret_cast<const uint4 *>(xs);
+                    for (uint32_t q = 0; q < (nx + 7u) / 8u; ++q) dst[q] = src[q];
+                }
+                wr += tot;
+            }
+            if (threadIdx.x == 0) S.ncomp = wr;
+            __syncthreads();
+        }
         // next slice whose candidates can matter: before the first fired jump
         // every component is on a noiseless orbit, so a candidate on a position
         // no orbit can excite leaves J empty and needs no draw; after it, only
@@ -1583,8 +1738,13 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 const uint32_t bits = m[wd] & (wd == (s0 >> 5) ? (0xFFFFFFFFu << (s0 & 31)) : 0xFFFFFFFFu);
                 if (bits) { s1 = min(T, 32 * wd + __ffs(bits) - 1); break; }
             }
+            if (mlog > 0 && s1 > 2 * n) s1 = 2 * n;          // merged components end an epoch at 2n
+            // explicit configurations end an epoch at sU, where they merge into binomial groups
+            if (binok && mlog == 0 && (!lazy || jumped) && s_prev < sU && s1 > sU) s1 = sU;
         }
         const bool final_epoch = s1 >= T;
+        const uint32_t mc = 1u << mlog;                    // configurations per component
+        const double k2m = k2 * (double)mc;
         if (threadIdx.x == 0) {
             S.cl2 = 0;
             // data factors after damping slices 1..sw (tabulated per trajectory)
@@ -1746,6 +1906,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             uint32_t lab = 0, addr = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
             double w = 0.0;
             uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | ground (final) or non-empty mask << 2 | overlap sign + 1
+            const bool binc = alive && (cur.w & kBinFlag);   // binomial group (kBinFlag)
+            int binm = 0;                  // final epoch, binomial group: |phi ^ b_out|
             Ctx C;
             if (alive) {
                 unpack(cur, qubit, c, lab, addr);
@@ -1793,12 +1955,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     }
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
-                if (c.e >= 4096 || (uni && c.e >= H)) capfail = true;   // exponent bound (packed in 12 bits)
+                {
+                    const int etop = c.e + (binc ? 2 * n * P.k : 0);   // the group's largest exponent
+                    if (etop >= 4096 || (uni && etop >= H)) capfail = true;   // exponent bound (packed in 12 bits)
+                }
                 if (!final_epoch) {
                     c1 = mask_first(c, xs, C, S.candbits, S.cl2, mcnt);
                     if (!uni) {
                         const double ae = apow(S, c.e);
-                        w = col_w2(P, lab) * k2 * ae * ae;
+                        w = col_w2(P, lab) * k2m * ae * ae * (binc ? S.bw : 1.0);
                         wsum += w;
                         if (mcnt == 0) wempty += w;
                     } else {
@@ -1812,17 +1977,20 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         const uint32_t col = lab;
                         if (qubit) {
                             const uint32_t bout = __ldg(P.bus + col) ^ __ldg(P.mem + C.i);
-                            ovs = ((c.sign + __popc(c.cb & bout)) & 1u) ? -1 : 1;
+                            if (binc) { binm = __popc((c.cb ^ bout) & kmask); ovs = (c.sign & 1u) ? -1 : 1; }
+                            else ovs = ((c.sign + __popc(c.cb & bout)) & 1u) ? -1 : 1;
                         } else if (c.cb == (__ldg(P.bus + col) ^ __ldg(P.mem + C.i))) {
                             ovs = 1;
                         }
                     }
                     if (!uni) {
-                        w = col_w2(P, lab) * k2 * ae * ae;
+                        w = col_w2(P, lab) * k2 * ae * ae * (binc ? S.bw : 1.0);
                         wsum += w;
                         if (ground) wempty += w;
                         if (ovs) {
-                            const double base = col_w2(P, lab) * k2 * ae;
+                            double base = col_w2(P, lab) * k2 * ae;
+                            if (binc)                                 // prod over the data qubits of 1 +- a^(2n)
+                                for (int q = 0; q < P.k; ++q) base *= q < binm ? 1.0 - S.a2n : 1.0 + S.a2n;
                             if (!qubit && c.sign) {                   // w^sign, w = exp(2 pi i / 3)
                                 ovl -= 0.5 * base;
                                 ovi += (c.sign == 1 ? 0.5 : -0.5) * sqrt(3.0) * base;
@@ -1834,16 +2002,27 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         hkey = ((uint32_t)c.e << 3) | ((ground ? 1u : 0u) << 2) | (uint32_t)(ovs + 1);
                     }
                     if (P.dump_mode && threadIdx.x < NT) {
-                        const uint32_t di = atomicAdd(P.dump.count, 1u);
-                        if (di < P.dump.cap) {
+                        // a binomial group emits each of its wall configurations c
+                        const uint32_t nout = binc ? (1u << P.k) : 1u;
+                        const uint32_t d0 = atomicAdd(P.dump.count, nout);
+                        const uint64_t hh = config_hash(c, xs, C);
+                        for (uint32_t q = 0; q < nout; ++q) {
+                            const uint32_t di = d0 + q;
+                            if (di >= P.dump.cap) break;
                             const uint32_t col = lab;
-                            const double sc = (qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0) * ae;
-                            double pr = (qubit && c.sign) ? -1.0 : 1.0, pim = 0.0;   // phase of the component
-                            if (!qubit && c.sign) { pr = -0.5; pim = (c.sign == 1 ? 0.5 : -0.5) * sqrt(3.0); }
+                            uint32_t sg = c.sign, cbq = c.cb;
+                            double sc = (qubit ? sqrt(ldexp(1.0, -P.k)) : 1.0) * ae;
+                            if (binc) {
+                                cbq = q;
+                                sg = (c.sign + __popc(q & c.cb)) & 1u;
+                                sc *= apow(S, 2 * n * __popc(q));
+                            }
+                            double pr = (qubit && sg) ? -1.0 : 1.0, pim = 0.0;   // phase of the component
+                            if (!qubit && sg) { pr = -0.5; pim = (sg == 1 ? 0.5 : -0.5) * sqrt(3.0); }
                             const double ar = __ldg(P.amp_re + col), ai = __ldg(P.amp_im + col);
                             P.dump.col[di] = col;
-                            P.dump.bus[di] = c.cb;
-                            P.dump.hash[di] = config_hash(c, xs, C);
+                            P.dump.bus[di] = cbq;
+                            P.dump.hash[di] = hh;
                             P.dump.re[di] = (ar * pr - ai * pim) * sc;
                             P.dump.im[di] = (ar * pim + ai * pr) * sc;
                         }
@@ -1852,12 +2031,28 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             }
             if (uni) {
                 // integer histogram counts (shared-memory atomics; sums are order-free)
-                if (hkey != 0xFFFFFFFFu) {
+                if (hkey != 0xFFFFFFFFu && !binc) {
                     const uint32_t e = hkey >> 3;
-                    atomicAdd(&hall[e], 1u);
-                    if ((hkey >> 2) & 1u) atomicAdd(&hemp[e], 1u);
+                    atomicAdd(&hall[e], mc);
+                    if ((hkey >> 2) & 1u) atomicAdd(&hemp[e], mc);
                     const int ovs = (int)(hkey & 3u) - 1;
                     if (ovs) atomicAdd(&hov[e], ovs);
+                } else if (hkey != 0xFFFFFFFFu) {
+                    // a binomial group: C(k, w) configurations at exponent e0 + 2n w;
+                    // overlap (-1)^s0 K_w(|phi ^ b_out|) at the final epoch
+                    const uint32_t e = hkey >> 3;
+                    const int ovs = (int)(hkey & 3u) - 1;
+                    for (int q = 0; q <= P.k; ++q) {
+                        const uint32_t eb = e + (uint32_t)(2 * n * q);
+                        if (eb >= (uint32_t)H) break;
+                        const uint32_t cnt = (uint32_t)binom(P.k, q);
+                        atomicAdd(&hall[eb], cnt);
+                        if ((hkey >> 2) & 1u) atomicAdd(&hemp[eb], cnt);
+                        if (ovs) {
+                            const int kv = ovs * kraw(P.k, q, binm);
+                            if (kv) atomicAdd(&hov[eb], kv);
+                        }
+                    }
                 }
             }
             {
@@ -1865,7 +2060,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ne);
                 if (ne) {
                     const uint32_t pos = wcur + __popc(bal & ((1u << lane) - 1u));
-                    selk[pos] = sel_key(c1, mcnt, uni ? c.e : 0);
+                    selk[pos] = sel_key(c1, mcnt, uni ? c.e : 0, binc);
                     if (!uni) selw[pos] = w;
                 }
                 wcur += __popc(bal);
@@ -1873,10 +2068,10 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             if (compact) {
                 uint32_t tot;
                 const uint32_t pre = block_scan_flag(alive, &tot, S);
-                if (alive && !final_epoch) store_comp(scr, cbase + wr + pre, c, xs, qubit, lab, addr);
+                if (alive && !final_epoch) store_comp(scr, cbase + wr + pre, c, xs, qubit, lab | (binc ? kBinFlag : 0u), addr);
                 wr += tot;
             } else if (alive && !final_epoch) {
-                store_comp(scr, cbase + r, c, xs, qubit, lab, addr);
+                store_comp(scr, cbase + r, c, xs, qubit, lab | (binc ? kBinFlag : 0u), addr);
             }
         }
         if (lane == 0) S.segn[warp] = wcur;
@@ -1978,7 +2173,16 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             // explicit state (after the gates of s1, K0 through s1 - 1) and
             // the compact list of (first element, size, weight) the descent reads
             const uint32_t pos = S.cl2 & P.orbit.occ[s1];
-            const uint32_t ncw = qubit ? (1u << P.k) : 1u;
+            // before the first wall no data qubit is in the tree (no data
+            // hits): one merged component per branch stands for its 2^k
+            // configurations
+            if (qubit && s1 <= 2 * n) mlog = P.k;
+            // from slice sU on every data qubit is in the bus: one binomial
+            // group per branch (its configurations are on the noiseless orbit:
+            // exponents E0 + 2n|c|, signs c.(j ^ d), Lemma 1)
+            const bool mbin = binok && s1 >= sU;
+            const uint32_t ncw = (qubit && mlog == 0 && !mbin) ? (1u << P.k) : 1u;
+            const double wmul = (double)(1u << mlog) * (mbin ? S.bw : 1.0);
             uint32_t base = 0;
             bool capfail = false;
             for (uint32_t b0 = 0; b0 < (uint32_t)P.D; b0 += NT) {
@@ -1989,6 +2193,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     i = __ldg(P.addr + b); j = __ldg(P.bus + b); d = __ldg(P.mem + i);
                     if ((S.hitbits[i >> 5] >> (i & 31u)) & 1u) tm = orbit_hits(P, S.candbits, pos, s1, i, j, d, all);
                     cnt = all ? ncw : (tm ? ncw - (ncw >> __popc(tm)) : 0u);
+                    if ((mlog > 0 || mbin) && tm) { capfail = true; cnt = 0; }   // (no data qubit in the tree then)
                 }
                 uint32_t tot;
                 const uint32_t pre = block_scan_count(cnt, &tot, S);
@@ -2005,22 +2210,24 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     if (take) {
                         CompR c = orbit_state(P, s1, i, cw, j, d);
                         c.e = E0 + (qubit ? data_exposure(P, cw, s1 - 1) : 0);
-                        store_comp(scr, cbase + r, c, nullptr, qubit, b, i);
+                        if (mbin) c.cb = (j ^ (d & P.orbit.fetched[s1])) & kmask;   // phi of the group
+                        store_comp(scr, cbase + r, c, nullptr, qubit, b | (mbin ? kBinFlag : 0u), i);
                         ++r;
                         c1 = mask_first(c, nullptr, C, S.candbits, S.cl2, mcnt);
                         ce = c.e;
                         if (uni) {
-                            if (c.e >= 4096 || c.e >= H) capfail = true;  // the key holds 12 bits of e
+                            const int etop = c.e + (mbin ? 2 * n * P.k : 0);
+                            if (etop >= 4096 || etop >= H) capfail = true;  // the key holds 12 bits of e
                         } else {
                             const double ae = apow(S, c.e);
-                            w = w2 * ae * ae;
+                            w = w2 * ae * ae * wmul;
                         }
                     }
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
                     if (take) {
                         const uint32_t q = wcur + __popc(bal & ((1u << lane) - 1u));
                         if (q < scr.selseg) {
-                            selk[q] = sel_key(c1, mcnt, uni ? ce : 0);
+                            selk[q] = sel_key(c1, mcnt, uni ? ce : 0, mbin);
                             if (!uni) selw[q] = w;
                         }
                         else capfail = true;
@@ -2058,12 +2265,19 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         const double *sw = sw0 + q * (size_t)scr.selseg;
                         for (uint32_t e = threadIdx.x; e < S.segn[q]; e += NT) {
                             const uint32_t kv = sk[e], code = kv & 0xFFFFu;
-                            const bool in = eq_only_single ? code == ceq && ((kv >> 16) & 15u) == 1u : code <= cmax;
+                            const bool in = eq_only_single ? code == ceq && ((kv >> 16) & 7u) == 1u : code <= cmax;
                             if (eq_only_single && code == ceq && !in) mm = 1;
                             if (in) {
                                 if (uni) {
                                     const uint32_t ex = kv >> 20;
-                                    if (ex < (uint32_t)H) atomicAdd(&hall[ex], 1u);
+                                    if (!((kv >> 19) & 1u)) {
+                                        if (ex < (uint32_t)H) atomicAdd(&hall[ex], 1u);
+                                    } else {                   // a binomial group
+                                        for (int q = 0; q <= P.k; ++q) {
+                                            const uint32_t eb = ex + (uint32_t)(2 * n * q);
+                                            if (eb < (uint32_t)H) atomicAdd(&hall[eb], (uint32_t)binom(P.k, q));
+                                        }
+                                    }
                                 } else {
                                     f += sw[e];
                                 }
@@ -2081,7 +2295,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         }
                     }
                     if (multi) *multi = mm;
-                    return block_sum(f, S.redA, S) * (uni ? w2u : 1.0);
+                    return block_sum(f, S.redA, S) * (uni ? w2u * (double)(1u << mlog) : 1.0);
                 };
                 uint32_t lo = 0, hi = ncodes;
                 double Flo = 0.0;
@@ -2111,12 +2325,14 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     double we = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
                         CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
-                        unpack(scr.cs[cbase + r], qubit, c, lab, addr);
+                        const uint4 rv = scr.cs[cbase + r];
+                        unpack(rv, qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         if (mask_query(c, xs, C, S.candbits, pref, level) == -1) {
                             const double ae = apow(S, c.e);
-                            we += (uni ? w2u : col_w2(P, lab) * k2) * ae * ae;
+                            we += (uni ? w2u : col_w2(P, lab) * k2) * (double)(1u << mlog) * ae * ae *
+                                  ((rv.w & kBinFlag) ? S.bw : 1.0);
                         }
                     }
                     we = block_sum(we, S.redA, S);
@@ -2132,13 +2348,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     double f = 0.0;
                     for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
                         CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
-                        unpack(scr.cs[cbase + r], qubit, c, lab, addr);
+                        const uint4 rv = scr.cs[cbase + r];
+                        unpack(rv, qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
                         const long long q = mask_query(c, xs, C, S.candbits, pref, level);
                         if (q >= 0 && (uint32_t)q <= cmid) {
                             const double ae = apow(S, c.e);
-                            f += (uni ? w2u : col_w2(P, lab) * k2) * ae * ae;
+                            f += (uni ? w2u : col_w2(P, lab) * k2) * (double)(1u << mlog) * ae * ae *
+                                 ((rv.w & kBinFlag) ? S.bw : 1.0);
                         }
                     }
                     f = block_sum(f, S.redA, S);
@@ -2186,6 +2404,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             S.nJ = nsel;
             if (lazy_pre && nsel == 0) S.ncomp = 0;       // no jump: the branches stay implicit
         }
+        if (lazy_pre && nsel == 0) mlog = 0;
         __syncthreads();
         if (nsel > 0) {
             if (!jumped) first_jump = (uint32_t)s1;
