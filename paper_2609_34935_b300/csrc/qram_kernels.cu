@@ -1568,18 +1568,24 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     // wall on.  Before it, one component per branch stands for all 2^k
     // (multiplicity 2^mlog in every weight); at the epoch boundary forced at
     // slice 2n they are expanded into the 2^k configurations.
-    int mlog = (qubit && !lazy) ? kb : 0;
+    // (k = 1: two configurations per branch; the forced epoch boundaries would cost more than merging saves)
+    const bool mergeable = qubit && P.k >= 2;
+    int mlog = (mergeable && !lazy) ? kb : 0;
+    // components created here: one per column (merged, or qutrit), or its 2^k wall configurations
+    const int clog = (qubit && mlog == 0) ? kb : 0;
+    const uint32_t ncreate = S.nexpl << clog;
     if (S.status == QRAM_OK && !lazy) {
-        for (uint32_t r = threadIdx.x; r < S.nexpl; r += NT) {
-            const uint32_t col = expl[r];
+        for (uint32_t r = threadIdx.x; r < ncreate; r += NT) {
+            const uint32_t col = expl[r >> clog], cw = r & ((1u << clog) - 1u);
             CompR c;
             c.pw = 0; c.pwR = 0; c.pwB = 0; c.ldiv = -1; c.e = 0; c.nexc = 0;
-            c.cb = qubit ? 0u : __ldg(P.bus + col);                     // qubit: wall configurations at expansion
-            c.sign = 0;
+            const uint32_t j = __ldg(P.bus + col);
+            if (qubit) { c.cb = cw; c.sign = __popc(j & cw) & 1u; }   // first wall: (-1)^(j.c) (merged: c = 0)
+            else { c.cb = j; c.sign = 0; }
             store_comp(scr, cbase + r, c, nullptr, qubit, col, __ldg(P.addr + col));
         }
     }
-    if (threadIdx.x == 0) S.ncomp = (S.status == QRAM_OK && !lazy) ? S.nexpl : 0;
+    if (threadIdx.x == 0) S.ncomp = (S.status == QRAM_OK && !lazy) ? ncreate : 0;
     __syncthreads();
 
     // ---- 4. epochs ----------------------------------------------------------
@@ -1610,7 +1616,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     }
     // binomial groups from slice sU on (every data qubit back in the bus)
     const int sU = 4 * n + 2 * P.k - 1;
-    const bool binok = qubit && !depol;
+    const bool binok = mergeable && !depol;
     const uint32_t kmask = (1u << P.k) - 1u;
     for (;;) {
         if (mlog > 0 && s_prev >= 2 * n) {
@@ -2176,7 +2182,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             // before the first wall no data qubit is in the tree (no data
             // hits): one merged component per branch stands for its 2^k
             // configurations
-            if (qubit && s1 <= 2 * n) mlog = P.k;
+            if (mergeable && s1 <= 2 * n) mlog = P.k;
             // from slice sU on every data qubit is in the bus: one binomial
             // group per branch (its configurations are on the noiseless orbit:
             // exponents E0 + 2n|c|, signs c.(j ^ d), Lemma 1)
