@@ -18,7 +18,7 @@ _SRC = os.path.join(_HERE, "qram_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 
 OK, E_ARG, E_OOM, E_SCHED, E_CAP = 0, 1, 2, 3, 4
-DAMPING, DEPHASING = 0, 1      # the per-slice channel (amplitude damping; the phase-damping channel)
+DAMPING, DEPHASING, HEATING = 0, 1, 2   # the per-slice channel (amplitude damping; phase damping; heating)
 G_LOAD, G_UNLOAD, G_BUS, G_ISWAP, G_CSWAP, G_FETCH = 1, 2, 3, 4, 5, 6
 GATE_NAMES = {1: "load", 2: "unload", 3: "bus", 4: "iswap", 5: "cswap", 6: "fetch"}
 
@@ -67,7 +67,7 @@ def lib():
         L.oracle_sample_faults.argtypes = [vp, u64, u64, f64, vp, vp, i32, vp, vp, vp, vp]
         L.oracle_schedule.argtypes = [i32, i32, vp, vp, vp, i32, vp]
         L.oracle_occupancy.argtypes = [vp, vp]
-        L.oracle_joint_layer.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp, i32]
+        L.oracle_joint_layer.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp, i32, vp]
         L.oracle_bad_range.argtypes = [i32, i32, C.c_uint32, vp, vp]
         L.oracle_bad_range.restype = None
         L.oracle_philox.argtypes = [vp, u64, vp]
@@ -274,8 +274,9 @@ def occupancy(prob) -> np.ndarray:
     return occ.reshape(T, M)
 
 
-def joint_layer(comps, cand, gamma: float, u: float, channel: int = DAMPING):
-    """One joint layer (amplitude damping, or dephasing) on an explicit state.
+def joint_layer(comps, cand, gamma: float, u: float, channel: int = DAMPING, levels=None):
+    """One joint layer (amplitude damping, dephasing or heating) on an explicit state;
+    levels: heating only, the target level (1 = L / excited, 2 = R) of each candidate in sorted order.
 
     comps: list of (addr, bus, config, amp) with config a tuple of (site, level).
     Returns (new comps, J as tuple of (site, level))."""
@@ -294,13 +295,15 @@ def joint_layer(comps, cand, gamma: float, u: float, channel: int = DAMPING):
     re = np.array([complex(c[3]).real for c in comps], np.float64)
     im = np.array([complex(c[3]).imag for c in comps], np.float64)
     cnd = np.ascontiguousarray(sorted(cand) or [0], dtype=np.int32)
+    hl = np.ascontiguousarray([levels[q] for q in sorted(cand)] if levels is not None and len(cand) else [1],
+                              dtype=np.uint8)
     nout = C.c_int32(0)
     jn = C.c_int32(0)
     js = np.zeros(maxe, np.uint32)
     jl = np.zeros(maxe, np.uint8)
     _check(L.oracle_joint_layer(m, _ptr(addr), _ptr(bus), _ptr(ne), _ptr(sites), _ptr(lvls), _ptr(re),
                                 _ptr(im), C.byref(nout), _ptr(cnd), len(cand), gamma, u,
-                                C.byref(jn), _ptr(js), _ptr(jl), int(channel)), "joint_layer")
+                                C.byref(jn), _ptr(js), _ptr(jl), int(channel), _ptr(hl)), "joint_layer")
     out = []
     for r in range(nout.value):
         cfg = tuple((int(sites[r * maxe + e]), int(lvls[r * maxe + e])) for e in range(int(ne[r])))

@@ -62,10 +62,12 @@ def simulate(encoding: int, n: int, k: int, memory, gamma: float, addr=None, bus
              eps: float = 0.0, depol_first: bool = True, channel: str = "damping"):
     """Returns (F_rho, trace, marginal distribution over (address, bus)).
 
-    channel: "damping" (Eqs. (5)-(6)) or "dephasing": the phase-damping
+    channel: "damping" (Eqs. (5)-(6)); "dephasing": the phase-damping
     channel with the same no-jump operator diag(1, a) (qutrit diag(1, a, a))
-    and the jump sqrt(gamma)|1><1| (qutrit sqrt(gamma)|L><L|, sqrt(gamma)|R><R|),
-    the diagonal channel of the outlook (Sec. VII).
+    and the jump sqrt(gamma)|1><1| (qutrit sqrt(gamma)|L><L|, sqrt(gamma)|R><R|);
+    "heating": the no-jump operator diag(a, 1) (qutrit diag(a, 1, 1)) with the
+    jump sqrt(gamma)|1><0| (qutrit sqrt(gamma/2)|L><W|, sqrt(gamma/2)|R><W|);
+    the diagonal channels of the outlook (Sec. VII).
 
     eps: depolarizing channel of strength eps on every tree site after the
     gates of every slice (Sec. II.B): with probability eps one of the
@@ -178,13 +180,20 @@ def simulate(encoding: int, n: int, k: int, memory, gamma: float, addr=None, bus
         return r.reshape(dim, dim)
 
     H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2)
-    if channel not in ("damping", "dephasing"):
+    if channel not in ("damping", "dephasing", "heating"):
         raise ValueError(channel)
     if encoding == 1 and channel == "damping":
         kraus = [np.array([[1, 0], [0, a]], dtype=np.complex128),
                  np.array([[0, sq], [0, 0]], dtype=np.complex128)]
+    elif encoding == 1 and channel == "heating":
+        kraus = [np.diag([a, 1]).astype(np.complex128), np.array([[0, 0], [sq, 0]], dtype=np.complex128)]
     elif encoding == 1:
         kraus = [np.diag([1, a]).astype(np.complex128), np.diag([0, sq]).astype(np.complex128)]
+    elif channel == "heating":
+        h = math.sqrt(gamma / 2.0)
+        kraus = [np.diag([a, 1, 1]).astype(np.complex128),
+                 np.array([[0, 0, 0], [h, 0, 0], [0, 0, 0]], dtype=np.complex128),
+                 np.array([[0, 0, 0], [0, 0, 0], [h, 0, 0]], dtype=np.complex128)]
     elif channel == "damping":
         kraus = [np.diag([1, a, a]).astype(np.complex128),
                  np.array([[0, sq, 0], [0, 0, 0], [0, 0, 0]], dtype=np.complex128),

@@ -89,6 +89,16 @@
  *      for damping and the joint sampler of Sec. IV.D applies unchanged
  *      (Theorem 3's argument only uses that diagonal); a jump projects onto
  *      the components holding the site excited instead of lowering it.
+ *      Heating (the outlook's qutrit heating channel; also run for qubits)
+ *      is taken as the diagonal no-jump operator K0 = diag(a, 1, 1) on
+ *      {W, L, R} (qubit diag(a, 1)) with the jumps sqrt(gamma/2)|L><W| and
+ *      sqrt(gamma/2)|R><W| (qubit sqrt(gamma)|1><0|).  K_J^dagger K_J is again
+ *      diagonal, so the joint sampler applies with the masks taken over the
+ *      ground sites: J = {(q, level_q) : q in C, x_q = W}, each candidate's
+ *      target level (qutrit) drawn with the candidates: bit 0 of word 0 of
+ *      counter (site, slice | 6 << 24, traj) on stream HEAT=6 (0 -> L,
+ *      1 -> R).  K0 then weighs a component by a per ground site outside J,
+ *      i.e. by a^(-#excited) relative to a factor common to all.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -103,7 +113,7 @@ enum { OR_OK = 0, OR_E_ARG = 1, OR_E_OOM = 2, OR_E_SCHED = 3, OR_E_CAP = 4 };
 enum { G_LOAD = 1, G_UNLOAD, G_BUS, G_ISWAP, G_CSWAP, G_FETCH };
 enum { ENC_QUTRIT = 0, ENC_QUBIT = 1 };
 enum { LV_W = 0, LV_L = 1, LV_R = 2 };   /* qubit: 0 / 1 use LV_W / LV_L */
-enum { CH_DAMPING = 0, CH_DEPHASING = 1 };  /* the per-slice channel (S7) */
+enum { CH_DAMPING = 0, CH_DEPHASING = 1, CH_HEATING = 2 };  /* the per-slice channel (S7) */
 
 typedef struct {
     int32_t encoding, n, k;
@@ -126,7 +136,7 @@ typedef struct {
     int32_t stop_slice;                      /* > 0: stop after this slice's damping layer and
                                               * return that state (an observation point for tests;
                                               * the outputs then describe the partial query) */
-    int32_t channel;                         /* CH_DAMPING (0) or CH_DEPHASING (1), S7 */
+    int32_t channel;                         /* CH_DAMPING (0), CH_DEPHASING (1) or CH_HEATING (2), S7 */
 } ohist;
 
 typedef struct {
@@ -500,6 +510,24 @@ static int cmp_omw(const void *pa, const void *pb)
     return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
 }
 
+/* heating (S7): the target level of candidate (slice, site) */
+static int heat_level(uint64_t seed, uint64_t traj, int slice, int32_t site, int qubit)
+{
+    if (qubit) return LV_L;
+    uint32_t o[4];
+    draw(seed, (uint32_t)site, (uint32_t)slice, 6u, traj, o);
+    return (o[0] & 1u) ? LV_R : LV_L;
+}
+
+/* heating mask: the candidate sites x holds at the ground level, with the
+ * candidates' target levels (lv[j] for cand[j]) */
+static void mask_of_heat(const ocomp *x, const int32_t *cand, const uint8_t *lv, int nc, omask *m)
+{
+    m->n = 0;
+    for (int j = 0; j < nc; j++)
+        if (get_lvl(x, (uint32_t)cand[j]) == LV_W) { m->site[m->n] = (uint32_t)cand[j]; m->lvl[m->n] = lv[j]; m->n++; }
+}
+
 /* mask J(x) = C intersect X(x) with the levels of x (Eq. (21)) */
 static void mask_of(const ocomp *x, const int32_t *cand, int nc, omask *m)
 {
@@ -515,7 +543,8 @@ static void mask_of(const ocomp *x, const int32_t *cand, int nc, omask *m)
 /* One joint layer on the state: candidate set cand[0..nc) (sorted),
  * auxiliary uniform u.  Selects J (written to Jout), applies K_J of Eq. (17)
  * and normalises.  Returns 0 on success. */
-static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, double u, int channel, omask *Jout)
+static int joint_layer(ostate *st, const int32_t *cand, const uint8_t *hlv, int nc, double gamma, double u,
+                       int channel, omask *Jout)
 {
     double a = sqrt(1.0 - gamma), sg = sqrt(gamma);
     Jout->n = 0;
@@ -529,7 +558,8 @@ static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, do
             double w = x->re * x->re + x->im * x->im;
             W += w;
             omask m;
-            mask_of(x, cand, nc, &m);
+            if (channel == CH_HEATING) mask_of_heat(x, cand, hlv, nc, &m);
+            else mask_of(x, cand, nc, &m);
             if (m.n == 0) w_empty += w;
             else { list[nl].m = m; list[nl].w = w; list[nl].idx = r; nl++; }
         }
@@ -560,6 +590,25 @@ static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, do
      * level is annihilated, and K0 = diag(1, a) (diag(1, a, a)) gives a
      * factor a per excited site outside J. */
     size_t w = 0;
+    if (channel == CH_HEATING) {
+        /* heating: K_J needs every site of J at the ground level and raises it
+         * to its target level; K0 gives a per ground site outside J, i.e.
+         * a^(M - #excited - |J|): a^(-#excited) up to a factor common to all */
+        for (size_t r = 0; r < st->n; r++) {
+            ocomp x = st->c[r];
+            int alive = 1;
+            for (int j = 0; j < Jout->n; j++)
+                if (get_lvl(&x, Jout->site[j]) != LV_W) { alive = 0; break; }
+            if (!alive) continue;
+            double f = 1.0;
+            for (int e = 0; e < x.ne; e++) f /= a;
+            for (int j = 0; j < Jout->n; j++)
+                if (set_lvl(&x, Jout->site[j], Jout->lvl[j])) return OR_E_CAP;
+            x.re *= f; x.im *= f;
+            st->c[w++] = x;
+        }
+        st->n = w;
+    } else
     for (size_t r = 0; r < st->n; r++) {
         ocomp x = st->c[r];
         int alive = 1;
@@ -590,9 +639,10 @@ static int joint_layer(ostate *st, const int32_t *cand, int nc, double gamma, do
 int oracle_joint_layer(int32_t ncomp, uint32_t *addr, uint32_t *bus, int32_t *ne, uint32_t *sites,
                        uint8_t *lvls, double *re, double *im, int32_t *ncomp_out,
                        const int32_t *cand, int32_t nc, double gamma, double u,
-                       int32_t *jn, uint32_t *jsite, uint8_t *jlvl, int32_t channel)
+                       int32_t *jn, uint32_t *jsite, uint8_t *jlvl, int32_t channel, const uint8_t *hlv)
 {
-    if (channel != CH_DAMPING && channel != CH_DEPHASING) return OR_E_ARG;
+    if (channel != CH_DAMPING && channel != CH_DEPHASING && channel != CH_HEATING) return OR_E_ARG;
+    if (channel == CH_HEATING && !hlv) return OR_E_ARG;
     ostate st = { 0 };
     for (int r = 0; r < ncomp; r++) {
         ocomp x; memset(&x, 0, sizeof(x));
@@ -603,7 +653,7 @@ int oracle_joint_layer(int32_t ncomp, uint32_t *addr, uint32_t *bus, int32_t *ne
         if (push(&st, &x)) { free(st.c); return OR_E_OOM; }
     }
     omask J;
-    int rc = joint_layer(&st, cand, nc, gamma, u, channel, &J);
+    int rc = joint_layer(&st, cand, hlv, nc, gamma, u, channel, &J);
     if (rc) { free(st.c); return rc; }
     *jn = J.n;
     for (int j = 0; j < J.n; j++) { jsite[j] = J.site[j]; jlvl[j] = J.lvl[j]; }
@@ -880,7 +930,12 @@ static int run_traj(const oproblem *P, const osched *S, uint64_t seed, uint64_t 
             else { uint32_t o[4]; draw(seed, 0, (uint32_t)s, 2u, traj, o); u = uniform53(o[0], o[1]); }
         }
         omask J;
-        if ((rc = joint_layer(&st, cand, ncs, gamma, u, channel, &J))) goto fail;
+        uint8_t hlv[OR_MAXE * 64];
+        if (channel == CH_HEATING) {
+            if (ncs > (int)sizeof(hlv)) { rc = OR_E_CAP; goto fail; }
+            for (int j = 0; j < ncs; j++) hlv[j] = (uint8_t)heat_level(seed, traj, s, cand[j], qubit);
+        }
+        if ((rc = joint_layer(&st, cand, hlv, ncs, gamma, u, channel, &J))) goto fail;
         if (J.n > 0) {
             if (out->jumps == 0) out->first_jump_slice = (uint32_t)s;
             out->jumps++;
@@ -973,11 +1028,11 @@ int oracle_run_eps(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntr
     return oracle_run_ch(P, seed, traj0, ntraj, gamma, eps, CH_DAMPING, nthreads, out);
 }
 
-/* channel: CH_DAMPING or CH_DEPHASING (S7) */
+/* channel: CH_DAMPING, CH_DEPHASING or CH_HEATING (S7) */
 int oracle_run_ch(const oproblem *P, uint64_t seed, uint64_t traj0, int32_t ntraj, const double *gamma,
                   double eps, int32_t channel, int32_t nthreads, otraj_out *out)
 {
-    if (channel != CH_DAMPING && channel != CH_DEPHASING) return OR_E_ARG;
+    if (channel != CH_DAMPING && channel != CH_DEPHASING && channel != CH_HEATING) return OR_E_ARG;
     int rc = check_problem(P);
     if (rc) return rc;
     osched *S = malloc(sizeof(osched));
@@ -1013,7 +1068,10 @@ int oracle_run_one(const oproblem *P, uint64_t seed, uint64_t traj, double gamma
     if (!S) return OR_E_OOM;
     if ((rc = build_schedule(P->n, P->k, S))) { free(S); return rc; }
     ostate st = { 0 };
-    if (H && H->channel != CH_DAMPING && H->channel != CH_DEPHASING) { free(S); return OR_E_ARG; }
+    if (H && H->channel != CH_DAMPING && H->channel != CH_DEPHASING && H->channel != CH_HEATING) {
+        free(S);
+        return OR_E_ARG;
+    }
     rc = run_traj(P, S, seed, traj, gamma, H ? H->eps : 0.0, H ? H->channel : CH_DAMPING, H, out, &st, NULL);
     free(S);
     if (rc) return rc;

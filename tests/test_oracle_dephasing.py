@@ -1,6 +1,8 @@
-"""Oracle pins for the dephasing channel (the diagonal channel named in the
-outlook, Sec. VII), taken as phase damping with the no-jump operator of
-Eq. (5): its single-layer exactness is pinned in test_oracle_joint.py; here
+"""Oracle pins for the other diagonal channels of the outlook (Sec. VII).
+Dephasing is taken as phase damping with the no-jump operator of Eq. (5),
+heating as the no-jump operator diag(a, 1, 1) on the ground level with jumps
+to the excited levels: their single-layer exactness is pinned in
+test_oracle_joint.py; here
 the trajectory average of the fidelity matches the density-matrix oracle
 applying the fixed Kraus matrices (qubit n = 2 with the Tab. IV memory,
 qutrit n = 1), jump-free trajectories keep the closed-form fidelity of the
@@ -70,3 +72,22 @@ def test_dephasing_jump_keeps_the_configuration():
     _, da = core.run_one(p, 9, 0, 0.3, hist, channel=core.DAMPING)
     assert len(dd.configs) > 0 and all(any(q == site for q, _ in cfg) for cfg in dd.configs)
     assert len(da.configs) > 0 and all(all(q != site for q, _ in cfg) for cfg in da.configs)
+
+
+@pytest.mark.parametrize("enc,n,gamma,seed", [(W.QUBIT, 2, 0.01, 61), (W.QUBIT, 2, 0.03, 62), (W.QUTRIT, 1, 0.02, 63),
+                                               (W.QUTRIT, 1, 0.08, 64)])
+def test_heating_matches_density_matrix(enc, n, gamma, seed):
+    """Heating excites idle sites of every branch: the trajectory mean of the
+    fidelity matches the density-matrix oracle (qubit n=2 with the Tab. IV
+    memory, qutrit n=1)."""
+    p = W.data_loading(enc, n, 1, seed=seed)
+    if enc == W.QUBIT:
+        p.memory = np.array([0, 1, 1, 0], np.uint8)
+    want, tr, _ = dm.simulate(enc, n, 1, p.memory, gamma, channel="heating")
+    assert abs(tr - 1.0) < 1e-12
+    N = 20000
+    r = core.run(p, 900 + seed, 0, np.full(N, gamma), channel=core.HEATING)
+    assert np.all(r["status"] == 0)
+    m, se = _mean_se(r["fidelity"])
+    assert abs(m - want) < 5 * se + 1e-3, (m, se, want)
+    assert want < 0.99                                   # the channel does act

@@ -12,6 +12,12 @@ from oracle import core
 
 def _kraus(qubit, gamma, channel=core.DAMPING):
     a, s = math.sqrt(1 - gamma), math.sqrt(gamma)
+    if channel == core.HEATING:                # diagonal no-jump operator on the ground level
+        if qubit:
+            return [np.diag([a, 1]), np.array([[0, 0], [s, 0]])]
+        h = math.sqrt(gamma / 2)
+        return [np.diag([a, 1, 1]), np.array([[0, 0, 0], [h, 0, 0], [0, 0, 0]]),
+                np.array([[0, 0, 0], [0, 0, 0], [h, 0, 0]])]
     if channel == core.DEPHASING:              # phase damping: same no-jump operator, diagonal jumps
         if qubit:
             return [np.diag([1, a]), np.diag([0, s])]
@@ -105,4 +111,61 @@ def test_theorem3_single_layer(qubit, seed, channel):
             v = _vec(out, sites, base, nlab)
             assert np.linalg.norm(v) == pytest.approx(1.0, abs=1e-12)
             got += pc * pj * np.outer(v, v.conj())
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
+def _interval_mids_heat(comps, cand, levels):
+    """Heating: the masks are the candidate sites a component holds at the
+    ground level, with the candidates' target levels."""
+    W = sum(abs(c[3]) ** 2 for c in comps)
+    groups = {}
+    for addr, bus, cfg, amp in comps:
+        lv = dict(cfg)
+        J = tuple((q, levels[q]) for q in sorted(cand) if lv.get(q, 0) == 0)
+        groups[J] = groups.get(J, 0.0) + abs(amp) ** 2
+    mids, cum = [], 0.0
+    for J in sorted(groups):
+        w = groups[J]
+        if w > 0:
+            mids.append((J, (cum + w / 2) / W, w / W))
+        cum += w
+    return mids
+
+
+@pytest.mark.parametrize("qubit", [True, False])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_theorem3_single_layer_heating(qubit, seed):
+    """The joint sampler with masks over the ground sites reproduces the
+    heating channel (diagonal no-jump operator on the ground level, jumps to
+    the excited levels; qutrit target level drawn per candidate) exactly,
+    averaged over candidates, target levels and the auxiliary draw."""
+    rng = np.random.default_rng(10 + seed)
+    base = 2 if qubit else 3
+    sites = [1, 4, 5]
+    nlab = 3
+    gamma = 0.31
+    d = {}
+    for lab in range(nlab):
+        for _ in range(3):
+            cfg = tuple((q, int(rng.integers(1, base))) for q in sites if rng.random() < 0.5)
+            d[(lab, cfg)] = d.get((lab, cfg), 0) + complex(rng.normal(), rng.normal())
+    comps = [(k[0], 0, k[1], v) for k, v in d.items()]
+    nrm = math.sqrt(sum(abs(c[3]) ** 2 for c in comps))
+    comps = [(a, b, c, v / nrm) for a, b, c, v in comps]
+    psi = _vec(comps, sites, base, nlab)
+    rho_in = np.outer(psi, psi.conj())
+    want = _channel(rho_in, sites, base, nlab, _kraus(qubit, gamma, core.HEATING))
+    got = np.zeros_like(rho_in)
+    for mask in itertools.product([0, 1], repeat=len(sites)):
+        cand = [q for q, m in zip(sites, mask) if m]
+        pc = gamma ** len(cand) * (1 - gamma) ** (len(sites) - len(cand))
+        for tl in itertools.product([1] if qubit else [1, 2], repeat=len(cand)):
+            levels = dict(zip(cand, tl))
+            pt = 1.0 if qubit else 0.5 ** len(cand)
+            for J, u, pj in _interval_mids_heat(comps, set(cand), levels):
+                out, Jo = core.joint_layer(comps, cand, gamma, u, core.HEATING, levels)
+                assert Jo == J
+                v = _vec(out, sites, base, nlab)
+                assert np.linalg.norm(v) == pytest.approx(1.0, abs=1e-12)
+                got += pc * pt * pj * np.outer(v, v.conj())
     assert np.max(np.abs(got - want)) < 1e-13
