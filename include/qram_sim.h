@@ -66,7 +66,7 @@ enum { QRAM_QUTRIT = 0, QRAM_QUBIT = 1 };
 
 /* Noise channel of the layer that follows every slice's gates (see
  * qram_set_channel). */
-enum { QRAM_CHANNEL_DAMPING = 0, QRAM_CHANNEL_DEPHASING = 1 };
+enum { QRAM_CHANNEL_DAMPING = 0, QRAM_CHANNEL_DEPHASING = 1, QRAM_CHANNEL_HEATING = 2 };
 
 /* One QRAM query problem (Sec. II.A; input class of Sec. IV.D: a coherent
  * superposition over addresses with one bus column per address). */
@@ -280,8 +280,18 @@ int qram_set_depolarizing(qram_sim_t *sim, double eps, int eps_equals_gamma);
  * K_J^dagger K_J is the damping one, so the candidate sampling, the marking,
  * the joint draw of Sec. IV.D and the good-branch closed forms (Prop. 1,
  * Theorem 2) are unchanged; a fired jump projects onto the components that
- * hold its sites excited and leaves their configuration as it is.  Applies
- * to both modes and to qram_dump_state; QRAM_E_ARG for another value. */
+ * hold its sites excited and leaves their configuration as it is.
+ * QRAM_CHANNEL_HEATING is the outlook's heating channel: the diagonal
+ * no-jump operator K0 = diag(a, 1, 1) on {W, L, R} (qubit diag(a, 1)) with
+ * the jumps sqrt(gamma/2)|L><W| and sqrt(gamma/2)|R><W| (qubit
+ * sqrt(gamma)|1><0|).  The joint draw runs over the candidate sites a
+ * component holds at the ground level, each with a target level drawn with
+ * the candidate (qutrit: bit 0 of word 0 of counter (site, slice | 6 << 24,
+ * traj_lo, traj_hi); 0 -> L, 1 -> R); a fired J raises its sites.  Heating
+ * jumps reach idle sites of every branch, so with heating both modes evolve
+ * every branch (as with depolarizing faults, which cannot be combined with
+ * it: QRAM_E_STATE).  Applies to both modes and to qram_dump_state;
+ * QRAM_E_ARG for another value. */
 int qram_set_channel(qram_sim_t *sim, int channel);
 
 /* Low-weight truncation of the predicted good branches in qram_dump_state

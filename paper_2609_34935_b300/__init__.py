@@ -265,9 +265,12 @@ class QramSim:
                "qram_set_depolarizing")
 
     def set_channel(self, channel: str):
-        """The per-slice channel: "damping" (amplitude damping, the default)
-        or "dephasing" (phase damping with the same no-jump operator)."""
-        _check(self.lib.qram_set_channel(self.h, {"damping": 0, "dephasing": 1}[channel]), "qram_set_channel")
+        """The per-slice channel: "damping" (amplitude damping, the default),
+        "dephasing" (phase damping with the same no-jump operator) or
+        "heating" (diagonal no-jump operator on the ground level, jumps to the
+        excited levels; every branch explicit)."""
+        _check(self.lib.qram_set_channel(self.h, {"damping": 0, "dephasing": 1, "heating": 2}[channel]),
+               "qram_set_channel")
 
     def set_gamma_bound(self, gmax: float):
         _check(self.lib.qram_set_gamma_bound(self.h, gmax), "qram_set_gamma_bound")

@@ -894,13 +894,16 @@ uint64_t qram_launch_count(const qram_sim_t *S) { return S ? S->launches : 0; }
 
 int qram_set_depolarizing(qram_sim_t *S, double eps, int eps_equals_gamma) {
     if (!S || !(eps >= 0.0 && eps < 1.0)) return QRAM_E_ARG;
+    if (S->channel == QRAM_CHANNEL_HEATING && (eps > 0.0 || eps_equals_gamma)) return QRAM_E_STATE;
     S->eps = eps;
     S->eps_gamma = eps_equals_gamma ? 1 : 0;
     return QRAM_OK;
 }
 
 int qram_set_channel(qram_sim_t *S, int channel) {
-    if (!S || (channel != QRAM_CHANNEL_DAMPING && channel != QRAM_CHANNEL_DEPHASING)) return QRAM_E_ARG;
+    if (!S || (channel != QRAM_CHANNEL_DAMPING && channel != QRAM_CHANNEL_DEPHASING && channel != QRAM_CHANNEL_HEATING))
+        return QRAM_E_ARG;
+    if (channel == QRAM_CHANNEL_HEATING && (S->eps > 0.0 || S->eps_gamma)) return QRAM_E_STATE;
     S->channel = channel;
     return QRAM_OK;
 }

@@ -1077,6 +1077,81 @@ __device__ __noinline__ CompR pauli_site(CompR c, uint16_t *xs, const Ctx C, uin
     return c;
 }
 
+// ---- heating (the outlook's diagonal heating channel) --------------------
+// Jumps raise ground sites: the mask J(x) is the candidate sites that x
+// holds at the ground level, each with its candidate's target level (qubit:
+// the excited level; qutrit: L or R, tgt[c] = 1 or 2 for candidate c).  Codes
+// as for damping, site << 1 | isR; the slice's candidates cand[c0 .. c1)
+// are in site order, so the first ground candidate is the first element.
+__device__ __forceinline__ uint32_t heat_code(const Ctx &C, uint32_t site, const uint32_t *tgt, uint32_t q) {
+    return (site << 1) | ((C.enc == QRAM_QUTRIT && tgt[q] == 2u) ? 1u : 0u);
+}
+
+__device__ uint32_t mask_first_heat(const CompR &c, const uint16_t *xs, const Ctx &C, const uint32_t *cand,
+                                    const uint32_t *tgt, uint32_t c0, uint32_t c1, uint32_t &cnt) {
+    const uint32_t iB = b_addr(c, C);
+    uint32_t first = 0xFFFFFFFFu;
+    cnt = 0;
+    for (uint32_t q = c0; q < c1; ++q) {
+        const uint32_t site = cand[q] & 0xFFFFu;
+        int b;
+        if (locate(c, xs, C, iB, site, b) >= 0) continue;          // excited: K0 there is 1, no jump
+        if (first == 0xFFFFFFFFu) first = heat_code(C, site, tgt, q);
+        ++cnt;
+    }
+    return first;
+}
+
+// the heating mask starts with pref[0 .. np): next element, -1 if equal, -2 if not
+__device__ long long mask_query_heat(const CompR &c, const uint16_t *xs, const Ctx &C, const uint32_t *cand,
+                                     const uint32_t *tgt, uint32_t c0, uint32_t c1, const uint32_t *pref, int np) {
+    const uint32_t iB = b_addr(c, C);
+    int got = 0;
+    for (uint32_t q = c0; q < c1; ++q) {
+        const uint32_t site = cand[q] & 0xFFFFu;
+        int b;
+        if (locate(c, xs, C, iB, site, b) >= 0) continue;
+        const uint32_t code = heat_code(C, site, tgt, q);
+        if (got < np) {
+            if (code != pref[got]) return -2;
+            ++got;
+            continue;
+        }
+        return (long long)code;
+    }
+    return got == np ? -1 : -2;
+}
+
+// K_J of heating: every site of J at the ground level (else the component
+// is annihilated), raised to its target level.  By value; *okp = 0 if a
+// capacity was exceeded.
+__device__ __noinline__ CompR heat_apply(CompR c, uint16_t *xs, const Ctx C, const uint32_t *J, int nJ, bool *alive,
+                                        int *okp) {
+    *okp = 1;
+    const uint32_t iB = b_addr(c, C);
+    for (int j = 0; j < nJ; ++j) {
+        int b;
+        if (locate(c, xs, C, iB, J[j] >> 1, b) >= 0) { *alive = false; return c; }
+    }
+    *alive = true;
+    for (int j = 0; j < nJ; ++j) {
+        const uint32_t site = J[j] >> 1;
+        const int lvl = (C.enc == QRAM_QUTRIT && (J[j] & 1u)) ? 2 : 1;
+        const uint32_t u = site >> 1;
+        const int L = layer_of(u);
+        if (L < C.n && u == path_node(C.i, C.n, L)) {
+            const int bb = 2 * L + (int)(site & 1u);
+            c.pw |= 1u << bb;
+            if (lvl == 2) c.pwR |= 1u << bb;
+            continue;
+        }
+        Ents E;
+        to_ents(c, xs, C, E);
+        if (!ent_set(E, site, lvl) || !from_ents(c, xs, C, E)) { *okp = 0; return c; }
+    }
+    return c;
+}
+
 // FNV-1a over the sorted (site << 2 | level) list; 0 for the ground state
 __device__ __noinline__ uint64_t config_hash(const CompR c, const uint16_t *xs, const Ctx C) {
     if (is_ground(c)) return 0;
@@ -1409,6 +1484,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     // depolarizing fault events (their own stream; every branch explicit)
     const double eps = P.eps_gamma ? gamma : P.eps;
     const bool depol = DEPOL && valid && eps > 0.0 && eps < 1.0;
+    // heating: every branch explicit (its jumps raise idle sites of every branch)
+    const bool heat = P.channel == QRAM_CHANNEL_HEATING;
     uint32_t *pev = scr.pev + slot * scr.cand_cap;
     uint32_t npev = 0;
     if (depol) {
@@ -1422,8 +1499,13 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     for (uint32_t c = threadIdx.x; c < ncand; c += NT) {
         const uint32_t s = cand[c] >> 16, q = cand[c] & 0xFFFFu;
         const int L = layer_of(q >> 1);
-        if (depol || ((P.occ2[s] >> (2 * L + (int)(q & 1u))) & 1u))   // a noiseless orbit can hold it excited
+        if (depol || heat || ((P.occ2[s] >> (2 * L + (int)(q & 1u))) & 1u))   // a noiseless orbit can hold it excited
             atomicOr(&S.syncmask[s >> 5], 1u << (s & 31u));
+        if (heat && P.enc == QRAM_QUTRIT) {               // target level of each heating candidate (stream 6)
+            uint32_t w0 = q, w1 = s | (6u << 24), w2 = (uint32_t)traj, w3 = (uint32_t)(traj >> 32);
+            philox(w0, w1, w2, w3, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+            pev[c] = (w0 & 1u) ? 2u : 1u;
+        }
     }
     for (int s = threadIdx.x; s <= T; s += NT) {
         uint32_t lo = 0, hi = ncand;
@@ -1491,12 +1573,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     // pruned mode keeps every branch implicit until a jump fires (the state
     // dump takes the same form: a jump-free trajectory is emitted from the
     // closed forms of every branch, a jumped one from its explicit survivors)
-    const bool lazy = P.mode == kPruned && P.orbit.ok && !depol;
+    const bool lazy = P.mode == kPruned && P.orbit.ok && !depol && !heat;
     // lazy epochs in product form: qubit input over every address, equal weights
     const bool factored = lazy && P.col_of != nullptr && P.w2u != nullptr && *P.w2u > 0.0;
 
     // ---- 3. explicit set ----------------------------------------------------
-    const double a = sqrt(1.0 - (valid ? gamma : 0.0));
+    // damping and dephasing: a = sqrt(1 - gamma) per excited site; heating:
+    // a per ground site, i.e. 1 / sqrt(1 - gamma) per excited site up to a
+    // factor common to every component
+    const double a = heat ? 1.0 / sqrt(1.0 - (valid ? gamma : 0.0)) : sqrt(1.0 - (valid ? gamma : 0.0));
     if (threadIdx.x < 128) {                        // a^j and a^(64 j) by binary powering
         const int j = (int)threadIdx.x & 63;
         double x = a, p = 1.0;
@@ -1545,7 +1630,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             bool take = false;
             if (b < (uint32_t)P.D) {
                 const uint32_t i = __ldg(P.addr + b);
-                take = P.mode == kFull || depol || ((S.badbits[i >> 5] >> (i & 31u)) & 1u) || (int)b == S.refcol;
+                take = P.mode == kFull || depol || heat || ((S.badbits[i >> 5] >> (i & 31u)) & 1u) || (int)b == S.refcol;
             }
             uint32_t tot;
             const uint32_t pre = block_scan_flag(take, &tot, S);
@@ -1569,7 +1654,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     // (multiplicity 2^mlog in every weight); at the epoch boundary forced at
     // slice 2n they are expanded into the 2^k configurations.
     // (k = 1: two configurations per branch; the forced epoch boundaries would cost more than merging saves)
-    const bool mergeable = qubit && P.k >= 2;
+    const bool mergeable = qubit && P.k >= 2 && !heat;
     int mlog = (mergeable && !lazy) ? kb : 0;
     // components created here: one per column (merged, or qutrit), or its 2^k wall configurations
     const int clog = (qubit && mlog == 0) ? kb : 0;
@@ -1924,7 +2009,12 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     // excited (a projection), and K0 then acts only on the
                     // excited sites outside J
                     int keep = 0;
-                    if (nJ > 0) {
+                    if (nJ > 0 && heat) {                   // raise the ground sites of J
+                        int okh;
+                        c = heat_apply(c, xs, C, S.J, nJ, &alive, &okh);
+                        if (!okh) capfail = true;
+                        keep = nJ;
+                    } else if (nJ > 0) {
                         alive = holds_all(c, xs, C, S.J, nJ);
                         if (alive && P.channel == QRAM_CHANNEL_DAMPING)
                             for (int j = 0; j < nJ; ++j) {
@@ -1966,7 +2056,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     if (etop >= 4096 || (uni && etop >= H)) capfail = true;   // exponent bound (packed in 12 bits)
                 }
                 if (!final_epoch) {
-                    c1 = mask_first(c, xs, C, S.candbits, S.cl2, mcnt);
+                    c1 = heat ? mask_first_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], mcnt)
+                              : mask_first(c, xs, C, S.candbits, S.cl2, mcnt);
                     if (!uni) {
                         const double ae = apow(S, c.e);
                         w = col_w2(P, lab) * k2m * ae * ae * (binc ? S.bw : 1.0);
@@ -2119,7 +2210,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         // good branches of the eager form: closed-form weights before the
         // first jump (Eq. (21))
         double wgs = 0.0, ogs = 0.0;
-        if (P.mode == kPruned && !jumped && !lazy && !depol) {
+        if (P.mode == kPruned && !jumped && !lazy && !depol && !heat) {
             const int sw = final_epoch ? T - 1 : s1 - 1;
             for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
                 const uint32_t i = __ldg(P.addr + b);
@@ -2163,7 +2254,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 if (P.dump_mode) {
                     P.dump.scal[0] = Wtot;
                     P.dump.scal[1] = jumped ? 1.0 : 0.0;
-                    P.dump.scal[2] = depol ? 1.0 : 0.0;           // every branch explicit: nothing to predict
+                    P.dump.scal[2] = (depol || heat) ? 1.0 : 0.0; // every branch explicit: nothing to predict
                     P.dump.scal[3] = lazy ? 1.0 : 0.0;            // no branch explicit before a jump
                 }
             }
@@ -2335,7 +2426,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         unpack(rv, qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
-                        if (mask_query(c, xs, C, S.candbits, pref, level) == -1) {
+                        if ((heat ? mask_query_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], pref, level) : mask_query(c, xs, C, S.candbits, pref, level)) == -1) {
                             const double ae = apow(S, c.e);
                             we += (uni ? w2u : col_w2(P, lab) * k2) * (double)(1u << mlog) * ae * ae *
                                   ((rv.w & kBinFlag) ? S.bw : 1.0);
@@ -2358,7 +2449,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         unpack(rv, qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
-                        const long long q = mask_query(c, xs, C, S.candbits, pref, level);
+                        const long long q = (heat ? mask_query_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], pref, level) : mask_query(c, xs, C, S.candbits, pref, level));
                         if (q >= 0 && (uint32_t)q <= cmid) {
                             const double ae = apow(S, c.e);
                             f += (uni ? w2u : col_w2(P, lab) * k2) * (double)(1u << mlog) * ae * ae *
@@ -2378,7 +2469,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                         unpack(scr.cs[cbase + r], qubit, c, lab, addr);
                         if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                         const Ctx C = make_ctx(P.enc, n, P.mem, addr);
-                        const long long q = mask_query(c, xs, C, S.candbits, pref, level);
+                        const long long q = (heat ? mask_query_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], pref, level) : mask_query(c, xs, C, S.candbits, pref, level));
                         if (q >= 0 && (best == 0xFFFFFFFFu || (uint32_t)q > best)) best = (uint32_t)q;
                     }
                     __shared__ uint32_t sbest;
@@ -2433,7 +2524,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             const uint32_t r = S.region;
             for (uint32_t c = S.slice_off[s1 + 1] + threadIdx.x; c < S.slice_off[T]; c += NT) {
                 const uint32_t u = (cand[c] & 0xFFFFu) >> 1, sc = cand[c] >> 16;
-                if (depol || tree_related(u, r)) atomicOr(&S.syncmask[4 + (sc >> 5)], 1u << (sc & 31u));
+                if (depol || heat || tree_related(u, r)) atomicOr(&S.syncmask[4 + (sc >> 5)], 1u << (sc & 31u));
             }
         }
         // clear the candidate bitmaps of s1 (the hit bitmap word by word: a
