@@ -156,7 +156,7 @@ void cand_caps(int n, int k, double gmax, int threads, uint32_t *cand_cap, uint3
 }
 
 struct Layout {
-    size_t o_cand, o_pev, o_seg, o_expl, o_cs, o_exc, o_selk, o_selw, total;
+    size_t o_cand, o_pev, o_seg, o_expl, o_cs, o_exc, o_selk, o_selw, o_pfr, total;
     uint32_t cc, sc, ecap, selseg;
 };
 
@@ -179,6 +179,8 @@ Layout scratch_layout(int enc, int n, int k, int D, size_t slots, double gmax, i
     L.selseg = (uint32_t)std::max(per_comp, per_branch);
     L.o_selk = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 4);
     L.o_selw = off; off = align_up(off + slots * (size_t)NWARP * L.selseg * 8);
+    // product-form records: qubit, k >= 2 (one per component, 8 words)
+    L.o_pfr = off; off = align_up(off + ((enc == QRAM_QUBIT && k >= 2) ? slots * (size_t)L.ecap * 32 : 0));
     L.total = off;
     return L;
 }
@@ -204,6 +206,7 @@ int ensure_scratch(qram_sim *S, double gmax) {
     S->scr.exc = (uint16_t *)(b + L.o_exc);
     S->scr.selk = (uint32_t *)(b + L.o_selk);
     S->scr.selw = (double *)(b + L.o_selw);
+    S->scr.pfr = (uint32_t *)(b + L.o_pfr);
     S->scr.selseg = L.selseg;
     S->scr.cand_cap = L.cc;
     S->scr.seg_cap = L.sc;
@@ -394,6 +397,7 @@ size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, int t
         scr->exc = (uint16_t *)(b + L.o_exc);
         scr->selk = (uint32_t *)(b + L.o_selk);
         scr->selw = (double *)(b + L.o_selw);
+        scr->pfr = (uint32_t *)(b + L.o_pfr);
         scr->selseg = L.selseg;
         scr->cand_cap = L.cc;
         scr->seg_cap = L.sc;

@@ -55,6 +55,7 @@ struct Scratch {
     uint16_t *exc;       // [slots][ecap][kXcap] off-path sites (site << 1 | isR)
     uint32_t *selk;      // [slots][nwarps][selseg] components with a non-empty mask: first code | size << 16
     double *selw;        // [slots][nwarps][selseg] their weights
+    uint32_t *pfr;       // [slots][ecap][8] product-form components: one record per data qubit
     uint32_t cand_cap, seg_cap, ecap, selseg;
 };
 

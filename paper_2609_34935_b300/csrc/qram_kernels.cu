@@ -167,6 +167,7 @@ struct Smem {
     uint64_t gq[kGapBits];         // fault stream: 64-bit fixed-point (1 - gamma)^(2^m)
     uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
     uint32_t wk[8];                // work of this trajectory (see Params::ctr)
+    uint32_t haspf, pfnext;        // components in product form exist (pfnext: written during a pass)
     double fprod2[kMaxT];          // product-form lazy weights: prod_l (1 + a^(2 ov_l(s))) per slice s
     double fprod1;                 // prod_l (1 + a^(ov_l(T-1))): the final overlap
     int16_t etab[4][16];           // lazy epochs: address exposure by nibble of the address
@@ -277,6 +278,9 @@ __device__ uint32_t block_scan_flag(bool f, uint32_t *tot, Smem<NT> &S) {
 // the component is a binomial group (bit 19, see kBinFlag), and for
 // equal-magnitude inputs the exponent e (12 bits), from which the descent
 // recomputes the weight w2u a^(2e) instead of the pass storing a double.
+// (kPFKey in place of e: the weight is in the FP64 list, as for every
+// entry of unequal magnitudes.)
+constexpr uint32_t kPFKey = 0xFFFu;
 __device__ __forceinline__ uint32_t sel_key(uint32_t c1, uint32_t mcnt, int e, bool bin) {
     return (c1 & 0xFFFFu) | (min(mcnt, 7u) << 16) | ((bin ? 1u : 0u) << 19) | ((uint32_t)e & 0xFFFu) << 20;
 }
@@ -905,8 +909,11 @@ __device__ __forceinline__ int excited_count(const CompR &c) {
 // prefix.  The order is ascending code, so J(x) starts with pref exactly when
 // it holds every code of pref and no other code below pref[np - 1]; the next
 // element is then the smallest code above it.  No ordered walk is needed.
+// xc[0..nxc): further codes of the mask (data qubits of a component in
+// product form), already known to be candidates.
 __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *xs, const Ctx &C,
-                                                const uint32_t *candbits, const uint32_t *pref, int np) {
+                                                const uint32_t *candbits, const uint32_t *pref, int np,
+                                                const uint32_t *xc = nullptr, int nxc = 0) {
     const uint32_t last = np > 0 ? pref[np - 1] : 0u;
     uint32_t next = 0xFFFFFFFFu;
     int got = 0;
@@ -938,6 +945,7 @@ __device__ __forceinline__ long long mask_query(const CompR &c, const uint16_t *
         const uint32_t site = xs[q] >> 1;
         if ((candbits[site >> 5] >> (site & 31u)) & 1u) take((uint32_t)xs[q]);
     }
+    for (int q = 0; q < nxc; ++q) take(xc[q]);
     if (bad || got != np) return -2;
     return next == 0xFFFFFFFFu ? -1 : (long long)next;
 }
@@ -1150,6 +1158,230 @@ __device__ __noinline__ CompR heat_apply(CompR c, uint16_t *xs, const Ctx C, con
         if (!ent_set(E, site, lvl) || !from_ents(c, xs, C, E)) { *okp = 0; return c; }
     }
     return c;
+}
+
+// ---- product form of the data qubits (qubit, damping) ---------------------
+// From the first Hadamard wall (before the gates of slice 2n+1) until the
+// last data qubit is back in the bus (slice 4n+2k-1), the 2^k wall
+// configurations c of a branch differ only in which data qubits are excited.
+// Every gate of those slices moves slot contents as the routers direct,
+// whatever the contents are (Sec. II.A; App. C), and the routers only change
+// when a data qubit would be swapped into one (or loaded into at d_0).  Until
+// then the configurations share the state of every other slot (the address
+// part, an ordinary component) and each data qubit t has one position, one
+// exposure m_t and one phase bit ph_t: configuration c is the address part
+// with data qubit t excited at its position when c_t = 1, exponent
+// e + sum_t c_t m_t and sign s + sum_t c_t ph_t (Lemma 1 for the exposures;
+// the wall sign (-1)^(j.c) starts ph = j).  One component (kPFFlag) then
+// stands for all 2^k configurations and its weight factorises,
+// a^(2e) prod_t (1 + a^(2 m_t)).  A jump on a data qubit's site keeps the
+// configurations with c_t = 1: its exposure and phase join e and s, and the
+// qubit (now ground) becomes part of the address part.  The address part
+// holds ground at every free data qubit's position, so a configuration adds
+// the excitations without collisions.  Records, one word per data qubit
+// (Scratch::pfr; 0 = fixed):
+//   bit 31 free | bit 23 ph | bits 16-22 m | bit 15 in the bus | bits 0-14 site, or bus slot
+constexpr uint32_t kPFFlag = 1u << 30;
+constexpr uint32_t kPFree = 1u << 31, kPBus = 1u << 15, kPPh = 1u << 23;
+
+__device__ __forceinline__ uint32_t pf_m(uint32_t w) { return (w >> 16) & 0x7Fu; }
+
+__device__ __forceinline__ void pf_load(const Scratch &scr, size_t g, uint32_t *rec) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(scr.pfr + g * 8);
+    const uint4 a = src[0], b = src[1];
+    rec[0] = a.x; rec[1] = a.y; rec[2] = a.z; rec[3] = a.w;
+    rec[4] = b.x; rec[5] = b.y; rec[6] = b.z; rec[7] = b.w;
+}
+__device__ __forceinline__ void pf_store(const Scratch &scr, size_t g, const uint32_t *rec) {
+    uint4 *dst = reinterpret_cast<uint4 *>(scr.pfr + g * 8);
+    dst[0] = make_uint4(rec[0], rec[1], rec[2], rec[3]);
+    dst[1] = make_uint4(rec[4], rec[5], rec[6], rec[7]);
+}
+
+// router value of node v in the address part
+__device__ __forceinline__ uint32_t pf_router(const CompR &c, const uint16_t *xs, const Ctx &C, uint32_t iB,
+                                              uint32_t v) {
+    int b;
+    return locate(c, xs, C, iB, 2u * v, b) >= 0 ? 1u : 0u;
+}
+
+// Moves the free data qubits through the gates of one slice, after the
+// address part went through them (the routers that a slice's controlled
+// swaps and fetch read are not changed by that slice: its gates act on
+// disjoint slots).  A data qubit at a leaf during a fetch takes the phase of
+// its cell.  damp: K0 of the slice follows (one more exposure in the tree).
+// Returns false when a data qubit would be loaded into d_0 or swapped into a
+// router (the configurations would part).
+__device__ __noinline__ bool pf_move(const SliceOps op, const CompR c, const uint16_t *xs, const Ctx C,
+                                     uint32_t *rec, int k, bool damp) {
+    const int n = C.n;
+    const uint32_t iB = b_addr(c, C);
+    for (int t = 0; t < k; ++t) {
+        uint32_t w = rec[t];
+        if (!(w & kPFree)) continue;
+        uint32_t pos = w & 0x7FFFu;
+        bool bus = (w & kPBus) != 0u, moved = false;
+        if (op.bus >= 0) {                                               // d_0 <-> bus slot
+            if (!bus && pos == 1u) { bus = true; pos = (uint32_t)op.bus; moved = true; }
+            else if (bus && pos == (uint32_t)op.bus) { bus = false; pos = 1u; moved = true; }
+        }
+        if (op.load >= 0 && !bus && pos == 1u) return false;
+        if (!bus && !moved) {
+            const uint32_t u = pos >> 1;
+            const int L = layer_of(u);
+            if ((op.iswap >> L) & 1u) return false;
+            if ((op.cswap >> L) & 1u) {                                  // down to the routed child
+                pos = 2u * (2u * u + 1u + pf_router(c, xs, C, iB, u)) + 1u;
+            } else if (L > 0 && ((op.cswap >> (L - 1)) & 1u)) {          // up, if the parent routes here
+                const uint32_t p = (u - 1u) >> 1;
+                if (2u * p + 1u + pf_router(c, xs, C, iB, p) == u) pos = 2u * p + 1u;
+            } else if (op.fetch >= 0 && L == n - 1) {
+                const uint32_t cell = 2u * (u - ((1u << (n - 1)) - 1u)) + pf_router(c, xs, C, iB, u);
+                if ((__ldg(C.mem + cell) >> op.fetch) & 1u) w ^= kPPh;
+            }
+        }
+        const uint32_t m = pf_m(w) + ((damp && !bus) ? 1u : 0u);
+        rec[t] = kPFree | (w & kPPh) | (m << 16) | (bus ? kPBus : 0u) | pos;
+    }
+    return true;
+}
+
+// K_J on a component in product form (damping), then K0 on the excited
+// sites outside J: a site of J held by a free data qubit fixes that qubit
+// (c_t = 1; its exposure and phase join e and s); every other site of J must
+// be held by the address part (else no configuration survives: *alive =
+// false) and is cleared there.  By value; *okp = 0 if a capacity was exceeded.
+__device__ __noinline__ CompR pf_jump(CompR c, uint16_t *xs, const Ctx C, uint32_t *rec, int k, const uint32_t *J,
+                                     int nJ, bool *alive, int *okp) {
+    *okp = 1;
+    *alive = true;
+    uint64_t dat = 0;                  // elements of J held by data qubits
+    for (int j = 0; j < nJ; ++j) {
+        const uint32_t site = J[j] >> 1;
+        for (int t = 0; t < k; ++t) {
+            const uint32_t w = rec[t];
+            if ((w & kPFree) && !(w & kPBus) && (w & 0x7FFFu) == site) {
+                c.e += (int)pf_m(w);
+                c.sign ^= (w & kPPh) ? 1u : 0u;
+                rec[t] = 0u;
+                dat |= 1ull << j;
+            }
+        }
+    }
+    const uint32_t iB = b_addr(c, C);
+    for (int j = 0; j < nJ; ++j) {
+        int b;
+        if (!((dat >> j) & 1ull) && locate(c, xs, C, iB, J[j] >> 1, b) < 0) { *alive = false; return c; }
+    }
+    for (int j = 0; j < nJ; ++j) {
+        if ((dat >> j) & 1ull) continue;
+        int okc;
+        c = clear_site(c, xs, C, J[j] >> 1, &okc);
+        if (!okc) *okp = 0;
+    }
+    c.e += excited_count(c);
+    for (int t = 0; t < k; ++t) {
+        const uint32_t w = rec[t];
+        if ((w & kPFree) && !(w & kPBus)) rec[t] = w + (1u << 16);
+    }
+    return c;
+}
+
+// Configuration cw (bit t: c_t) of a component in product form as an
+// explicit component (its free data qubits only; fixed ones have c_t = 1 in
+// e and s already).  False if the off-path list would overflow.
+__device__ __noinline__ CompR pf_config(CompR c, uint16_t *xs, const Ctx C, const uint32_t *rec, int k, uint32_t cw,
+                                       int *okp) {
+    *okp = 1;
+    for (int t = 0; t < k; ++t) {
+        const uint32_t w = rec[t];
+        if (!(w & kPFree) || !((cw >> t) & 1u)) continue;
+        c.e += (int)pf_m(w);
+        c.sign ^= (w & kPPh) ? 1u : 0u;
+        if (w & kPBus) { c.cb |= 1u << (w & 7u); continue; }
+        const uint32_t site = w & 0x7FFFu, u = site >> 1;
+        const int L = layer_of(u);
+        if (u == path_node(C.i, C.n, L)) { c.pw |= 1u << (2 * L + 1); continue; }
+        Ents E;
+        to_ents(c, xs, C, E);
+        if (!ent_set(E, site, 1) || !from_ents(c, xs, C, E)) { *okp = 0; return c; }
+    }
+    return c;
+}
+
+// The masks of a component in product form: the address part's mask plus
+// the sites of the free data qubits with c_t = 1 that hold a candidate
+// (T_C, at most k).  For a subset S of T_C the configurations with c = S on
+// T_C have weight base * prod_{t in S} f_t, base = a^(2e) prod over the free
+// data qubits outside T_C of (1 + a^(2 m_t)), f_t = a^(2 m_t).
+struct PFMasks {
+    double base;
+    uint32_t ntc;
+    uint32_t code[kMaxK];
+    double f[kMaxK];
+};
+
+__device__ __forceinline__ void pf_masks(const uint32_t *rec, int k, int e, const uint32_t *candbits,
+                                         const double *powlo, const double *powhi, PFMasks &M) {
+    auto ap = [&](int x) { return powlo[x & 63] * powhi[(x >> 6) & 63]; };
+    const double ae = ap(e);
+    M.base = ae * ae;
+    M.ntc = 0;
+    for (int t = 0; t < k; ++t) {
+        const uint32_t w = rec[t];
+        if (!(w & kPFree)) continue;
+        const double am = ap((int)pf_m(w)), f = am * am;
+        const uint32_t site = w & 0x7FFFu;
+        if (!(w & kPBus) && ((candbits[site >> 5] >> (site & 31u)) & 1u)) {
+            M.code[M.ntc] = site << 1;
+            M.f[M.ntc] = f;
+            ++M.ntc;
+        } else {
+            M.base *= 1.0 + f;
+        }
+    }
+}
+
+// the largest exponent of a component's configurations (product form: every free data qubit excited)
+__device__ __forceinline__ int pf_etop(const uint32_t *rec, int k, int e) {
+    for (int t = 0; t < k; ++t)
+        if (rec[t] & kPFree) e += (int)pf_m(rec[t]);
+    return e;
+}
+
+// Appends this thread's entries to its warp's selection segment: nent of
+// them.  Without pm the one entry of an ordinary component or binomial
+// group (first code c1, size mcnt, key exponent ke, FP64 weight w when
+// wlist); with pm one per non-empty mask of a component in product form
+// (subset S of T_C in increasing order, skipping the empty subset when the
+// address part's mask is empty), weight wf * base * prod_{t in S} f_t in the
+// FP64 list.  Entries past the segment set capfail.  Warp-uniform call.
+__device__ __forceinline__ void put_entries(uint32_t nent, const PFMasks *pm, uint32_t c1, uint32_t mcnt, int ke,
+                                            bool bin, double w, bool wlist, double wf, uint32_t *selk, double *selw,
+                                            uint32_t selseg, uint32_t &wcur, uint32_t lane, bool &capfail) {
+    const uint32_t mx = __reduce_max_sync(0xFFFFFFFFu, nent);
+    for (uint32_t q = 0; q < mx; ++q) {
+        const bool ne = q < nent;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ne);
+        if (ne) {
+            const uint32_t pos = wcur + __popc(bal & ((1u << lane) - 1u));
+            if (pos >= selseg) {
+                capfail = true;
+            } else if (!pm) {
+                selk[pos] = sel_key(c1, mcnt, ke, bin);
+                if (wlist) selw[pos] = w;
+            } else {
+                const uint32_t sb = q + (mcnt == 0 ? 1u : 0u);
+                uint32_t first = c1, cnt = mcnt;
+                double wt = wf * pm->base;
+                for (uint32_t i = 0; i < pm->ntc; ++i)
+                    if ((sb >> i) & 1u) { first = min(first, pm->code[i]); ++cnt; wt *= pm->f[i]; }
+                selk[pos] = sel_key(first, cnt, (int)kPFKey, false);
+                selw[pos] = wt;
+            }
+        }
+        wcur += __popc(bal);
+    }
 }
 
 // FNV-1a over the sorted (site << 2 | level) list; 0 for the ground state
@@ -1703,7 +1935,158 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
     const int sU = 4 * n + 2 * P.k - 1;
     const bool binok = mergeable && !depol;
     const uint32_t kmask = (1u << P.k) - 1u;
+    // product form of the data qubits from the first wall to sU (damping).
+    // After a jump, an epoch boundary before each router swap of the unload
+    // in that window lets the components whose data qubit would enter a
+    // router go explicit first.  (Before a jump every component is on its
+    // noiseless orbit, where no data qubit meets a router swap; and before
+    // the first fetch, 3n+1, no data qubit can be off its schedule: going
+    // down it moves one layer per slice whatever the routers say.)
+    const bool pfok = binok && P.channel == QRAM_CHANNEL_DAMPING;
+    auto pfchk = [&](int s) { return s > 3 * n + 1 && s <= sU && P.ops[s].iswap != 0u; };
+    if (threadIdx.x == 0) S.haspf = 0u;
     for (;;) {
+        if (mlog > 0 && s_prev >= 2 * n && pfok) {
+            // each merged component becomes one in product form: every data
+            // qubit free in its own bus slot, no exposure, phase bit j_t
+            // (first wall)
+            const uint32_t nc = S.ncomp;
+            for (uint32_t r = threadIdx.x; r < nc; r += NT) {
+                uint4 v = scr.cs[cbase + r];
+                const uint32_t j = __ldg(P.bus + (v.w & 0x3FFFu));
+                uint32_t rec[8];
+                for (int t = 0; t < 8; ++t)
+                    rec[t] = t < P.k ? (kPFree | (((j >> t) & 1u) ? kPPh : 0u) | kPBus | (uint32_t)t) : 0u;
+                v.w |= kPFFlag;
+                scr.cs[cbase + r] = v;
+                pf_store(scr, cbase + r, rec);
+            }
+            if (threadIdx.x == 0) S.haspf = nc > 0 ? 1u : 0u;
+            mlog = 0;
+            __syncthreads();
+        }
+        if (pfok && S.haspf && (s_prev == sU || (jumped && pfchk(s_prev + 1)))) {
+            // At sU each component in product form becomes a binomial group
+            // (every data qubit free, in its own bus slot, exposed for its
+            // whole window: the group's exponents e + 2n|c| and signs
+            // s + c.ph) or its explicit configurations; before a router swap
+            // of the unload, the components with a free data qubit in a data
+            // slot of a swapped layer go explicit.  1: output counts and
+            // offsets (in the selection list area, free here); 2: top-down
+            // chunks (outputs of component r start at offset >= r).
+            const bool atU = s_prev == sU;
+            const uint32_t isw = atU ? 0u : P.ops[s_prev + 1].iswap;
+            const uint32_t nc = S.ncomp;
+            uint32_t *offs = scr.selk + slot * NW * (size_t)scr.selseg;
+            auto action = [&](const uint32_t *rec) {     // 0 keep, 1 binomial group, 2 explicit
+                bool group = atU, risk = false;
+                for (int t = 0; t < P.k; ++t) {
+                    const uint32_t w = rec[t];
+                    group = group && (w & kPFree) && (w & kPBus) && pf_m(w) == 2u * n;
+                    if ((w & kPFree) && !(w & kPBus) && ((isw >> layer_of((w & 0x7FFFu) >> 1)) & 1u)) risk = true;
+                }
+                return atU ? (group ? 1 : 2) : (risk ? 2 : 0);
+            };
+            auto nfree = [&](const uint32_t *rec) {
+                int f = 0;
+                for (int t = 0; t < P.k; ++t) f += (rec[t] & kPFree) ? 1 : 0;
+                return f;
+            };
+            uint32_t base = 0;
+            for (uint32_t r0 = 0; r0 < nc; r0 += NT) {
+                const uint32_t r = r0 + threadIdx.x;
+                uint32_t cnt = 0;
+                if (r < nc) {
+                    cnt = 1;
+                    if (scr.cs[cbase + r].w & kPFFlag) {
+                        uint32_t rec[8];
+                        pf_load(scr, cbase + r, rec);
+                        if (action(rec) == 2) cnt = 1u << nfree(rec);
+                    }
+                }
+                uint32_t tot;
+                const uint32_t pre = block_scan_count(cnt, &tot, S);
+                if (r < nc) offs[r] = base + pre;
+                base += tot;
+            }
+            bool capf = false, kept = false;
+            if (base <= scr.ecap) {
+                for (int r0 = ((int)nc - 1) / NT * NT; r0 >= 0; r0 -= NT) {
+                    const uint32_t r = (uint32_t)r0 + threadIdx.x;
+                    const bool have = r < nc;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    alignas(16) uint16_t xs[kXcap];
+                    uint32_t rec[8], o = 0;
+                    int act = 0;
+                    if (have) {
+                        v = scr.cs[cbase + r];
+                        const uint32_t nx = (v.z >> 21) & 0x3Fu;
+                        if (nx) load_exc(scr, cbase + r, nx, xs);
+                        if (v.w & kPFFlag) { pf_load(scr, cbase + r, rec); act = action(rec); }
+                        o = offs[r];
+                    }
+                    __syncthreads();
+                    if (have) {
+                        const size_t g = cbase + o;
+                        const uint32_t nx = (v.z >> 21) & 0x3Fu;
+                        if (act == 0) {
+                            if (o != r) {
+                                scr.cs[g] = v;
+                                uint4 *dst = reinterpret_cast<uint4 *>(scr.exc + g * kXcap);
+                                const uint4 *src = reinterpret_cast<const uint4 *>(xs);
+                                for (uint32_t q = 0; q < (nx + 7u) / 8u; ++q) dst[q] = src[q];
+                                if (v.w & kPFFlag) pf_store(scr, g, rec);
+                            }
+                            if (v.w & kPFFlag) kept = true;
+                        } else if (act == 1) {
+                            uint32_t phi = 0;
+                            // phi by bus slot: the group's bus word is c permuted to the slots
+                            for (int t = 0; t < P.k; ++t) phi |= ((rec[t] & kPPh) ? 1u : 0u) << (rec[t] & 7u);
+                            CompR c; uint32_t lab, addr;
+                            unpack(v, qubit, c, lab, addr);
+                            uint4 g4;
+                            g4.x = v.x; g4.y = v.y;
+                            g4.z = ((uint32_t)c.e & 0xFFFu) | (phi << 12) | ((c.sign & 1u) << 20) | (v.z & (0x3FFu << 21));
+                            g4.w = (v.w & 0x0FFFFFFFu) | kBinFlag;
+                            scr.cs[g] = g4;
+                            if (o != r) {
+                                uint4 *dst = reinterpret_cast<uint4 *>(scr.exc + g * kXcap);
+                                const uint4 *src = reinterpret_cast<const uint4 *>(xs);
+                                for (uint32_t q = 0; q < (nx + 7u) / 8u; ++q) dst[q] = src[q];
+                            }
+                        } else {
+                            CompR c; uint32_t lab, addr;
+                            unpack(v, qubit, c, lab, addr);
+                            const Ctx C = make_ctx(P.enc, n, P.mem, addr);
+                            uint32_t fm = 0;
+                            for (int t = 0; t < P.k; ++t) fm |= ((rec[t] & kPFree) ? 1u : 0u) << t;
+                            // configurations over the free data qubits, in increasing order
+                            uint32_t q = 0, cw = 0;
+                            do {
+                                alignas(16) uint16_t xd[kXcap];
+                                for (uint32_t x = 0; x < nx; ++x) xd[x] = xs[x];
+                                int okc;
+                                const CompR d = pf_config(c, xd, C, rec, P.k, cw, &okc);
+                                if (!okc) capf = true;
+                                store_comp(scr, g + q, d, xd, qubit, lab, addr);
+                                ++q;
+                                cw = (cw - fm) & fm;
+                            } while (cw != 0u);
+                        }
+                    }
+                    __syncthreads();
+                }
+            } else {
+                capf = true;
+            }
+            const bool anyk = __syncthreads_or(kept);
+            if (__syncthreads_or(capf) && threadIdx.x == 0) S.status = QRAM_E_CAP;
+            if (threadIdx.x == 0) {
+                if (base <= scr.ecap) S.ncomp = base;
+                S.haspf = anyk ? 1u : 0u;
+            }
+            __syncthreads();
+        }
         if (mlog > 0 && s_prev >= 2 * n) {
             // expand the merged components into the 2^k wall configurations
             // (the pending K_J of slice s_prev acts on each in the pass below).
@@ -1736,7 +2119,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             mlog = 0;
             __syncthreads();
         }
-        if (binok && mlog == 0 && s_prev == sU && (!lazy || jumped)) {
+        // (with the product form every explicit configuration at sU comes
+        // from a component that could not be a group: nothing to merge)
+        if (binok && !pfok && mlog == 0 && s_prev == sU && (!lazy || jumped)) {
             // merge each branch's 2^k wall configurations into a binomial
             // group where they qualify (see kBinFlag).  A branch's
             // configurations are consecutive components.  1: the first slot
@@ -1832,12 +2217,16 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             if (mlog > 0 && s1 > 2 * n) s1 = 2 * n;          // merged components end an epoch at 2n
             // explicit configurations end an epoch at sU, where they merge into binomial groups
             if (binok && mlog == 0 && (!lazy || jumped) && s_prev < sU && s1 > sU) s1 = sU;
+            if (pfok && S.haspf && jumped)                    // before a router swap of the unload
+                for (int s = s_prev + 2; s <= s1 && s <= sU; ++s)
+                    if (pfchk(s)) { s1 = s - 1; break; }
         }
         const bool final_epoch = s1 >= T;
         const uint32_t mc = 1u << mlog;                    // configurations per component
         const double k2m = k2 * (double)mc;
         if (threadIdx.x == 0) {
             S.cl2 = 0;
+            S.pfnext = 0u;
             // data factors after damping slices 1..sw (tabulated per trajectory)
             const int sw = final_epoch ? T - 1 : s1 - 1;
             const double dn = qubit ? S.fdn[sw] : 1.0;
@@ -1998,13 +2387,23 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             double w = 0.0;
             uint32_t hkey = 0xFFFFFFFFu;   // histogram key: e << 3 | ground (final) or non-empty mask << 2 | overlap sign + 1
             const bool binc = alive && (cur.w & kBinFlag);   // binomial group (kBinFlag)
+            const bool pfc = alive && (cur.w & kPFFlag);     // product form (kPFFlag)
+            uint32_t rec[8];
+            PFMasks pm;
+            uint32_t nent = 0;             // selection entries of this component
+            double pwf = 0.0;              // product form: weight factor of its entries
             int binm = 0;                  // final epoch, binomial group: |phi ^ b_out|
             Ctx C;
             if (alive) {
                 unpack(cur, qubit, c, lab, addr);
                 if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
                 C = make_ctx(P.enc, n, P.mem, addr);
-                if (s_prev > 0) {                           // pending K_J of slice s_prev
+                if (pfc) pf_load(scr, cbase + r, rec);
+                if (s_prev > 0 && pfc) {                    // pending K_J, then K0 (product form)
+                    int okp;
+                    c = pf_jump(c, xs, C, rec, P.k, S.J, nJ, &alive, &okp);
+                    if (!okp) capfail = true;
+                } else if (s_prev > 0) {                    // pending K_J of slice s_prev
                     // damping lowers the sites of J; dephasing keeps them
                     // excited (a projection), and K0 then acts only on the
                     // excited sites outside J
@@ -2035,6 +2434,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 for (int s = s_prev + 1; s <= slast; ++s) {
                     const int form = apply_slice(P.ops[s], c, xs, C, LX);
                     if (!form) { capfail = true; break; }
+                    if (pfc && !pf_move(P.ops[s], c, xs, C, rec, P.k, s < s1)) { capfail = true; break; }
                     n2p += (form == kPathFast && c.pwB) ? 1u : 0u;
                     nreg += form == kPathReg ? 1u : 0u;
                     nmem += form == kPathMem ? 1u : 0u;
@@ -2052,13 +2452,25 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     if (s < s1) c.e += excited_count(c);     // no candidates: K0 on every site
                 }
                 {
-                    const int etop = c.e + (binc ? 2 * n * P.k : 0);   // the group's largest exponent
+                    // the largest exponent of its configurations
+                    const int etop = pfc ? pf_etop(rec, P.k, c.e) : c.e + (binc ? 2 * n * P.k : 0);
                     if (etop >= 4096 || (uni && etop >= H)) capfail = true;   // exponent bound (packed in 12 bits)
                 }
+                if (pfc && final_epoch) capfail = true;      // (the product form ends at slice 4n+2k-1)
                 if (!final_epoch) {
                     c1 = heat ? mask_first_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], mcnt)
                               : mask_first(c, xs, C, S.candbits, S.cl2, mcnt);
-                    if (!uni) {
+                    nent = mcnt > 0 ? 1u : 0u;
+                    if (pfc) {
+                        // sum over the configurations, the empty-mask part (c = 0 on T_C)
+                        pf_masks(rec, P.k, c.e, S.candbits, S.powlo, S.powhi, pm);
+                        pwf = uni ? 1.0 : col_w2(P, lab) * k2;
+                        double wt = pm.base;
+                        for (uint32_t q = 0; q < pm.ntc; ++q) wt *= 1.0 + pm.f[q];
+                        wsum += pwf * wt;
+                        if (mcnt == 0) wempty += pwf * pm.base;
+                        nent = (1u << pm.ntc) - (mcnt == 0 ? 1u : 0u);
+                    } else if (!uni) {
                         const double ae = apow(S, c.e);
                         w = col_w2(P, lab) * k2m * ae * ae * (binc ? S.bw : 1.0);
                         wsum += w;
@@ -2152,26 +2564,24 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     }
                 }
             }
+            put_entries((alive && !final_epoch) ? nent : 0u, pfc ? &pm : nullptr, c1, mcnt, uni ? c.e : 0, binc, w,
+                        !uni, pwf, selk, selw, scr.selseg, wcur, lane, capfail);
             {
-                const bool ne = alive && !final_epoch && mcnt > 0;
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ne);
-                if (ne) {
-                    const uint32_t pos = wcur + __popc(bal & ((1u << lane) - 1u));
-                    selk[pos] = sel_key(c1, mcnt, uni ? c.e : 0, binc);
-                    if (!uni) selw[pos] = w;
+                const uint32_t flags = (binc ? kBinFlag : 0u) | (pfc ? kPFFlag : 0u);
+                size_t dst = cbase + r;
+                if (compact) {
+                    uint32_t tot;
+                    const uint32_t pre = block_scan_flag(alive, &tot, S);
+                    dst = cbase + wr + pre;
+                    wr += tot;
                 }
-                wcur += __popc(bal);
-            }
-            if (compact) {
-                uint32_t tot;
-                const uint32_t pre = block_scan_flag(alive, &tot, S);
-                if (alive && !final_epoch) store_comp(scr, cbase + wr + pre, c, xs, qubit, lab | (binc ? kBinFlag : 0u), addr);
-                wr += tot;
-            } else if (alive && !final_epoch) {
-                store_comp(scr, cbase + r, c, xs, qubit, lab | (binc ? kBinFlag : 0u), addr);
+                if (alive && !final_epoch) {
+                    store_comp(scr, dst, c, xs, qubit, lab | flags, addr);
+                    if (pfc) { pf_store(scr, dst, rec); S.pfnext = 1u; }
+                }
             }
         }
-        if (lane == 0) S.segn[warp] = wcur;
+        if (lane == 0) S.segn[warp] = min(wcur, scr.selseg);
         nsl = __reduce_add_sync(0xFFFFFFFFu, nsl);
         if (lane == 0 && nsl) atomicAdd(&S.wk[1], nsl);
         if (__any_sync(0xFFFFFFFFu, (n2p | nreg | nmem | noff) != 0u)) {
@@ -2191,6 +2601,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
         __syncthreads();
         if (threadIdx.x == 0 && compact) S.ncomp = wr;
+        if (threadIdx.x == 0 && !lazy_pre) S.haspf = S.pfnext;
         if (uni && !(lazy_pre && factored)) {
             // fold the histograms (and leave them zero for the next epoch)
             __syncthreads();
@@ -2278,7 +2689,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             // group per branch (its configurations are on the noiseless orbit:
             // exponents E0 + 2n|c|, signs c.(j ^ d), Lemma 1)
             const bool mbin = binok && s1 >= sU;
-            const uint32_t ncw = (qubit && mlog == 0 && !mbin) ? (1u << P.k) : 1u;
+            // in between, one component in product form per branch
+            const bool mpf = pfok && mlog == 0 && !mbin;
+            const uint32_t ncw = (qubit && mlog == 0 && !mbin && !mpf) ? (1u << P.k) : 1u;
             const double wmul = (double)(1u << mlog) * (mbin ? S.bw : 1.0);
             uint32_t base = 0;
             bool capfail = false;
@@ -2300,42 +2713,60 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 const double w2 = cnt ? (uni ? w2u : col_w2(P, b) * k2) : 0.0;
                 const Ctx C = make_ctx(P.enc, n, P.mem, i);
                 for (uint32_t cw = 0; cw < ncw; ++cw) {
-                    const bool take = cnt && (all || (cw & tm));
-                    uint32_t c1 = 0, mcnt = 0;
+                    const bool take = cnt && (mpf || all || (cw & tm));
+                    uint32_t c1 = 0, mcnt = 0, nent = 0;
                     int ce = 0;
-                    double w = 0.0;
+                    double w = 0.0, pwf = 0.0;
+                    PFMasks pm;
                     if (take) {
                         CompR c = orbit_state(P, s1, i, cw, j, d);
                         c.e = E0 + (qubit ? data_exposure(P, cw, s1 - 1) : 0);
                         if (mbin) c.cb = (j ^ (d & P.orbit.fetched[s1])) & kmask;   // phi of the group
-                        store_comp(scr, cbase + r, c, nullptr, qubit, b | (mbin ? kBinFlag : 0u), i);
+                        uint32_t rec[8];
+                        if (mpf) {
+                            // the address part is configuration 0; data qubit t on its
+                            // orbit position (or bus slot), exposed for its window so
+                            // far, phase bit j_t plus its fetched memory bit
+                            for (int t = 0; t < 8; ++t) rec[t] = 0u;
+                            const uint32_t fm = P.orbit.fetched[s1], bm = P.orbit.bus[s1];
+                            for (int t = 0; t < P.k; ++t) {
+                                const uint32_t m = (uint32_t)ov(2 * n + 2 * t + 1, 4 * n + 2 * t, s1 - 1);
+                                const uint32_t ph = ((j >> t) ^ ((fm >> t) & (d >> t))) & 1u;
+                                rec[t] = kPFree | (ph ? kPPh : 0u) | (m << 16) | kPBus | (uint32_t)t;
+                                if ((bm >> t) & 1u) continue;
+                                for (uint32_t ww = P.orbit.occ[s1]; ww; ww &= ww - 1u) {
+                                    const int bb = __ffs(ww) - 1;
+                                    if (P.orbit.item[s1][bb] == 1 + n + t)
+                                        rec[t] = kPFree | (ph ? kPPh : 0u) | (m << 16) |
+                                                 (2u * path_node(i, n, bb >> 1) + (uint32_t)(bb & 1));
+                                }
+                            }
+                            pf_store(scr, cbase + r, rec);
+                        }
+                        store_comp(scr, cbase + r, c, nullptr, qubit, b | (mbin ? kBinFlag : 0u) | (mpf ? kPFFlag : 0u), i);
                         ++r;
                         c1 = mask_first(c, nullptr, C, S.candbits, S.cl2, mcnt);
                         ce = c.e;
-                        if (uni) {
-                            const int etop = c.e + (mbin ? 2 * n * P.k : 0);
-                            if (etop >= 4096 || etop >= H) capfail = true;  // the key holds 12 bits of e
-                        } else {
+                        nent = 1;
+                        const int etop = mpf ? pf_etop(rec, P.k, c.e) : c.e + (mbin ? 2 * n * P.k : 0);
+                        if (etop >= 4096 || (uni && etop >= H)) capfail = true;  // the key holds 12 bits of e
+                        if (mpf) {
+                            pf_masks(rec, P.k, c.e, S.candbits, S.powlo, S.powhi, pm);
+                            pwf = uni ? 1.0 : w2;
+                            nent = (1u << pm.ntc) - (mcnt == 0 ? 1u : 0u);
+                        } else if (!uni) {
                             const double ae = apow(S, c.e);
                             w = w2 * ae * ae * wmul;
                         }
                     }
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
-                    if (take) {
-                        const uint32_t q = wcur + __popc(bal & ((1u << lane) - 1u));
-                        if (q < scr.selseg) {
-                            selk[q] = sel_key(c1, mcnt, uni ? ce : 0, mbin);
-                            if (!uni) selw[q] = w;
-                        }
-                        else capfail = true;
-                    }
-                    wcur += __popc(bal);
+                    put_entries(nent, mpf ? &pm : nullptr, c1, mcnt, uni ? ce : 0, mbin, w, !uni, pwf, selk, selw,
+                                scr.selseg, wcur, lane, capfail);
                 }
                 base += tot;
             }
             if (lane == 0) S.segn[warp] = min(wcur, scr.selseg);
             if (__syncthreads_or(capfail) && threadIdx.x == 0) S.status = QRAM_E_CAP;
-            if (threadIdx.x == 0) S.ncomp = base;
+            if (threadIdx.x == 0) { S.ncomp = base; S.haspf = (mpf && base > 0) ? 1u : 0u; }
             __syncthreads();
         }
         if (!(Wemp > tgt) && S.status == QRAM_OK) {
@@ -2365,8 +2796,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                             const bool in = eq_only_single ? code == ceq && ((kv >> 16) & 7u) == 1u : code <= cmax;
                             if (eq_only_single && code == ceq && !in) mm = 1;
                             if (in) {
-                                if (uni) {
-                                    const uint32_t ex = kv >> 20;
+                                const uint32_t ex = kv >> 20;
+                                if (uni && ex != kPFKey) {
                                     if (!((kv >> 19) & 1u)) {
                                         if (ex < (uint32_t)H) atomicAdd(&hall[ex], 1u);
                                     } else {                   // a binomial group
@@ -2416,22 +2847,42 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     else start = 1;                                     // longer masks: general descent
                 }
             }
+            // fn(q, weight) for each mask of component r: q is mask_query's
+            // answer for the prefix pref[0..level); a component in product
+            // form has one mask per subset of its data qubits at candidates
+            auto masks_of = [&](uint32_t r, int level, auto &&fn) {
+                CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
+                const uint4 rv = scr.cs[cbase + r];
+                unpack(rv, qubit, c, lab, addr);
+                if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
+                const Ctx C = make_ctx(P.enc, n, P.mem, addr);
+                const double wf = uni ? w2u : col_w2(P, lab) * k2;
+                if (rv.w & kPFFlag) {
+                    uint32_t rec[8];
+                    PFMasks pm;
+                    pf_load(scr, cbase + r, rec);
+                    pf_masks(rec, P.k, c.e, S.candbits, S.powlo, S.powhi, pm);
+                    for (uint32_t sb = 0; sb < (1u << pm.ntc); ++sb) {
+                        uint32_t xc[kMaxK];
+                        int nx = 0;
+                        double wt = wf * pm.base;
+                        for (uint32_t q = 0; q < pm.ntc; ++q)
+                            if ((sb >> q) & 1u) { xc[nx++] = pm.code[q]; wt *= pm.f[q]; }
+                        fn(mask_query(c, xs, C, S.candbits, pref, level, xc, nx), wt);
+                    }
+                    return;
+                }
+                const long long q = heat ? mask_query_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], pref, level)
+                                         : mask_query(c, xs, C, S.candbits, pref, level);
+                const double ae = apow(S, c.e);
+                fn(q, wf * (double)(1u << mlog) * ae * ae * ((rv.w & kBinFlag) ? S.bw : 1.0));
+            };
             for (int level = start; level < kMaxJ && !decided; ++level) {
                 // weight of components whose mask equals the prefix exactly
                 if (level > 0) {
                     double we = 0.0;
-                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
-                        const uint4 rv = scr.cs[cbase + r];
-                        unpack(rv, qubit, c, lab, addr);
-                        if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
-                        const Ctx C = make_ctx(P.enc, n, P.mem, addr);
-                        if ((heat ? mask_query_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], pref, level) : mask_query(c, xs, C, S.candbits, pref, level)) == -1) {
-                            const double ae = apow(S, c.e);
-                            we += (uni ? w2u : col_w2(P, lab) * k2) * (double)(1u << mlog) * ae * ae *
-                                  ((rv.w & kBinFlag) ? S.bw : 1.0);
-                        }
-                    }
+                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT)
+                        masks_of(r, level, [&](long long q, double wt) { if (q == -1) we += wt; });
                     we = block_sum(we, S.redA, S);
                     if (O + we > tgt) break;                  // J = prefix
                     O += we;
@@ -2443,19 +2894,8 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     const uint32_t mid = (lo + hi) >> 1;
                     const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
                     double f = 0.0;
-                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
-                        const uint4 rv = scr.cs[cbase + r];
-                        unpack(rv, qubit, c, lab, addr);
-                        if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
-                        const Ctx C = make_ctx(P.enc, n, P.mem, addr);
-                        const long long q = (heat ? mask_query_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], pref, level) : mask_query(c, xs, C, S.candbits, pref, level));
-                        if (q >= 0 && (uint32_t)q <= cmid) {
-                            const double ae = apow(S, c.e);
-                            f += (uni ? w2u : col_w2(P, lab) * k2) * (double)(1u << mlog) * ae * ae *
-                                 ((rv.w & kBinFlag) ? S.bw : 1.0);
-                        }
-                    }
+                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT)
+                        masks_of(r, level, [&](long long q, double wt) { if (q >= 0 && (uint32_t)q <= cmid) f += wt; });
                     f = block_sum(f, S.redA, S);
                     if (O + f > tgt) hi = mid;
                     else { lo = mid + 1; Flo = f; }
@@ -2464,14 +2904,10 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     // rounding left the target above the total: take the last
                     // group with weight (the oracle's rule); descend on the largest code
                     uint32_t best = 0xFFFFFFFFu;
-                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT) {
-                        CompR c; alignas(16) uint16_t xs[kXcap]; uint32_t lab, addr;
-                        unpack(scr.cs[cbase + r], qubit, c, lab, addr);
-                        if (c.nexc) load_exc(scr, cbase + r, c.nexc, xs);
-                        const Ctx C = make_ctx(P.enc, n, P.mem, addr);
-                        const long long q = (heat ? mask_query_heat(c, xs, C, cand, pev, S.slice_off[s1], S.slice_off[s1 + 1], pref, level) : mask_query(c, xs, C, S.candbits, pref, level));
-                        if (q >= 0 && (best == 0xFFFFFFFFu || (uint32_t)q > best)) best = (uint32_t)q;
-                    }
+                    for (uint32_t r = threadIdx.x; r < S.ncomp; r += NT)
+                        masks_of(r, level, [&](long long q, double) {
+                            if (q >= 0 && (best == 0xFFFFFFFFu || (uint32_t)q > best)) best = (uint32_t)q;
+                        });
                     __shared__ uint32_t sbest;
                     if (threadIdx.x == 0) sbest = 0u;
                     __syncthreads();
@@ -2499,7 +2935,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         }
         if (threadIdx.x == 0) {
             S.nJ = nsel;
-            if (lazy_pre && nsel == 0) S.ncomp = 0;       // no jump: the branches stay implicit
+            if (lazy_pre && nsel == 0) { S.ncomp = 0; S.haspf = 0u; }   // no jump: the branches stay implicit
         }
         if (lazy_pre && nsel == 0) mlog = 0;
         __syncthreads();

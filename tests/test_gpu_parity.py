@@ -331,12 +331,12 @@ def test_work_counters_exact():
     w = sim.work_counters(reset=True)
     assert w["draws"] == 0
     # one merged component per branch through slices 1..2n (before the first
-    # wall its 2^k configurations share the tree), every configuration from
-    # 2n+1 to sU = 4n+2k-1, then one binomial group per branch (every data
-    # qubit back in the bus)
-    sU = 4 * n + 2 * k - 1
-    assert w["comp_slices"] == ntraj * p.D * (2 * n + (1 << k) * (sU - 2 * n) + (T - 1 - sU))
-    assert w["comp_epochs"] == ntraj * p.D * (2 + (1 << k))
+    # wall its 2^k configurations share the tree), one in product form from
+    # 2n+1 to 4n+2k-1 (the data qubits follow the routers whatever their
+    # values), then one binomial group per branch (every data qubit back in
+    # the bus): three epochs of one component per branch
+    assert w["comp_slices"] == ntraj * p.D * (T - 1)
+    assert w["comp_epochs"] == ntraj * p.D * 3
     sim.results(sim.run_pruned(0, g0))
     w = sim.work_counters(reset=True)
     assert w["comp_slices"] == 0 and w["comp_epochs"] == 0
