@@ -659,50 +659,54 @@ __device__ __forceinline__ bool fast_slice(const SliceOps &op, CompR &c, const C
 
 // ---- register generic path: path A as bits, a few other sites in registers --
 // The same gate semantics as slow_slice for a component whose excitations off
-// its address path (path B and the off-path list together) fit in kHX
-// registers: path A follows the fast path's bit operations, the other sites
-// form an unsorted list with compile-time indices (so it stays in registers),
-// and a router of path A that points away from A exchanges its data slot with
-// that list.  Returns *okp = 0, leaving c and xs untouched, when the list
-// would overflow.
-constexpr int kHX = 8;
-
+// its address path (path B and the off-path list together) fit in CAP
+// registers (8, else 16): path A follows the fast path's bit operations, the
+// other sites form an unsorted list with compile-time indices (so it stays
+// in registers), and a router of path A that points away from A exchanges
+// its data slot with that list.  Returns *okp = 0, leaving c and xs
+// untouched, when the list would overflow.  (The memory form keeps sorted
+// lists in local memory; its insertion sorts are long chains of dependent
+// local accesses, several times slower, so it is left for lists above 16.)
+template <int CAP>
 struct HX {
-    uint32_t v[kHX];     // site << 2 | level (1: excited / L, 2: R); 0 = empty
+    uint32_t v[CAP];     // site << 2 | level (1: excited / L, 2: R); 0 = empty
 };
 
-__device__ __forceinline__ int hx_get(const HX &X, uint32_t site) {
+template <int CAP>
+__device__ __forceinline__ int hx_get(const HX<CAP> &X, uint32_t site) {
     int l = 0;
 #pragma unroll
-    for (int q = 0; q < kHX; ++q)
+    for (int q = 0; q < CAP; ++q)
         if (X.v[q] != 0u && (X.v[q] >> 2) == site) l = (int)(X.v[q] & 3u);
     return l;
 }
 
 // set the level of a site (0 removes it); false if the list is full
-__device__ __forceinline__ bool hx_set(HX &X, uint32_t site, int lvl) {
+template <int CAP>
+__device__ __forceinline__ bool hx_set(HX<CAP> &X, uint32_t site, int lvl) {
     bool done = false;
 #pragma unroll
-    for (int q = 0; q < kHX; ++q)
+    for (int q = 0; q < CAP; ++q)
         if (!done && X.v[q] != 0u && (X.v[q] >> 2) == site) {
             X.v[q] = lvl ? ((site << 2) | (uint32_t)lvl) : 0u;
             done = true;
         }
     if (done || lvl == 0) return true;
 #pragma unroll
-    for (int q = 0; q < kHX; ++q)
+    for (int q = 0; q < CAP; ++q)
         if (!done && X.v[q] == 0u) { X.v[q] = (site << 2) | (uint32_t)lvl; done = true; }
     return done;
 }
 
-__device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t *xs, const Ctx C, int *okp) {
+template <int CAP>
+__device__ __forceinline__ CompR hybrid_cap(const SliceOps &op, CompR c, uint16_t *xs, const Ctx &C, int *okp) {
     *okp = 0;
     const bool qubit = C.enc == QRAM_QUBIT;
     const int n = C.n;
-    if (__popc(c.pwB) + (int)c.nexc > kHX) return c;
-    HX X;
+    if (__popc(c.pwB) + (int)c.nexc > CAP) return c;
+    HX<CAP> X;
 #pragma unroll
-    for (int q = 0; q < kHX; ++q) X.v[q] = 0u;
+    for (int q = 0; q < CAP; ++q) X.v[q] = 0u;
     {
         const uint32_t iB = b_addr(c, C);
         for (uint32_t w = c.pwB; w; w &= w - 1u) {
@@ -740,14 +744,14 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
         t = (pwR ^ (pwR >> 1)) & op.iswap2;
         pwR ^= t | (t << 1);
 #pragma unroll
-        for (int q = 0; q < kHX; ++q)
+        for (int q = 0; q < CAP; ++q)
             if (X.v[q] != 0u && ((op.iswap >> layer_of(X.v[q] >> 3)) & 1u)) X.v[q] ^= 4u;   // router <-> data
     }
     if (op.cswap) {
-        // routers do not move: read them before moving data
-        HX Y = X;
+        // routers do not move, so each data entry moves in place, once, by
+        // the routers' values
 #pragma unroll
-        for (int q = 0; q < kHX; ++q) {
+        for (int q = 0; q < CAP; ++q) {
             const uint32_t e = X.v[q], site = e >> 2, u = site >> 1;
             if (e == 0u || !(site & 1u)) continue;
             const int L = layer_of(u);
@@ -755,17 +759,16 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
                 const int r = hx_get(X, 2u * u);
                 if (!qubit && r == 0) continue;
                 const uint32_t child = qubit ? 2u * u + 1u + (uint32_t)r : 2u * u + (uint32_t)r;
-                Y.v[q] = ((2u * child + 1u) << 2) | (e & 3u);
+                X.v[q] = ((2u * child + 1u) << 2) | (e & 3u);
             } else if (L >= 1 && ((op.cswap >> (L - 1)) & 1u)) {
                 const uint32_t par = (u - 1u) >> 1;
                 if (par == path_node(C.i, n, L - 1)) continue;           // exchange with path A below
                 const int r = hx_get(X, 2u * par);
                 if (!qubit && r == 0) continue;
                 const uint32_t child = qubit ? 2u * par + 1u + (uint32_t)r : 2u * par + (uint32_t)r;
-                if (child == u) Y.v[q] = ((2u * par + 1u) << 2) | (e & 3u);
+                if (child == u) X.v[q] = ((2u * par + 1u) << 2) | (e & 3u);
             }
         }
-        X = Y;
         for (uint32_t m = op.cswap; m; m &= m - 1u) {
             const int L = __ffs(m) - 1;
             if (L + 1 >= n) continue;
@@ -801,7 +804,7 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
                 if ((__ldg(C.mem + cell) >> op.fetch) & 1u) sign ^= 1u;
             }
 #pragma unroll
-            for (int q = 0; q < kHX; ++q) {
+            for (int q = 0; q < CAP; ++q) {
                 const uint32_t e = X.v[q], site = e >> 2, u = site >> 1;
                 if (e == 0u || !(site & 1u) || layer_of(u) != L) continue;
                 const uint32_t cell = 2u * (u - lo) + (uint32_t)hx_get(X, 2u * u);
@@ -817,9 +820,9 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
                     else if (dR) { pw &= ~bit; pwR &= ~bit; }
                 }
             }
-            uint32_t flip[kHX];
+            uint32_t flip[CAP];
 #pragma unroll
-            for (int q = 0; q < kHX; ++q) {
+            for (int q = 0; q < CAP; ++q) {
                 const uint32_t e = X.v[q], site = e >> 2, u = site >> 1;
                 flip[q] = 0u;
                 if (e == 0u || (site & 1u) || layer_of(u) != L) continue;
@@ -827,7 +830,7 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
                 if ((__ldg(C.mem + cell) >> op.fetch) & 1u) flip[q] = 2u * u + 2u;   // data site + 1
             }
 #pragma unroll
-            for (int q = 0; q < kHX; ++q) {
+            for (int q = 0; q < CAP; ++q) {
                 if (!flip[q]) continue;
                 const uint32_t ds = flip[q] - 1u;
                 const int d = hx_get(X, ds);
@@ -838,12 +841,12 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
     // sorted off-path list (insertion into xs in site order)
     uint32_t cnt = 0;
 #pragma unroll
-    for (int q = 0; q < kHX; ++q) cnt += X.v[q] != 0u ? 1u : 0u;
+    for (int q = 0; q < CAP; ++q) cnt += X.v[q] != 0u ? 1u : 0u;
     uint32_t prev = 0u;
     for (uint32_t k = 0; k < cnt; ++k) {
         uint32_t best = 0xFFFFFFFFu;
 #pragma unroll
-        for (int q = 0; q < kHX; ++q)
+        for (int q = 0; q < CAP; ++q)
             if (X.v[q] != 0u && X.v[q] > prev && X.v[q] < best) best = X.v[q];
         const uint32_t site = best >> 2;
         xs[k] = (uint16_t)((site << 1) | ((best & 3u) == 2u ? 1u : 0u));
@@ -852,6 +855,14 @@ __device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t 
     c.pw = pw; c.pwR = qubit ? 0u : pwR; c.pwB = 0u; c.ldiv = -1; c.nexc = cnt; c.cb = cb; c.sign = sign;
     *okp = 1;
     return c;
+}
+
+__device__ __noinline__ CompR hybrid_slice(const SliceOps op, CompR c, uint16_t *xs, const Ctx C, int *okp) {
+    CompR h = c;
+    *okp = 0;
+    if (__popc(c.pwB) + (int)c.nexc <= 8) h = hybrid_cap<8>(op, c, xs, C, okp);
+    if (!*okp) h = hybrid_cap<16>(op, c, xs, C, okp);            // more items, or the list grew past 8
+    return *okp ? h : c;
 }
 
 // layers holding off-path items (bit L)
@@ -2010,7 +2021,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 base += tot;
             }
             bool capf = false, kept = false;
-            if (base <= scr.ecap) {
+            if (!atU && base == nc) {
+                kept = true;                             // every component stays as it is
+            } else if (base <= scr.ecap) {
                 for (int r0 = ((int)nc - 1) / NT * NT; r0 >= 0; r0 -= NT) {
                     const uint32_t r = (uint32_t)r0 + threadIdx.x;
                     const bool have = r < nc;
