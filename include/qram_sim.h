@@ -55,7 +55,7 @@ enum {
     QRAM_E_ARG = 1,      /* invalid argument (sizes, gamma, duplicate address, norm) */
     QRAM_E_OOM = 2,      /* device or host allocation failed */
     QRAM_E_CUDA = 3,     /* a CUDA runtime call failed */
-    QRAM_E_TIMEOUT = 4,  /* a bounded device wait gave up */
+    QRAM_E_TIMEOUT = 4,  /* a bounded device wait gave up; per trajectory: its cycle budget (2^34) ran out */
     QRAM_E_BUSY = 5,     /* server queue full / resource busy */
     QRAM_E_CAP = 6,      /* a per-trajectory capacity was exceeded (result marked) */
     QRAM_E_STATE = 7,    /* call not valid in the current state */

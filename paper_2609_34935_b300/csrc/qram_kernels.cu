@@ -168,6 +168,8 @@ struct Smem {
     uint32_t hitbits[512];         // lazy epochs: addresses under a candidate on an occupied position
     uint32_t wk[8];                // work of this trajectory (see Params::ctr)
     uint32_t haspf, pfnext;        // components in product form exist (pfnext: written during a pass)
+    uint32_t anyent;               // a component of this pass has a non-empty mask
+    long long t_start;             // clock64 at the trajectory's start (watchdog)
     double fprod2[kMaxT];          // product-form lazy weights: prod_l (1 + a^(2 ov_l(s))) per slice s
     double fprod1;                 // prod_l (1 + a^(ov_l(T-1))): the final overlap
     int16_t etab[4][16];           // lazy epochs: address exposure by nibble of the address
@@ -1193,6 +1195,10 @@ __device__ __noinline__ CompR heat_apply(CompR c, uint16_t *xs, const Ctx C, con
 // (Scratch::pfr; 0 = fixed):
 //   bit 31 free | bit 23 ph | bits 16-22 m | bit 15 in the bus | bits 0-14 site, or bus slot
 constexpr uint32_t kPFFlag = 1u << 30;
+// Cycle budget of one trajectory (about 8 s at 2 GHz, thousands of times the
+// slowest trajectory of the benchmark workloads): past it the trajectory
+// ends with QRAM_E_TIMEOUT instead of holding its CTA.
+constexpr long long kCycleBudget = 1ll << 34;
 constexpr uint32_t kPFree = 1u << 31, kPBus = 1u << 15, kPPh = 1u << 23;
 
 __device__ __forceinline__ uint32_t pf_m(uint32_t w) { return (w >> 16) & 0x7Fu; }
@@ -1696,6 +1702,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         return;
     }
     if (threadIdx.x == 0) {
+        S.t_start = clock64();
         S.status = valid ? QRAM_OK : QRAM_E_ARG; S.refcol = -1; S.nbad = 0; S.nJ = 0;
         for (int q = 0; q < 8; ++q) S.wk[q] = 0;
     }
@@ -2233,6 +2240,9 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             if (pfok && S.haspf && jumped)                    // before a router swap of the unload
                 for (int s = s_prev + 2; s <= s1 && s <= sU; ++s)
                     if (pfchk(s)) { s1 = s - 1; break; }
+            // a trajectory past its cycle budget, or an epoch that would not
+            // advance, goes to its final epoch (status QRAM_E_TIMEOUT)
+            if (S.status == QRAM_E_TIMEOUT || s1 <= s_prev) s1 = T;
         }
         const bool final_epoch = s1 >= T;
         const uint32_t mc = 1u << mlog;                    // configurations per component
@@ -2240,6 +2250,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         if (threadIdx.x == 0) {
             S.cl2 = 0;
             S.pfnext = 0u;
+            S.anyent = 0u;
             // data factors after damping slices 1..sw (tabulated per trajectory)
             const int sw = final_epoch ? T - 1 : s1 - 1;
             const double dn = qubit ? S.fdn[sw] : 1.0;
@@ -2577,6 +2588,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     }
                 }
             }
+            if (alive && !final_epoch && nent) S.anyent = 1u;
             put_entries((alive && !final_epoch) ? nent : 0u, pfc ? &pm : nullptr, c1, mcnt, uni ? c.e : 0, binc, w,
                         !uni, pwf, selk, selw, scr.selseg, wcur, lane, capfail);
             {
@@ -2615,7 +2627,15 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         __syncthreads();
         if (threadIdx.x == 0 && compact) S.ncomp = wr;
         if (threadIdx.x == 0 && !lazy_pre) S.haspf = S.pfnext;
-        if (uni && !(lazy_pre && factored)) {
+        // No component with a non-empty mask: every weight went into both sums
+        // alike, so Wemp = Wtot and no jump can fire; the sums are not needed
+        // (the histograms are only cleared).
+        const bool nodraw = !final_epoch && !lazy_pre && !S.anyent && (compact ? wr : ncomp) > 0u;
+        if (nodraw) {
+            for (int b = threadIdx.x; uni && b < H; b += NT)
+                if (hall[b]) { hall[b] = 0; hemp[b] = 0; hov[b] = 0; }
+            wsum = 1.0; wempty = 1.0;
+        } else if (uni && !(lazy_pre && factored)) {
             // fold the histograms (and leave them zero for the next epoch)
             __syncthreads();
             for (int b = threadIdx.x; b < H; b += NT) {
@@ -2630,11 +2650,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 hall[b] = 0; hemp[b] = 0; hov[b] = 0;
             }
         }
-        block_sum3(wsum, wempty, ovl, S, S.fW, S.fW, S.fO);
+        if (!nodraw) block_sum3(wsum, wempty, ovl, S, S.fW, S.fW, S.fO);
         // good branches of the eager form: closed-form weights before the
         // first jump (Eq. (21))
         double wgs = 0.0, ogs = 0.0;
-        if (P.mode == kPruned && !jumped && !lazy && !depol && !heat) {
+        if (P.mode == kPruned && !jumped && !lazy && !depol && !heat && !nodraw) {
             const int sw = final_epoch ? T - 1 : s1 - 1;
             for (uint32_t b = threadIdx.x; b < (uint32_t)P.D; b += NT) {
                 const uint32_t i = __ldg(P.addr + b);
@@ -2840,10 +2860,58 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 };
                 uint32_t lo = 0, hi = ncodes;
                 double Flo = 0.0;
+                // A short list (at most 8 NT entries) is searched directly: each
+                // entry's first code is turned once into its index among the
+                // slice's codes (the candidate sites staged, ascending, in the
+                // zero hemp area) and its weight into FP64, in place in the
+                // list; every step of the search is then a compare-and-add per
+                // entry and one block sum.  Longer lists (a first jump of many
+                // branches) keep the histogram sums.
+                const uint32_t ncs = ncodes / 2u;
+                uint32_t tot = 0;
+                for (uint32_t q = 0; q < NW; ++q) tot += S.segn[q];
+                const bool direct = tot <= 8u * NT && ncs <= (uint32_t)P.hist_pad;
+                uint32_t *skw = scr.selk + slot * NW * (size_t)scr.selseg;
+                double *sww = scr.selw + slot * NW * (size_t)scr.selseg;
+                auto each_entry = [&](auto &&fn) {
+                    for (uint32_t q = 0; q < NW; ++q) {
+                        const uint32_t nq = S.segn[q];
+                        for (uint32_t e = threadIdx.x; e < nq; e += NT) fn(q * (size_t)scr.selseg + e);
+                    }
+                };
+                const double fsc = uni ? w2u * (double)(1u << mlog) : 1.0;
+                if (direct) {
+                    for (uint32_t c = threadIdx.x; c < ncs; c += NT) hemp[c] = cand[cb0 + c] & 0xFFFFu;
+                    __syncthreads();
+                    each_entry([&](size_t at) {
+                        const uint32_t kv = skw[at], code = kv & 0xFFFFu, site = code >> 1, ex = kv >> 20;
+                        uint32_t a0 = 0, a1 = ncs;
+                        while (a0 < a1) {
+                            const uint32_t m = (a0 + a1) >> 1;
+                            if (hemp[m] < site) a0 = m + 1; else a1 = m;
+                        }
+                        double w;
+                        if (!uni || ex == kPFKey) {
+                            w = sww[at];
+                        } else {
+                            const double ae = apow(S, (int)ex);
+                            w = ae * ae * (((kv >> 19) & 1u) ? S.bw : 1.0);       // a binomial group: (1 + a^(4n))^k
+                        }
+                        skw[at] = (2u * a0 + (code & 1u)) | (((kv >> 16) & 7u) << 16);
+                        sww[at] = w;
+                    });
+                    __syncthreads();
+                    for (uint32_t c = threadIdx.x; c < ncs; c += NT) hemp[c] = 0u;
+                }
+                auto Fdir = [&](uint32_t ximax) {
+                    double f = 0.0;
+                    each_entry([&](size_t at) { if ((skw[at] & 0xFFFFu) <= ximax) f += sww[at]; });
+                    return block_sum(f, S.redA, S) * fsc;
+                };
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi) >> 1;
                     const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
-                    const double f = Fsum(cmid, 0, false, nullptr);
+                    const double f = direct ? Fdir(mid) : Fsum(cmid, 0, false, nullptr);
                     if (O + f > tgt) hi = mid;
                     else { lo = mid + 1; Flo = f; }
                 }
@@ -2851,7 +2919,18 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                     const uint32_t code = 2u * (cand[cb0 + (lo >> 1)] & 0xFFFFu) + (lo & 1u);
                     O += Flo;
                     int mm = 0;
-                    const double wex = Fsum(0, code, true, &mm);
+                    double wex;
+                    if (direct) {
+                        double f = 0.0;
+                        each_entry([&](size_t at) {
+                            const uint32_t kv = skw[at];
+                            if ((kv & 0xFFFFu) != lo) return;
+                            if (((kv >> 16) & 7u) == 1u) f += sww[at]; else mm = 1;
+                        });
+                        wex = block_sum(f, S.redA, S) * fsc;
+                    } else {
+                        wex = Fsum(0, code, true, &mm);
+                    }
                     const int multi = __syncthreads_or(mm);
                     if (threadIdx.x == 0) pref[0] = code;
                     __syncthreads();
@@ -2984,6 +3063,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         }
         if (lazy_pre)
             for (uint32_t wd = threadIdx.x; wd < ((1u << n) + 31u) / 32u; wd += NT) S.hitbits[wd] = 0u;
+        if (threadIdx.x == 0 && (clock64() - S.t_start > kCycleBudget || s1 <= s_prev)) S.status = QRAM_E_TIMEOUT;
         __syncthreads();
         s_prev = s1;
     }
