@@ -134,6 +134,8 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
+constexpr int kLook = 8;           // lazy slices evaluated per look-ahead
+
 template <int NT>
 struct Smem {
     static constexpr int NW = NT / 32;
@@ -169,6 +171,15 @@ struct Smem {
     uint32_t wk[8];                // work of this trajectory (see Params::ctr)
     uint32_t haspf, pfnext;        // components in product form exist (pfnext: written during a pass)
     uint32_t anyent;               // a component of this pass has a non-empty mask
+    // look-ahead over lazy epochs: slices, their occupied candidate positions,
+    // staging offsets, exposure tables, data factors, warp partials, hit sums
+    int lz_k;
+    int lz_s[kLook];
+    uint32_t lz_pos[kLook], lz_off[kLook + 1];
+    int16_t lz_etab[kLook][4][16];
+    double lz_qt[kLook][kMaxK];
+    double lz_wp[kLook][NW];
+    double lz_hit[kLook];
     long long t_start;             // clock64 at the trajectory's start (watchdog)
     double fprod2[kMaxT];          // product-form lazy weights: prod_l (1 + a^(2 ov_l(s))) per slice s
     double fprod1;                 // prod_l (1 + a^(ov_l(T-1))): the final overlap
@@ -1521,21 +1532,27 @@ __device__ __forceinline__ uint32_t orbit_value(const Params &P, int it, int s, 
 // candidates of slice s on the orbit of address i at the positions `pos`:
 // *all = every configuration has a non-empty mask; the return value (qubit)
 // = data qubits whose excitation at a candidate site makes it non-empty
-__device__ __forceinline__ uint32_t orbit_hits(const Params &P, const uint32_t *candbits, uint32_t pos, int s,
-                                               uint32_t i, uint32_t j, uint32_t d, bool &all) {
+template <typename IsCand>
+__device__ __forceinline__ uint32_t orbit_hits_by(const Params &P, IsCand is_cand, uint32_t pos, int s, uint32_t i,
+                                                  uint32_t j, uint32_t d, bool &all) {
     const int n = P.n;
     uint32_t tm = 0;
     all = false;
     for (uint32_t w = pos; w; w &= w - 1u) {
         const int b = __ffs(w) - 1;
         const uint32_t site = 2u * path_node(i, n, b >> 1) + (uint32_t)(b & 1);
-        if (!((candbits[site >> 5] >> (site & 31u)) & 1u)) continue;
+        if (!is_cand(site)) continue;
         const int it = P.orbit.item[s][b];
         if (P.enc == QRAM_QUBIT && it > n) { tm |= 1u << (it - 1 - n); continue; }
         uint32_t isR;
         if (orbit_value(P, it, s, i, 0u, j, d, isR)) all = true;
     }
     return tm;
+}
+__device__ __forceinline__ uint32_t orbit_hits(const Params &P, const uint32_t *candbits, uint32_t pos, int s,
+                                               uint32_t i, uint32_t j, uint32_t d, bool &all) {
+    return orbit_hits_by(P, [&](uint32_t site) { return ((candbits[site >> 5] >> (site & 31u)) & 1u) != 0u; }, pos, s, i,
+                         j, d, all);
 }
 
 // the explicit state of configuration cw of the branch with address i after
@@ -2244,6 +2261,124 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
             // advance, goes to its final epoch (status QRAM_E_TIMEOUT)
             if (S.status == QRAM_E_TIMEOUT || s1 <= s_prev) s1 = T;
         }
+        if (factored && !jumped && s1 < T && S.status == QRAM_OK) {
+            // Look-ahead over lazy epochs (product-form closed weights, before
+            // the first jump).  An epoch without a jump changes no state, so the
+            // next candidate slices c_0 = s1 < c_1 < ... (at most kLook) are
+            // evaluated together: per slice the empty-mask weight is the closed
+            // form minus the hit branches' share (as in the lazy pass below),
+            // their sums take one warp partial per slice and one reduction;
+            // the draws are then taken in order, and the slices before the
+            // first that fires are done.  That slice is left to the regular
+            // epoch.  Staging (hit bitmaps, candidate sites) uses the zero
+            // histogram area and leaves it zero.
+            if (threadIdx.x == 0) {
+                int kk = 0, x = s1;
+                while (kk < kLook && x < T) {
+                    S.lz_s[kk++] = x;
+                    int nx = T;
+                    for (int wd = (x + 1) >> 5; wd < 4; ++wd) {
+                        const uint32_t bits = S.syncmask[wd] & (wd == ((x + 1) >> 5) ? (0xFFFFFFFFu << ((x + 1) & 31)) : 0xFFFFFFFFu);
+                        if (bits) { nx = min(T, 32 * wd + __ffs(bits) - 1); break; }
+                    }
+                    x = nx;
+                }
+                const uint32_t W = ((1u << n) + 31u) >> 5;
+                uint32_t off = (uint32_t)kk * W;
+                for (int q = 0; q < kk; ++q) {
+                    S.lz_off[q] = off;
+                    off += S.slice_off[S.lz_s[q] + 1] - S.slice_off[S.lz_s[q]];
+                    S.lz_pos[q] = 0u;
+                }
+                S.lz_off[kk] = off;
+                S.lz_k = (kk >= 2 && off <= 3u * (uint32_t)P.hist_pad) ? kk : 0;   // (room to stage)
+            }
+            __syncthreads();
+            const int K = S.lz_k;
+            if (K >= 2) {
+                const uint32_t W = ((1u << n) + 31u) >> 5;
+                for (int t = (int)threadIdx.x; t < K * 64 + K * P.k; t += NT) {
+                    if (t < K * 64) {                               // exposure tables of slice j (Eq. (14))
+                        const int jj = t >> 6, g = (t >> 4) & 3, v = t & 15, sw = S.lz_s[jj] - 1;
+                        int e = 0;
+                        for (int q = 0; q < 4; ++q) {
+                            const int pb = 4 * g + q, l = n - 1 - pb;
+                            if (pb < n && ((v >> q) & 1)) e += ov(2 * l + 1, T - 2 * l - 2, sw);
+                        }
+                        S.lz_etab[jj][g][v] = (int16_t)e;
+                    } else {                                        // data factors 1 / (1 + a^(2 m_t))
+                        const int jj = (t - K * 64) / P.k, q = (t - K * 64) % P.k, sw = S.lz_s[jj] - 1;
+                        S.lz_qt[jj][q] = S.rdat[ov(2 * n + 2 * q + 1, 4 * n + 2 * q, sw)];
+                    }
+                }
+                for (int jj = 0; jj < K; ++jj) {                    // hit bitmaps and candidate sites
+                    const int sj = S.lz_s[jj];
+                    const uint32_t c0 = S.slice_off[sj], nc = S.slice_off[sj + 1] - c0;
+                    for (uint32_t c = threadIdx.x; c < nc; c += NT) {
+                        const uint32_t site = cand[c0 + c] & 0xFFFFu;
+                        const int b = 2 * layer_of(site >> 1) + (int)(site & 1u);
+                        hist[S.lz_off[jj] + c] = site;
+                        if ((P.orbit.occ[sj] >> b) & 1u) {
+                            mark_leaves(hist + (size_t)jj * W, n, site >> 1, true);
+                            atomicOr(&S.lz_pos[jj], 1u << b);
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int jj = 0; jj < K; ++jj) {
+                    const int sj = S.lz_s[jj];
+                    const uint32_t pos = S.lz_pos[jj], *bm = hist + (size_t)jj * W, *sites = hist + S.lz_off[jj];
+                    const uint32_t ns = S.lz_off[jj + 1] - S.lz_off[jj];
+                    auto in_slice = [&](uint32_t site) {
+                        uint32_t a0 = 0, a1 = ns;
+                        while (a0 < a1) {
+                            const uint32_t m = (a0 + a1) >> 1;
+                            if (sites[m] < site) a0 = m + 1; else a1 = m;
+                        }
+                        return a0 < ns && sites[a0] == site;
+                    };
+                    double acc = 0.0;
+                    for (uint32_t i = threadIdx.x; pos && i < (1u << n); i += NT) {
+                        if (!((bm[i >> 5] >> (i & 31u)) & 1u)) continue;
+                        const uint32_t b = __ldg(P.col_of + i);
+                        const int E = S.lz_etab[jj][0][i & 15u] + S.lz_etab[jj][1][(i >> 4) & 15u] +
+                                      S.lz_etab[jj][2][(i >> 8) & 15u] + S.lz_etab[jj][3][(i >> 12) & 15u];
+                        bool all = false;
+                        const uint32_t tm = orbit_hits_by(P, in_slice, pos, sj, i, __ldg(P.bus + b), __ldg(P.mem + i), all);
+                        if (!all && !tm) continue;
+                        const double ae = apow(S, E);
+                        double qp = 1.0;
+                        for (uint32_t x = tm; x; x &= x - 1u) qp *= S.lz_qt[jj][__ffs(x) - 1];
+                        acc += all ? ae * ae : ae * ae * (1.0 - qp);
+                    }
+                    if (__any_sync(0xFFFFFFFFu, acc != 0.0)) acc = warp_sum(acc);
+                    if ((threadIdx.x & 31u) == 0) S.lz_wp[jj][threadIdx.x >> 5] = acc;
+                }
+                __syncthreads();
+                if ((int)threadIdx.x < K) {                          // one thread per slice, fixed order
+                    const int jj = (int)threadIdx.x;
+                    double h = 0.0;
+                    for (int q = 0; q < NW; ++q) h += S.lz_wp[jj][q];
+                    S.lz_hit[jj] = h;
+                }
+                __syncthreads();
+                int jf = K;                                         // first slice whose draw fires
+                for (int jj = 0; jj < K; ++jj) {
+                    const int sw = S.lz_s[jj] - 1;
+                    const double fw = w2u * inv_k2 * S.fdn[sw];
+                    const double wt = S.fprod2[sw] * fw, we = (S.fprod2[sw] - S.lz_hit[jj]) * fw;
+                    if (!(we > uniform53(P.seed, (uint32_t)S.lz_s[jj], 2u, traj) * wt)) { jf = jj; break; }
+                }
+                for (uint32_t w = threadIdx.x; w < S.lz_off[K]; w += NT) hist[w] = 0u;
+                if (threadIdx.x == 0 && jf > 0) S.wk[2] += (uint32_t)P.D * (uint32_t)jf;
+                const int sdone = jf > 0 ? S.lz_s[jf - 1] : 0;
+                __syncthreads();
+                if (jf > 0) {                                       // those slices are done
+                    s_prev = sdone;
+                    continue;
+                }
+            }
+        }
         const bool final_epoch = s1 >= T;
         const uint32_t mc = 1u << mlog;                    // configurations per component
         const double k2m = k2 * (double)mc;
@@ -2394,17 +2529,12 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
         uint32_t *selk = scr.selk + (slot * NW + warp) * (size_t)scr.selseg;
         double *selw = scr.selw + (slot * NW + warp) * (size_t)scr.selseg;
         uint32_t wcur = 0;
-        // one chunk of look-ahead: the next chunk's packed state is in flight
-        // while this chunk evolves
-        uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
-        if (threadIdx.x < ncomp_pass) nxt = scr.cs[cbase + threadIdx.x];
         uint32_t nsl = 0;                                  // component-slices evolved by this thread
         uint32_t n2p = 0, nreg = 0, nmem = 0, noff = 0;    // by form: two paths, register / memory generic, off-path
         for (uint32_t r0 = 0; r0 < ncomp_pass; r0 += NT) {
             const uint32_t r = r0 + threadIdx.x;
             bool alive = r < ncomp_pass;
-            const uint4 cur = nxt;
-            if (r + NT < ncomp_pass) nxt = scr.cs[cbase + r + NT];
+            const uint4 cur = alive ? scr.cs[cbase + r] : make_uint4(0u, 0u, 0u, 0u);
             CompR c;
             alignas(16) uint16_t xs[kXcap];
             uint32_t lab = 0, addr = 0, c1 = 0xFFFFFFFFu, mcnt = 0;
