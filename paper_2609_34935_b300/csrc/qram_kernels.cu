@@ -171,6 +171,8 @@ struct Smem {
     uint32_t wk[8];                // work of this trajectory (see Params::ctr)
     uint32_t haspf, pfnext;        // components in product form exist (pfnext: written during a pass)
     uint32_t anyent;               // a component of this pass has a non-empty mask
+    uint32_t npres;                // direct level-0 search: codes present among the entries (list if <= 128)
+    uint16_t plist[128];
     // look-ahead over lazy epochs: slices, their occupied candidate positions,
     // staging offsets, exposure tables, data factors, warp partials, hit sums
     int lz_k;
@@ -3000,7 +3002,7 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 const uint32_t ncs = ncodes / 2u;
                 uint32_t tot = 0;
                 for (uint32_t q = 0; q < NW; ++q) tot += S.segn[q];
-                const bool direct = tot <= 8u * NT && ncs <= (uint32_t)P.hist_pad;
+                const bool direct = tot <= 8u * NT && ncs <= (uint32_t)P.hist_pad && ncodes / 16u + 2u <= (uint32_t)P.hist_pad;
                 uint32_t *skw = scr.selk + slot * NW * (size_t)scr.selseg;
                 double *sww = scr.selw + slot * NW * (size_t)scr.selseg;
                 auto each_entry = [&](auto &&fn) {
@@ -3027,23 +3029,59 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                             const double ae = apow(S, (int)ex);
                             w = ae * ae * (((kv >> 19) & 1u) ? S.bw : 1.0);       // a binomial group: (1 + a^(4n))^k
                         }
-                        skw[at] = (2u * a0 + (code & 1u)) | (((kv >> 16) & 7u) << 16);
+                        const uint32_t ci = 2u * a0 + (code & 1u);
+                        skw[at] = ci | (((kv >> 16) & 7u) << 16);
                         sww[at] = w;
+                        atomicOr(&hov[ci >> 5], 1u << (ci & 31u));     // the code occurs
                     });
                     __syncthreads();
                     for (uint32_t c = threadIdx.x; c < ncs; c += NT) hemp[c] = 0u;
+                    // F changes only at codes that occur: their ascending list
+                    // is what the search visits (the bitmap area doubles as the
+                    // block sums' partials, so the list sits in static memory)
+                    if (threadIdx.x == 0) {
+                        uint32_t m = 0;
+                        for (uint32_t wd = 0; wd < (ncodes + 31u) / 32u; ++wd)
+                            for (uint32_t bits = (uint32_t)hov[wd]; bits; bits &= bits - 1u) {
+                                if (m < 128u) S.plist[m] = (uint16_t)(32u * wd + (uint32_t)(__ffs(bits) - 1));
+                                ++m;
+                            }
+                        S.npres = m;
+                    }
+                    __syncthreads();
+                    for (uint32_t w = threadIdx.x; w < (ncodes + 31u) / 32u; w += NT) hov[w] = 0;
+                    __syncthreads();
                 }
                 auto Fdir = [&](uint32_t ximax) {
                     double f = 0.0;
                     each_entry([&](size_t at) { if ((skw[at] & 0xFFFFu) <= ximax) f += sww[at]; });
                     return block_sum(f, S.redA, S) * fsc;
                 };
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
-                    const double f = direct ? Fdir(mid) : Fsum(cmid, 0, false, nullptr);
-                    if (O + f > tgt) hi = mid;
-                    else { lo = mid + 1; Flo = f; }
+                if (direct && S.npres <= 128u) {
+                    const uint32_t np = S.npres;
+                    uint32_t a0 = 0, a1 = np;
+                    while (a0 < a1) {
+                        const uint32_t mid = (a0 + a1) >> 1;
+                        const double f = Fdir((uint32_t)S.plist[mid]);
+                        if (O + f > tgt) a1 = mid;
+                        else { a0 = mid + 1; Flo = f; }
+                    }
+                    lo = a0 < np ? (uint32_t)S.plist[a0] : ncodes;
+                } else if (direct) {
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        const double f = Fdir(mid);
+                        if (O + f > tgt) hi = mid;
+                        else { lo = mid + 1; Flo = f; }
+                    }
+                } else {
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        const uint32_t cmid = 2u * (cand[cb0 + (mid >> 1)] & 0xFFFFu) + (mid & 1u);
+                        const double f = Fsum(cmid, 0, false, nullptr);
+                        if (O + f > tgt) hi = mid;
+                        else { lo = mid + 1; Flo = f; }
+                    }
                 }
                 if (lo < ncodes) {
                     const uint32_t code = 2u * (cand[cb0 + (lo >> 1)] & 0xFFFFu) + (lo & 1u);
