@@ -366,6 +366,9 @@ void build_orbit(int n, int k, const SliceOps *ops, Orbit *orb) {
                 last[x] = s;
             }
         }
+        for (int t = 0; t < kMaxK; ++t) orb->dpos[s][t] = -1;
+        for (int b = 0; b < 2 * n; ++b)
+            if (pos[b] > n) orb->dpos[s][pos[b] - 1 - n] = (int8_t)b;
         for (int t = 0; t < k; ++t) if (bus[t] == 1 + n + t) bm |= 1u << t;
         orb->occ[s] = occ;
         orb->bus[s] = (uint8_t)bm;

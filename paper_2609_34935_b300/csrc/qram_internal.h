@@ -69,6 +69,7 @@ struct Orbit {
     uint32_t occ[kMaxT];             // positions holding an item
     uint8_t bus[kMaxT];              // bus slots holding their data qubit
     uint8_t fetched[kMaxT];          // data qubits already fetched
+    int8_t dpos[kMaxT][kMaxK];       // path-word position of data qubit t after slice s, -1 in the bus
     int ok;                          // 0: the schedule breaks the assumption (no lazy branches)
 };
 

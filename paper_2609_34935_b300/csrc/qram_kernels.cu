@@ -2874,7 +2874,11 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                 const uint32_t pre = block_scan_count(cnt, &tot, S);
                 if (base + tot > scr.ecap) { capfail = true; break; }
                 uint32_t r = base + pre;
-                const int E0 = cnt ? good_exposure(P, b, s1 - 1) : 0;
+                // (qubit: this epoch's nibble tables hold the exposure at s1 - 1)
+                const int E0 = !cnt ? 0
+                             : qubit ? S.etab[0][i & 15u] + S.etab[1][(i >> 4) & 15u] + S.etab[2][(i >> 8) & 15u] +
+                                           S.etab[3][(i >> 12) & 15u]
+                                     : good_exposure(P, b, s1 - 1);
                 const double w2 = cnt ? (uni ? w2u : col_w2(P, b) * k2) : 0.0;
                 const Ctx C = make_ctx(P.enc, n, P.mem, i);
                 for (uint32_t cw = 0; cw < ncw; ++cw) {
@@ -2898,13 +2902,10 @@ __device__ void run_one(const Params &P, Smem<NT> &S, uint32_t t, uint32_t *hist
                                 const uint32_t m = (uint32_t)ov(2 * n + 2 * t + 1, 4 * n + 2 * t, s1 - 1);
                                 const uint32_t ph = ((j >> t) ^ ((fm >> t) & (d >> t))) & 1u;
                                 rec[t] = kPFree | (ph ? kPPh : 0u) | (m << 16) | kPBus | (uint32_t)t;
-                                if ((bm >> t) & 1u) continue;
-                                for (uint32_t ww = P.orbit.occ[s1]; ww; ww &= ww - 1u) {
-                                    const int bb = __ffs(ww) - 1;
-                                    if (P.orbit.item[s1][bb] == 1 + n + t)
-                                        rec[t] = kPFree | (ph ? kPPh : 0u) | (m << 16) |
-                                                 (2u * path_node(i, n, bb >> 1) + (uint32_t)(bb & 1));
-                                }
+                                const int bb = P.orbit.dpos[s1][t];
+                                if (!((bm >> t) & 1u) && bb >= 0)
+                                    rec[t] = kPFree | (ph ? kPPh : 0u) | (m << 16) |
+                                             (2u * path_node(i, n, bb >> 1) + (uint32_t)(bb & 1));
                             }
                             pf_store(scr, cbase + r, rec);
                         }
