@@ -187,7 +187,7 @@ int qram_graph_create(qram_sim_t *sim, int mode, uint32_t ntraj, const double *g
 int qram_graph_launch(qram_graph_t *graph);
 void qram_graph_destroy(qram_graph_t *graph);
 
-/* Mixed persistent launch (spec batching pattern; no paper counterpart:
+/* Mixed persistent launch (batching of concurrent queries; no paper counterpart:
  * the paper runs one query at a time).  One work-stealing launch, captured
  * in a CUDA graph, over the trajectories of several problems of different
  * encodings, address widths n and data widths k: problem q contributes
