@@ -833,15 +833,15 @@ int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32
     if (rc) return rc;
     const uint32_t ecap = S->scr.ecap;
     const uint32_t W = ((1u << S->n) + 31u) >> 5;
-    const uint32_t ocap = ecap * 2 + ((uint32_t)S->D << S->k) + 16;
-    // one device block: gamma, dump buffers, outputs
+    // one device block: gamma, dump buffers; the output block is sized once the
+    // explicit entries are counted (each (column, tree state) group expands to
+    // every bus word, and so does each closed-form branch)
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
     const size_t o_g = take(8), o_cnt = take(8), o_scal = take(32), o_col = take(ecap * 4ull), o_bus = take(ecap * 4ull),
                  o_hash = take(ecap * 8ull), o_re = take(ecap * 8ull), o_im = take(ecap * 8ull), o_bb = take(W * 4ull),
-                 o_ref = take(8), o_res = take(sizeof(qram_result_t)), o_n = take(8), o_oa = take(ocap * 4ull),
-                 o_ob = take(ocap * 4ull), o_oh = take(ocap * 8ull), o_ore = take(ocap * 8ull), o_oim = take(ocap * 8ull);
-    char *b = nullptr;
+                 o_ref = take(8), o_res = take(sizeof(qram_result_t)), o_n = take(8);
+    char *b = nullptr, *ob = nullptr;
     if (!ok(cudaMalloc((void **)&b, off))) { cudaGetLastError(); return QRAM_E_OOM; }
     rc = QRAM_OK;
     do {
@@ -862,8 +862,17 @@ int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32
         if (!ok(cudaMemcpyAsync(&nin, b + o_cnt, 4, cudaMemcpyDeviceToHost, S->stream)) ||
             !ok(cudaStreamSynchronize(S->stream))) { rc = QRAM_E_CUDA; break; }
         if (nin > ecap) { rc = QRAM_E_CAP; break; }
-        if (!ok(launch_dump_finalize(P, nin, (uint32_t *)(b + o_n), ocap, (uint32_t *)(b + o_oa), (uint32_t *)(b + o_ob),
-                                     (uint64_t *)(b + o_oh), (double *)(b + o_ore), (double *)(b + o_oim), S->stream))) {
+        const uint64_t nw = S->enc == QRAM_QUBIT ? (uint64_t)1 << S->k : 1;
+        const uint64_t ocap64 = ((uint64_t)nin + (uint64_t)S->D) * nw + 16;
+        if (ocap64 > 0xFFFFFFFFull) { rc = QRAM_E_CAP; break; }
+        const uint32_t ocap = (uint32_t)ocap64;
+        size_t ooff = 0;
+        auto otake = [&](size_t bytes) { size_t o = ooff; ooff = align_up(ooff + bytes); return o; };
+        const size_t o_oa = otake(ocap * 4ull), o_ob = otake(ocap * 4ull), o_oh = otake(ocap * 8ull),
+                     o_ore = otake(ocap * 8ull), o_oim = otake(ocap * 8ull);
+        if (!ok(cudaMalloc((void **)&ob, ooff))) { cudaGetLastError(); rc = QRAM_E_OOM; break; }
+        if (!ok(launch_dump_finalize(P, nin, (uint32_t *)(b + o_n), ocap, (uint32_t *)(ob + o_oa), (uint32_t *)(ob + o_ob),
+                                     (uint64_t *)(ob + o_oh), (double *)(ob + o_ore), (double *)(ob + o_oim), S->stream))) {
             rc = QRAM_E_CUDA; break;
         }
         S->launches++;
@@ -873,11 +882,11 @@ int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32
         *count = nout;
         const uint32_t m = std::min(nout, std::min(cap, ocap));
         if (m) {
-            if (!ok(cudaMemcpyAsync(addr, b + o_oa, m * 4ull, cudaMemcpyDeviceToHost, S->stream)) ||
-                !ok(cudaMemcpyAsync(bus, b + o_ob, m * 4ull, cudaMemcpyDeviceToHost, S->stream)) ||
-                !ok(cudaMemcpyAsync(hash, b + o_oh, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
-                !ok(cudaMemcpyAsync(re, b + o_ore, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
-                !ok(cudaMemcpyAsync(im, b + o_oim, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
+            if (!ok(cudaMemcpyAsync(addr, ob + o_oa, m * 4ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(bus, ob + o_ob, m * 4ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(hash, ob + o_oh, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(re, ob + o_ore, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
+                !ok(cudaMemcpyAsync(im, ob + o_oim, m * 8ull, cudaMemcpyDeviceToHost, S->stream)) ||
                 !ok(cudaStreamSynchronize(S->stream))) { rc = QRAM_E_CUDA; break; }
         }
         qram_result_t R;
@@ -886,6 +895,7 @@ int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32
         if (nout > cap || nout > ocap) rc = QRAM_E_CAP;
     } while (0);
     cudaFree(b);
+    if (ob) cudaFree(ob);
     return rc;
 }
 
