@@ -140,7 +140,16 @@ int qram_sample_faults(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const do
  * gamma_lim = 1 - exp(-650 / ((2n + k)(T - 1))), i.e. 0.255 at n = 12, k = 4
  * and 0.20 at n = 14, k = 4 (the oracle renormalises every layer and has no
  * such limit).  A trajectory whose rate is outside [0, gamma_lim) reports
- * status QRAM_E_ARG; nothing is computed for it. */
+ * status QRAM_E_ARG; nothing is computed for it.
+ *
+ * Launch order (no paper counterpart).  With more trajectories than CTAs the
+ * run first sorts the trajectory indices by descending damping rate on the
+ * device (quarter-octave buckets; invalid rates last) and the persistent CTAs
+ * take them in that order, so that expensive trajectories do not start last.
+ * The permutation lives in stream-ordered memory (cudaMallocAsync on the
+ * simulator's stream, freed after the launch); if that allocation fails the
+ * run keeps index order.  Results are the same in either order.  Both runs
+ * and graphs (qram_graph_create) do this; qram_launch_count counts the sort. */
 int qram_run_pruned(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double *gamma,
                     qram_result_t *out);
 
@@ -173,7 +182,9 @@ int qram_set_launch_ctas(qram_sim_t *sim, uint32_t nctas);
 
 /* CUDA-graph capture of one persistent batched launch (pruned, mode 0, or
  * full, mode 1) of ntraj trajectories: the graph holds the work-counter reset
- * and the trajectory kernel.  The first trajectory index is read from
+ * (with more trajectories than CTAs also the launch-order sort, its memory
+ * allocated and freed inside the graph) and the trajectory kernel.  The
+ * first trajectory index is read from
  * traj0_dev (device, one uint64) when the graph runs, so one graph serves
  * successive batches; gamma (device, ntraj) and out (device, ntraj results)
  * are bound at capture.  Needs a damping-rate bound (qram_set_gamma_bound)

@@ -264,12 +264,44 @@ int bound_gamma(qram_sim *S, const double *gamma, uint32_t ntraj, double *gmax) 
     return QRAM_OK;
 }
 
-int launch(qram_sim *S, Params &P, uint32_t ntraj) {
-    if (!ok(cudaMemsetAsync(S->d_work, 0, sizeof(uint32_t), S->stream))) return QRAM_E_CUDA;
+// Enqueues one trajectory launch on st.  A pruned or full launch with more
+// trajectories than CTAs first sorts its trajectories by descending damping
+// rate (launch_order) into stream-ordered memory that is freed again after
+// the launch (inside a capture: memory nodes of the graph); without that
+// memory the trajectories go in index order.  *nk: kernels enqueued.
+int enqueue(qram_sim *S, Params &P, uint32_t ntraj, int grid, double gmax, cudaStream_t st, int *nk) {
+    *nk = 0;
+    uint32_t *perm = nullptr;
+    if ((P.mode == kPruned || P.mode == kFull) && ntraj > (uint32_t)grid && gmax > 0.0) {
+        if (ok(cudaMallocAsync((void **)&perm, (size_t)ntraj * sizeof(uint32_t), st))) {
+            if (!ok(launch_order(P.gamma, ntraj, gmax, P.gamma_lim, perm, st))) {
+                cudaFreeAsync(perm, st);
+                return QRAM_E_CUDA;
+            }
+            P.perm = perm;
+            ++*nk;
+        } else {
+            cudaGetLastError();
+            perm = nullptr;
+        }
+    }
+    int rc = QRAM_OK;
+    if (!ok(cudaMemsetAsync(S->d_work, 0, sizeof(uint32_t), st)) ||
+        !ok(launch_trajectories(P, grid, S->threads, S->dyn, st)))
+        rc = QRAM_E_CUDA;
+    else
+        ++*nk;
+    if (perm) cudaFreeAsync(perm, st);
+    P.perm = nullptr;
+    return rc;
+}
+
+int launch(qram_sim *S, Params &P, uint32_t ntraj, double gmax) {
     const int grid = (int)std::min<uint32_t>((uint32_t)S->slots, std::max<uint32_t>(ntraj, 1u));
-    if (!ok(launch_trajectories(P, grid, S->threads, S->dyn, S->stream))) return QRAM_E_CUDA;
-    S->launches++;
-    return QRAM_OK;
+    int nk = 0;
+    const int rc = enqueue(S, P, ntraj, grid, gmax, S->stream, &nk);
+    S->launches += (uint64_t)nk;
+    return rc;
 }
 
 int run_mode(qram_sim *S, int mode, uint64_t traj0, uint32_t ntraj, const double *gamma, qram_result_t *out) {
@@ -282,7 +314,7 @@ int run_mode(qram_sim *S, int mode, uint64_t traj0, uint32_t ntraj, const double
     if ((rc = ensure_scratch(S, gmax))) return rc;
     Params P = base_params(S);
     P.traj0 = traj0; P.ntraj = ntraj; P.gamma = gamma; P.mode = mode; P.out = out;
-    return launch(S, P, ntraj);
+    return launch(S, P, ntraj, gmax);
 }
 
 }  // namespace
@@ -538,7 +570,7 @@ int qram_sample_faults(qram_sim_t *S, uint64_t traj0, uint32_t ntraj, const doub
     Params P = base_params(S);
     P.traj0 = traj0; P.ntraj = ntraj; P.gamma = gamma; P.mode = kSampleOnly;
     P.o_cand = cand; P.o_ncand = ncand; P.o_badbits = bad_bits; P.o_bad = bad; P.o_ref = ref; P.o_cap = cap;
-    return launch(S, P, ntraj);
+    return launch(S, P, ntraj, gmax);
 }
 
 int qram_run_pruned(qram_sim_t *S, uint64_t traj0, uint32_t ntraj, const double *gamma, qram_result_t *out) {
@@ -562,6 +594,7 @@ struct qram_graph {
     qram_sim *sim = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int nk = 0;                      // kernels per replay
 };
 
 int qram_graph_create(qram_sim_t *S, int mode, uint32_t ntraj, const double *gamma, qram_result_t *out,
@@ -584,9 +617,7 @@ int qram_graph_create(qram_sim_t *S, int mode, uint32_t ntraj, const double *gam
     rc = QRAM_OK;
     if (!ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) rc = QRAM_E_CUDA;
     else {
-        if (!ok(cudaMemsetAsync(S->d_work, 0, sizeof(uint32_t), cap)) ||
-            !ok(launch_trajectories(P, grid, S->threads, S->dyn, cap)))
-            rc = QRAM_E_CUDA;
+        rc = enqueue(S, P, ntraj, grid, S->gamma_bound, cap, &G->nk);
         cudaGraph_t graph = nullptr;
         if (!ok(cudaStreamEndCapture(cap, &graph))) rc = QRAM_E_CUDA;
         G->graph = graph;
@@ -602,7 +633,7 @@ int qram_graph_launch(qram_graph_t *G) {
     if (!G || !G->exec) return QRAM_E_ARG;
     DeviceGuard g(G->sim->device);
     if (!ok(cudaGraphLaunch(G->exec, G->sim->stream))) return QRAM_E_CUDA;
-    G->sim->launches++;
+    G->sim->launches += (uint64_t)G->nk;
     return QRAM_OK;
 }
 
@@ -857,7 +888,7 @@ int qram_dump_state(qram_sim_t *S, int mode, uint64_t traj, double gamma, uint32
         P.dump.re = (double *)(b + o_re); P.dump.im = (double *)(b + o_im); P.dump.cap = ecap;
         P.dump.count = (uint32_t *)(b + o_cnt); P.dump.scal = (double *)(b + o_scal);
         P.o_badbits = (uint32_t *)(b + o_bb); P.o_ref = (int32_t *)(b + o_ref);
-        if ((rc = launch(S, P, 1))) break;
+        if ((rc = launch(S, P, 1, gamma))) break;
         uint32_t nin = 0;
         if (!ok(cudaMemcpyAsync(&nin, b + o_cnt, 4, cudaMemcpyDeviceToHost, S->stream)) ||
             !ok(cudaStreamSynchronize(S->stream))) { rc = QRAM_E_CUDA; break; }

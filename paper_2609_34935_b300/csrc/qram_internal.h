@@ -108,6 +108,7 @@ struct Params {
     const uint32_t *input_error;   // if non-null and nonzero at run time: every trajectory is QRAM_E_ARG
     const double *w2u;             // device scalar: |c|^2 (times 2^-k for qubits) when every column shares it, else 0
     const uint64_t *traj0_dev;     // if non-null, the first trajectory index is read here (graph replays)
+    const uint32_t *perm;          // if non-null: the w-th trajectory handed out is perm[w] (see launch_order)
     const uint32_t *col_of;        // qubit input over every address (D = 2^n): column of each address, else null
     double eps;                    // depolarizing strength per (slice, site)
     int eps_gamma;                 // nonzero: the strength of each trajectory is its damping rate
@@ -136,6 +137,12 @@ struct MultiParams {
 cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_trajectories_multi(const MultiParams &mp, int grid, int block, size_t smem, cudaStream_t s);
 int kernel_blocks_per_sm_multi(int threads, size_t dyn);
+// Launch order, longest first: perm = the indices 0 .. ntraj-1 sorted into
+// buckets of descending damping rate (quarter octaves below gmax; zero,
+// invalid and rejected rates last), one CTA, any order inside a bucket.
+constexpr int kOrderBuckets = 64;
+cudaError_t launch_order(const double *gamma, uint32_t ntraj, double gmax, double glim, uint32_t *perm,
+                         cudaStream_t s);
 cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s);
 cudaError_t launch_uniform_weight(const double *re, const double *im, int D, int qubit_k, double *out, cudaStream_t s);
 cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n, uint32_t cap,

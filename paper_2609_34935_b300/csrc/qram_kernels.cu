@@ -26,6 +26,7 @@
 //   6. final tree measurement and fidelity; the second Hadamard wall enters
 //      only through the Walsh coefficient (-1)^(bus . b_out).
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "qram_internal.h"
@@ -3250,7 +3251,10 @@ __global__ void __launch_bounds__(NT, MINB) traj_kernel(const __grid_constant__ 
     if (threadIdx.x == 0) S.part = reinterpret_cast<double *>(dyn_hist);
     __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) S.t = (int)atomicAdd(P.work, 1u);
+        if (threadIdx.x == 0) {
+            const uint32_t w = atomicAdd(P.work, 1u);
+            S.t = (int)((P.perm && w < P.ntraj) ? __ldg(P.perm + w) : w);   // longest first (launch_order)
+        }
         __syncthreads();
         const uint32_t t = (uint32_t)S.t;
         __syncthreads();
@@ -3418,6 +3422,61 @@ cudaError_t launch_uniform_weight(const double *re, const double *im, int D, int
 
 cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s) {
     fidelity_kernel<<<1, 256, 0, s>>>(res, ntraj, out2);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Launch order, longest first.  A trajectory's cost grows with its damping
+// rate (more jumps, larger explicit sets after them); handing the
+// trajectories out in descending rate keeps a launch from ending on a few
+// expensive trajectories that started last.  Results do not depend on it.
+// Bucket of a rate: quarter octaves below the key of gmax (the exponent and
+// two leading mantissa bits of a positive double grow with its value);
+// zero, invalid and rejected rates (nothing to evolve) go last.
+__device__ __forceinline__ uint32_t order_bucket(double g, int ktop, double glim) {
+    if (!(g > 0.0 && g < glim)) return kOrderBuckets - 1;
+    const int key = (int)((unsigned long long)__double_as_longlong(g) >> 50);
+    return (uint32_t)min(max(ktop - key, 0), kOrderBuckets - 2);
+}
+
+// Counting sort of the indices 0 .. n-1 by bucket into perm (one CTA;
+// shared-memory counts aggregated per warp over lanes of equal bucket).
+__global__ void __launch_bounds__(1024) order_kernel(const double *g, uint32_t n, int ktop, double glim,
+                                                     uint32_t *perm) {
+    __shared__ uint32_t cnt[kOrderBuckets];
+    const uint32_t lane = threadIdx.x & 31u;
+    if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint64_t b0 = 0; b0 < n; b0 += blockDim.x) {             // every warp runs every round
+        const uint64_t i = b0 + threadIdx.x;
+        const uint32_t b = i < n ? order_bucket(g[i], ktop, glim) : (uint32_t)kOrderBuckets;
+        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, b);
+        if (i < n && lane == (uint32_t)__ffs(grp) - 1u) atomicAdd(&cnt[b], (uint32_t)__popc(grp));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t sum = 0;
+        for (int b = 0; b < kOrderBuckets; ++b) { const uint32_t c = cnt[b]; cnt[b] = sum; sum += c; }
+    }
+    __syncthreads();
+    for (uint64_t b0 = 0; b0 < n; b0 += blockDim.x) {
+        const uint64_t i = b0 + threadIdx.x;
+        const uint32_t b = i < n ? order_bucket(g[i], ktop, glim) : (uint32_t)kOrderBuckets;
+        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, b);
+        const uint32_t lead = (uint32_t)__ffs(grp) - 1u;
+        uint32_t pos = 0;
+        if (i < n && lane == lead) pos = atomicAdd(&cnt[b], (uint32_t)__popc(grp));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, lead);
+        if (i < n) perm[pos + (uint32_t)__popc(grp & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_order(const double *gamma, uint32_t ntraj, double gmax, double glim, uint32_t *perm,
+                         cudaStream_t s) {
+    unsigned long long bits;
+    static_assert(sizeof(bits) == sizeof(gmax), "64-bit double");
+    memcpy(&bits, &gmax, sizeof(bits));
+    order_kernel<<<1, 1024, 0, s>>>(gamma, ntraj, (int)(bits >> 50), glim, perm);
     return cudaGetLastError();
 }
 
