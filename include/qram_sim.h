@@ -208,7 +208,10 @@ void qram_graph_destroy(qram_graph_t *graph);
  * ranges, so problems with uneven per-trajectory cost share the SMs; each
  * CTA runs Algorithm 1 for one trajectory of one problem at a time, and
  * every trajectory's result is bitwise the one that problem's own launch in
- * the same variant gives.
+ * the same variant gives.  With more trajectories than CTAs the graph first
+ * sorts all of them, longest first (see qram_run_pruned), by the key
+ * gamma * (2n + k)(T - 1) 2^n of their problem (expected jumps of a branch
+ * times the branches), in memory allocated and freed inside the graph.
  *   sims: 1 .. 16 simulators on one device, each with a damping-rate bound
  *         (qram_set_gamma_bound, else QRAM_E_STATE) and no depolarizing
  *         faults (else QRAM_E_ARG);

@@ -653,6 +653,7 @@ struct qram_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int threads = 0, grid = 0;
+    int nk = 0;                              // kernels per replay
 };
 
 int qram_batch_create(qram_sim_t *const *sims, uint32_t nsims, int mode, int threads, const uint64_t *traj0,
@@ -723,9 +724,32 @@ int qram_batch_create(qram_sim_t *const *sims, uint32_t nsims, int mode, int thr
         else {
             if (!ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) rc = QRAM_E_CUDA;
             else {
-                if (!ok(cudaMemsetAsync(B->d_work, 0, sizeof(uint32_t), cap)) ||
-                    !ok(launch_trajectories_multi(MP, B->grid, threads, dyn, cap)))
+                // launch order, longest first over all problems: the key of a
+                // trajectory is its rate times (2n + k)(T - 1) 2^n, the expected
+                // jumps of a branch times the branches of its problem
+                uint32_t *perm = nullptr;
+                if (total > (uint64_t)B->grid) {
+                    double scale[kMaxBatch], gm[kMaxBatch];
+                    for (uint32_t q = 0; q < nsims; ++q) {
+                        const qram_sim *S = sims[q];
+                        scale[q] = (double)(2 * S->n + S->k) * (double)(S->T - 1) * (double)(1u << S->n);
+                        gm[q] = S->gamma_bound;
+                    }
+                    if (ok(cudaMallocAsync((void **)&perm, (size_t)total * sizeof(uint32_t), cap))) {
+                        if (!ok(launch_order_multi(MP, scale, gm, perm, cap))) rc = QRAM_E_CUDA;
+                        else { MP.perm = perm; B->nk++; }
+                    } else {
+                        cudaGetLastError();
+                        perm = nullptr;
+                    }
+                }
+                if (!rc && (!ok(cudaMemsetAsync(B->d_work, 0, sizeof(uint32_t), cap)) ||
+                            !ok(launch_trajectories_multi(MP, B->grid, threads, dyn, cap))))
                     rc = QRAM_E_CUDA;
+                else if (!rc)
+                    B->nk++;
+                if (perm) cudaFreeAsync(perm, cap);
+                MP.perm = nullptr;
                 cudaGraph_t graph = nullptr;
                 if (!ok(cudaStreamEndCapture(cap, &graph))) rc = QRAM_E_CUDA;
                 B->graph = graph;
@@ -743,7 +767,7 @@ int qram_batch_launch(qram_batch_t *B) {
     if (!B || !B->exec) return QRAM_E_ARG;
     DeviceGuard g(B->device);
     if (!ok(cudaGraphLaunch(B->exec, B->stream))) return QRAM_E_CUDA;
-    for (qram_sim *S : B->sims) S->launches++;
+    for (qram_sim *S : B->sims) S->launches += (uint64_t)B->nk;
     return QRAM_OK;
 }
 

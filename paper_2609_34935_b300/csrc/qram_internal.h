@@ -131,6 +131,7 @@ struct MultiParams {
     uint32_t *work;               // work-stealing counter over all trajectories
     uint32_t nprob;
     uint32_t dyn_words;           // dynamic shared memory (32-bit words): the largest problem's
+    const uint32_t *perm;         // if non-null: the w-th trajectory handed out is perm[w] (launch_order_multi)
     uint32_t start[kMaxBatch + 1];
 };
 
@@ -143,6 +144,12 @@ int kernel_blocks_per_sm_multi(int threads, size_t dyn);
 constexpr int kOrderBuckets = 64;
 cudaError_t launch_order(const double *gamma, uint32_t ntraj, double gmax, double glim, uint32_t *perm,
                          cudaStream_t s);
+// The same over the concatenated ranges of a mixed launch (mp.probs on the
+// device, mp.start and mp.nprob set): the key of trajectory t of problem q is
+// gamma_t * scale[q] (a cost scale per problem), buckets below the largest
+// gmax[q] * scale[q].
+cudaError_t launch_order_multi(const MultiParams &mp, const double *scale, const double *gmax, uint32_t *perm,
+                               cudaStream_t s);
 cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s);
 cudaError_t launch_uniform_weight(const double *re, const double *im, int D, int qubit_k, double *out, cudaStream_t s);
 cudaError_t launch_dump_finalize(const Params &p, uint32_t n_in, uint32_t *out_n, uint32_t cap,

@@ -3281,7 +3281,10 @@ __global__ void __launch_bounds__(NT, MINB) traj_kernel_multi(const __grid_const
     const uint32_t total = MP.start[MP.nprob];
     int cur = -1;                                   // problem whose Params are in Ps (same in every thread)
     for (;;) {
-        if (threadIdx.x == 0) S.t = (int)atomicAdd(MP.work, 1u);
+        if (threadIdx.x == 0) {
+            const uint32_t w = atomicAdd(MP.work, 1u);
+            S.t = (int)((MP.perm && w < total) ? __ldg(MP.perm + w) : w);   // longest first (launch_order_multi)
+        }
         __syncthreads();
         const uint32_t t = (uint32_t)S.t;
         __syncthreads();
@@ -3430,26 +3433,56 @@ cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *ou
 // rate (more jumps, larger explicit sets after them); handing the
 // trajectories out in descending rate keeps a launch from ending on a few
 // expensive trajectories that started last.  Results do not depend on it.
-// Bucket of a rate: quarter octaves below the key of gmax (the exponent and
-// two leading mantissa bits of a positive double grow with its value);
-// zero, invalid and rejected rates (nothing to evolve) go last.
-__device__ __forceinline__ uint32_t order_bucket(double g, int ktop, double glim) {
-    if (!(g > 0.0 && g < glim)) return kOrderBuckets - 1;
-    const int key = (int)((unsigned long long)__double_as_longlong(g) >> 50);
-    return (uint32_t)min(max(ktop - key, 0), kOrderBuckets - 2);
+// Bucket of a positive cost key x: quarter octaves below the key of the
+// largest expected x (the exponent and two leading mantissa bits of a
+// positive double grow with its value), highest first; zero, invalid and
+// rejected rates (nothing to evolve) go to the last bucket.
+__device__ __forceinline__ int order_key(double x) {
+    return (int)((unsigned long long)__double_as_longlong(x) >> 50);
+}
+__device__ __forceinline__ uint32_t order_bucket(double x, int ktop) {
+    return (uint32_t)min(max(ktop - order_key(x), 0), kOrderBuckets - 2);
 }
 
+// one problem: the key is the rate itself
+struct RateKey {
+    const double *g;
+    int ktop;
+    double glim;
+    __device__ uint32_t operator()(uint32_t i) const {
+        const double x = g[i];
+        return (x > 0.0 && x < glim) ? order_bucket(x, ktop) : kOrderBuckets - 1u;
+    }
+};
+
+// several problems (mixed launch), index i of the concatenated ranges: the
+// key is the rate times the problem's scale (see launch_order_multi)
+struct MultiKey {
+    const Params *probs;
+    uint32_t nprob;
+    uint32_t start[kMaxBatch + 1];
+    double scale[kMaxBatch];
+    int ktop;
+    __device__ uint32_t operator()(uint32_t i) const {
+        uint32_t p = 0;
+        while (p + 1 < nprob && i >= start[p + 1]) ++p;
+        const double x = probs[p].gamma[i - start[p]];
+        return (x > 0.0 && x < probs[p].gamma_lim) ? order_bucket(x * scale[p], ktop) : kOrderBuckets - 1u;
+    }
+};
+
 // Counting sort of the indices 0 .. n-1 by bucket into perm (one CTA;
-// shared-memory counts aggregated per warp over lanes of equal bucket).
-__global__ void __launch_bounds__(1024) order_kernel(const double *g, uint32_t n, int ktop, double glim,
-                                                     uint32_t *perm) {
+// shared-memory counts aggregated per warp over lanes of equal bucket);
+// any order inside a bucket.
+template <class Key>
+__global__ void __launch_bounds__(1024) order_kernel(const __grid_constant__ Key key, uint32_t n, uint32_t *perm) {
     __shared__ uint32_t cnt[kOrderBuckets];
     const uint32_t lane = threadIdx.x & 31u;
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0u;
     __syncthreads();
     for (uint64_t b0 = 0; b0 < n; b0 += blockDim.x) {             // every warp runs every round
         const uint64_t i = b0 + threadIdx.x;
-        const uint32_t b = i < n ? order_bucket(g[i], ktop, glim) : (uint32_t)kOrderBuckets;
+        const uint32_t b = i < n ? key((uint32_t)i) : (uint32_t)kOrderBuckets;
         const uint32_t grp = __match_any_sync(0xFFFFFFFFu, b);
         if (i < n && lane == (uint32_t)__ffs(grp) - 1u) atomicAdd(&cnt[b], (uint32_t)__popc(grp));
     }
@@ -3461,7 +3494,7 @@ __global__ void __launch_bounds__(1024) order_kernel(const double *g, uint32_t n
     __syncthreads();
     for (uint64_t b0 = 0; b0 < n; b0 += blockDim.x) {
         const uint64_t i = b0 + threadIdx.x;
-        const uint32_t b = i < n ? order_bucket(g[i], ktop, glim) : (uint32_t)kOrderBuckets;
+        const uint32_t b = i < n ? key((uint32_t)i) : (uint32_t)kOrderBuckets;
         const uint32_t grp = __match_any_sync(0xFFFFFFFFu, b);
         const uint32_t lead = (uint32_t)__ffs(grp) - 1u;
         uint32_t pos = 0;
@@ -3471,12 +3504,37 @@ __global__ void __launch_bounds__(1024) order_kernel(const double *g, uint32_t n
     }
 }
 
+static int host_order_key(double x) {
+    unsigned long long bits;
+    static_assert(sizeof(bits) == sizeof(x), "64-bit double");
+    memcpy(&bits, &x, sizeof(bits));
+    return (int)(bits >> 50);
+}
+
 cudaError_t launch_order(const double *gamma, uint32_t ntraj, double gmax, double glim, uint32_t *perm,
                          cudaStream_t s) {
-    unsigned long long bits;
-    static_assert(sizeof(bits) == sizeof(gmax), "64-bit double");
-    memcpy(&bits, &gmax, sizeof(bits));
-    order_kernel<<<1, 1024, 0, s>>>(gamma, ntraj, (int)(bits >> 50), glim, perm);
+    RateKey key;
+    key.g = gamma;
+    key.ktop = host_order_key(gmax);
+    key.glim = glim;
+    order_kernel<RateKey><<<1, 1024, 0, s>>>(key, ntraj, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_multi(const MultiParams &mp, const double *scale, const double *gmax, uint32_t *perm,
+                               cudaStream_t s) {
+    MultiKey key;
+    memset(&key, 0, sizeof(key));
+    key.probs = mp.probs;
+    key.nprob = mp.nprob;
+    double top = 0.0;
+    for (uint32_t q = 0; q < mp.nprob && q < (uint32_t)kMaxBatch; ++q) {
+        key.scale[q] = scale[q];
+        top = top > gmax[q] * scale[q] ? top : gmax[q] * scale[q];
+    }
+    for (uint32_t q = 0; q <= mp.nprob && q <= (uint32_t)kMaxBatch; ++q) key.start[q] = mp.start[q];
+    key.ktop = host_order_key(top);
+    order_kernel<MultiKey><<<1, 1024, 0, s>>>(key, mp.start[mp.nprob], perm);
     return cudaGetLastError();
 }
 
