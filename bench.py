@@ -279,7 +279,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # > 126 MB L2
     base = trajectory_base(rank)                                          # disjoint trajectory ranges
     traj0 = torch.zeros(1, dtype=torch.int64, device=dev)
-    graph = sim.graph("pruned", gam, out, traj0)          # per step: the launch-order sort, one persistent launch
+    graph = sim.graph("pruned", gam, out, traj0)          # per step: launch-order score and sort, one persistent launch
 
     def step(j):
         traj0.fill_(base + j * NTRAJ)
@@ -478,7 +478,7 @@ def main():
                      "ms_per_step": 1e3 * t_full_step, "steps": full_steps,
                      "speedup_pruned_over_full": t_full_step / (t_dev / args.steps),
                      "trajectories": f"the same {NTRAJ} trajectories per step as the pruned steps (same indices, "
-                                     "damping rates and noise histories), one graph per step (launch-order sort, one persistent launch)",
+                                     "damping rates and noise histories), one graph per step (launch-order score and sort, one persistent launch)",
                      "max_abs_fidelity_diff_pruned_vs_full": agree, "integer_outputs_equal": same_int},
             "per_gamma_decade": per_decade,
             "eps_eq_gamma_per_decade": {"note": "depolarizing faults of strength eps = gamma on top of the damping "

@@ -143,13 +143,18 @@ int qram_sample_faults(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const do
  * status QRAM_E_ARG; nothing is computed for it.
  *
  * Launch order (no paper counterpart).  With more trajectories than CTAs the
- * run first sorts the trajectory indices by descending damping rate on the
- * device (quarter-octave buckets; invalid rates last) and the persistent CTAs
- * take them in that order, so that expensive trajectories do not start last.
- * The permutation lives in stream-ordered memory (cudaMallocAsync on the
- * simulator's stream, freed after the launch); if that allocation fails the
- * run keeps index order.  Results are the same in either order.  Both runs
- * and graphs (qram_graph_create) do this; qram_launch_count counts the sort. */
+ * run first scores every trajectory's expected cost on the device (its damping
+ * candidates of Sec. IV, regenerated from the same fault stream, each weighted
+ * by 2^(n - 2L) (T - s) for a candidate at slice s on layer L: the branches a
+ * jump there would leave explicit, times its probability, times the slices
+ * left), sorts the indices into quarter-octave buckets of descending score
+ * (rejected rates last), and the persistent CTAs take them in that order, so
+ * that expensive trajectories do not start last.  Scores and permutation live
+ * in stream-ordered memory (cudaMallocAsync on the simulator's stream, freed
+ * after the launch); if that allocation fails the run keeps index order.
+ * Results are the same in either order.  Both runs and graphs
+ * (qram_graph_create) do this; qram_launch_count counts the score and sort
+ * kernels. */
 int qram_run_pruned(qram_sim_t *sim, uint64_t traj0, uint32_t ntraj, const double *gamma,
                     qram_result_t *out);
 
@@ -182,8 +187,9 @@ int qram_set_launch_ctas(qram_sim_t *sim, uint32_t nctas);
 
 /* CUDA-graph capture of one persistent batched launch (pruned, mode 0, or
  * full, mode 1) of ntraj trajectories: the graph holds the work-counter reset
- * (with more trajectories than CTAs also the launch-order sort, its memory
- * allocated and freed inside the graph) and the trajectory kernel.  The
+ * (with more trajectories than CTAs also the launch-order score and sort,
+ * their memory allocated and freed inside the graph) and the trajectory
+ * kernel.  The
  * first trajectory index is read from
  * traj0_dev (device, one uint64) when the graph runs, so one graph serves
  * successive batches; gamma (device, ntraj) and out (device, ntraj results)
@@ -209,9 +215,9 @@ void qram_graph_destroy(qram_graph_t *graph);
  * CTA runs Algorithm 1 for one trajectory of one problem at a time, and
  * every trajectory's result is bitwise the one that problem's own launch in
  * the same variant gives.  With more trajectories than CTAs the graph first
- * sorts all of them, longest first (see qram_run_pruned), by the key
- * gamma * (2n + k)(T - 1) 2^n of their problem (expected jumps of a branch
- * times the branches), in memory allocated and freed inside the graph.
+ * sorts all of them, longest first, by the cost score of qram_run_pruned
+ * (comparable across problems), in memory allocated and freed inside the
+ * graph.
  *   sims: 1 .. 16 simulators on one device, each with a damping-rate bound
  *         (qram_set_gamma_bound, else QRAM_E_STATE) and no depolarizing
  *         faults (else QRAM_E_ARG);

@@ -265,21 +265,22 @@ int bound_gamma(qram_sim *S, const double *gamma, uint32_t ntraj, double *gmax) 
 }
 
 // Enqueues one trajectory launch on st.  A pruned or full launch with more
-// trajectories than CTAs first sorts its trajectories by descending damping
-// rate (launch_order) into stream-ordered memory that is freed again after
-// the launch (inside a capture: memory nodes of the graph); without that
-// memory the trajectories go in index order.  *nk: kernels enqueued.
+// trajectories than CTAs first scores and sorts its trajectories by expected
+// cost, longest first (launch_order), in stream-ordered memory that is freed
+// again after the launch (inside a capture: memory nodes of the graph);
+// without that memory the trajectories go in index order.  *nk: kernels
+// enqueued.
 int enqueue(qram_sim *S, Params &P, uint32_t ntraj, int grid, double gmax, cudaStream_t st, int *nk) {
     *nk = 0;
     uint32_t *perm = nullptr;
     if ((P.mode == kPruned || P.mode == kFull) && ntraj > (uint32_t)grid && gmax > 0.0) {
-        if (ok(cudaMallocAsync((void **)&perm, (size_t)ntraj * sizeof(uint32_t), st))) {
-            if (!ok(launch_order(P.gamma, ntraj, gmax, P.gamma_lim, perm, st))) {
+        if (ok(cudaMallocAsync((void **)&perm, (size_t)ntraj * (sizeof(uint32_t) + sizeof(float)), st))) {
+            if (!ok(launch_order(P, ntraj, perm, reinterpret_cast<float *>(perm + ntraj), st))) {
                 cudaFreeAsync(perm, st);
                 return QRAM_E_CUDA;
             }
             P.perm = perm;
-            ++*nk;
+            *nk += 2;
         } else {
             cudaGetLastError();
             perm = nullptr;
@@ -724,20 +725,19 @@ int qram_batch_create(qram_sim_t *const *sims, uint32_t nsims, int mode, int thr
         else {
             if (!ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) rc = QRAM_E_CUDA;
             else {
-                // launch order, longest first over all problems: the key of a
-                // trajectory is its rate times (2n + k)(T - 1) 2^n, the expected
-                // jumps of a branch times the branches of its problem
+                // launch order, longest first over all problems (the cost
+                // score of launch_order, comparable across problems)
                 uint32_t *perm = nullptr;
                 if (total > (uint64_t)B->grid) {
-                    double scale[kMaxBatch], gm[kMaxBatch];
+                    int nmax = 0, tmax = 0;
                     for (uint32_t q = 0; q < nsims; ++q) {
-                        const qram_sim *S = sims[q];
-                        scale[q] = (double)(2 * S->n + S->k) * (double)(S->T - 1) * (double)(1u << S->n);
-                        gm[q] = S->gamma_bound;
+                        nmax = std::max(nmax, sims[q]->n);
+                        tmax = std::max(tmax, sims[q]->T);
                     }
-                    if (ok(cudaMallocAsync((void **)&perm, (size_t)total * sizeof(uint32_t), cap))) {
-                        if (!ok(launch_order_multi(MP, scale, gm, perm, cap))) rc = QRAM_E_CUDA;
-                        else { MP.perm = perm; B->nk++; }
+                    if (ok(cudaMallocAsync((void **)&perm, (size_t)total * (sizeof(uint32_t) + sizeof(float)), cap))) {
+                        if (!ok(launch_order_multi(MP, nmax, tmax, perm, reinterpret_cast<float *>(perm + total), cap)))
+                            rc = QRAM_E_CUDA;
+                        else { MP.perm = perm; B->nk += 2; }
                     } else {
                         cudaGetLastError();
                         perm = nullptr;

@@ -138,17 +138,16 @@ struct MultiParams {
 cudaError_t launch_trajectories(const Params &p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_trajectories_multi(const MultiParams &mp, int grid, int block, size_t smem, cudaStream_t s);
 int kernel_blocks_per_sm_multi(int threads, size_t dyn);
-// Launch order, longest first: perm = the indices 0 .. ntraj-1 sorted into
-// buckets of descending damping rate (quarter octaves below gmax; zero,
-// invalid and rejected rates last), one CTA, any order inside a bucket.
+// Launch order, longest first: score = a cost score per trajectory (its
+// damping candidates, regenerated, weighted by the branches a jump there
+// would leave explicit), then perm = the indices 0 .. ntraj-1 sorted into
+// buckets of descending score (rejected rates last), any order inside a
+// bucket.  perm and score: device, ntraj entries each.
 constexpr int kOrderBuckets = 64;
-cudaError_t launch_order(const double *gamma, uint32_t ntraj, double gmax, double glim, uint32_t *perm,
-                         cudaStream_t s);
+cudaError_t launch_order(const Params &p, uint32_t ntraj, uint32_t *perm, float *score, cudaStream_t s);
 // The same over the concatenated ranges of a mixed launch (mp.probs on the
-// device, mp.start and mp.nprob set): the key of trajectory t of problem q is
-// gamma_t * scale[q] (a cost scale per problem), buckets below the largest
-// gmax[q] * scale[q].
-cudaError_t launch_order_multi(const MultiParams &mp, const double *scale, const double *gmax, uint32_t *perm,
+// device, mp.start and mp.nprob set); nmax, tmax: the largest n and T.
+cudaError_t launch_order_multi(const MultiParams &mp, int nmax, int tmax, uint32_t *perm, float *score,
                                cudaStream_t s);
 cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *out2, cudaStream_t s);
 cudaError_t launch_uniform_weight(const double *re, const double *im, int D, int qubit_k, double *out, cudaStream_t s);

@@ -25,6 +25,7 @@
 //      prefix first) by a deterministic block-wide descent;
 //   6. final tree measurement and fidelity; the second Hadamard wall enters
 //      only through the Walsh coefficient (-1)^(bus . b_out).
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <cuda_runtime.h>
@@ -3429,45 +3430,103 @@ cudaError_t launch_fidelity(const qram_result_t *res, uint32_t ntraj, double *ou
 }
 
 // ---------------------------------------------------------------------------
-// Launch order, longest first.  A trajectory's cost grows with its damping
-// rate (more jumps, larger explicit sets after them); handing the
-// trajectories out in descending rate keeps a launch from ending on a few
-// expensive trajectories that started last.  Results do not depend on it.
-// Bucket of a positive cost key x: quarter octaves below the key of the
-// largest expected x (the exponent and two leading mantissa bits of a
-// positive double grow with its value), highest first; zero, invalid and
-// rejected rates (nothing to evolve) go to the last bucket.
+// Launch order, longest first.  Trajectories differ in cost by orders of
+// magnitude: one whose first jump hits a router near the root while the
+// address is loaded keeps thousands of branches explicit for most of the
+// schedule.  Handing the expensive ones out first keeps a launch from ending
+// on one of them started late.  Results do not depend on the order.
+//
+// Cost score of a trajectory: its damping candidates (the same fault stream
+// as the trajectory kernel, regenerated) weighted by what a jump there would
+// leave explicit, sum over candidates (s, q) of 2^(n - 2L) (T - s), L the
+// layer of q: a jump on a layer-L router takes about 2^(n-L) branches out
+// of the closed form with probability about 2^-L, for the T - s slices
+// left.  Zero without candidates; -1 for a rate the trajectory rejects.
+__device__ float traj_score(const Params &P, uint32_t t, uint64_t *gq, uint32_t lane) {
+    const double gamma = P.gamma[t];
+    if (!(gamma >= 0.0 && gamma < 1.0 && gamma < P.gamma_lim)) return -1.0f;
+    const uint64_t thr = (uint64_t)__double2ull_rz(gamma * 18446744073709551616.0);
+    if (thr == 0) return 0.0f;
+    __syncwarp();
+    if (lane == 0) {
+        gq[0] = 0ull - thr;
+        for (int m = 0; m + 1 < kGapBits; ++m) gq[m + 1] = __umul64hi(gq[m], gq[m]);
+    }
+    __syncwarp();
+    const uint64_t traj = (P.traj0_dev ? *P.traj0_dev : P.traj0) + t;
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    const uint32_t tl = (uint32_t)traj, th = (uint32_t)(traj >> 32);
+    const uint32_t M = 2u * (uint32_t)P.nodes, X = (uint32_t)(P.T - 1) * M;
+    const uint32_t nblk = (X + kGapBlock - 1) / kGapBlock;
+    float sc = 0.0f;
+    for (uint32_t g = lane; g < nblk; g += 32) {
+        uint32_t pos = g * kGapBlock;
+        const uint32_t end = min(pos + kGapBlock, X);
+        uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+        for (uint32_t r = 0;; ++r) {
+            if ((r & 1u) == 0) {
+                o0 = g; o1 = (r >> 1) | (1u << 24); o2 = tl; o3 = th;
+                philox(o0, o1, o2, o3, k0, k1);
+            }
+            const uint64_t u = (r & 1u) ? ((uint64_t)o2 | ((uint64_t)o3 << 32)) : ((uint64_t)o0 | ((uint64_t)o1 << 32));
+            uint64_t acc = ~0ull;
+            uint32_t G = 0;
+            for (int m = kGapBits - 1; m >= 0; --m) {
+                const uint64_t v = __umul64hi(acc, gq[m]);
+                if (v > u) { acc = v; G += 1u << m; }
+            }
+            if (G >= end - pos) break;
+            pos += G;
+            const int s = 1 + (int)(pos / M), L = layer_of((pos % M) >> 1);
+            sc += ldexpf((float)(P.T - s), P.n - 2 * L);
+            ++pos;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xFFFFFFFFu, sc, o);
+    return sc;
+}
+
+// one warp per trajectory: score[i] of trajectory i of one problem (Params
+// by value) or of the concatenated ranges of a mixed launch (table on the
+// device)
+__global__ void __launch_bounds__(256) score_kernel(const __grid_constant__ Params P, uint32_t n, float *score) {
+    __shared__ uint64_t gq[8][kGapBits];
+    const uint32_t lane = threadIdx.x & 31u, wi = threadIdx.x >> 5;
+    for (uint64_t i = (uint64_t)blockIdx.x * 8 + wi; i < n; i += (uint64_t)gridDim.x * 8) {
+        const float sc = traj_score(P, (uint32_t)i, gq[wi], lane);
+        if (lane == 0) score[i] = sc;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256) score_kernel_multi(const __grid_constant__ MultiParams MP, float *score) {
+    __shared__ uint64_t gq[8][kGapBits];
+    const uint32_t lane = threadIdx.x & 31u, wi = threadIdx.x >> 5;
+    const uint32_t n = MP.start[MP.nprob];
+    for (uint64_t i = (uint64_t)blockIdx.x * 8 + wi; i < n; i += (uint64_t)gridDim.x * 8) {
+        uint32_t p = 0;
+        while (p + 1 < MP.nprob && i >= MP.start[p + 1]) ++p;
+        const float sc = traj_score(MP.probs[p], (uint32_t)i - MP.start[p], gq[wi], lane);
+        if (lane == 0) score[i] = sc;
+        __syncwarp();
+    }
+}
+
+// Bucket of a score: quarter octaves below the key of an upper estimate
+// (the exponent and two leading mantissa bits of a positive double grow
+// with its value), highest first; no candidates next to last; rejected
+// rates (nothing to evolve) last.
 __device__ __forceinline__ int order_key(double x) {
     return (int)((unsigned long long)__double_as_longlong(x) >> 50);
 }
-__device__ __forceinline__ uint32_t order_bucket(double x, int ktop) {
-    return (uint32_t)min(max(ktop - order_key(x), 0), kOrderBuckets - 2);
-}
-
-// one problem: the key is the rate itself
-struct RateKey {
-    const double *g;
-    int ktop;
-    double glim;
-    __device__ uint32_t operator()(uint32_t i) const {
-        const double x = g[i];
-        return (x > 0.0 && x < glim) ? order_bucket(x, ktop) : kOrderBuckets - 1u;
-    }
-};
-
-// several problems (mixed launch), index i of the concatenated ranges: the
-// key is the rate times the problem's scale (see launch_order_multi)
-struct MultiKey {
-    const Params *probs;
-    uint32_t nprob;
-    uint32_t start[kMaxBatch + 1];
-    double scale[kMaxBatch];
+struct ScoreKey {
+    const float *score;
     int ktop;
     __device__ uint32_t operator()(uint32_t i) const {
-        uint32_t p = 0;
-        while (p + 1 < nprob && i >= start[p + 1]) ++p;
-        const double x = probs[p].gamma[i - start[p]];
-        return (x > 0.0 && x < probs[p].gamma_lim) ? order_bucket(x * scale[p], ktop) : kOrderBuckets - 1u;
+        const float x = score[i];
+        if (x > 0.0f) return (uint32_t)min(max(ktop - order_key((double)x), 0), kOrderBuckets - 2);
+        return x == 0.0f ? kOrderBuckets - 2u : kOrderBuckets - 1u;
     }
 };
 
@@ -3504,37 +3563,40 @@ __global__ void __launch_bounds__(1024) order_kernel(const __grid_constant__ Key
     }
 }
 
-static int host_order_key(double x) {
+// top of the score buckets: 32 candidates on the root router at slice 0
+static int host_score_top(int n, int T) {
+    const double x = 32.0 * (double)T * (double)(1u << n);
     unsigned long long bits;
     static_assert(sizeof(bits) == sizeof(x), "64-bit double");
     memcpy(&bits, &x, sizeof(bits));
     return (int)(bits >> 50);
 }
 
-cudaError_t launch_order(const double *gamma, uint32_t ntraj, double gmax, double glim, uint32_t *perm,
-                         cudaStream_t s) {
-    RateKey key;
-    key.g = gamma;
-    key.ktop = host_order_key(gmax);
-    key.glim = glim;
-    order_kernel<RateKey><<<1, 1024, 0, s>>>(key, ntraj, perm);
+static int score_grid(uint32_t n) {
+    return (int)std::min<uint64_t>(((uint64_t)n + 7) / 8, 148ull * 16);
+}
+
+cudaError_t launch_order(const Params &p, uint32_t ntraj, uint32_t *perm, float *score, cudaStream_t s) {
+    score_kernel<<<score_grid(ntraj), 256, 0, s>>>(p, ntraj, score);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ScoreKey key;
+    key.score = score;
+    key.ktop = host_score_top(p.n, p.T);
+    order_kernel<ScoreKey><<<1, 1024, 0, s>>>(key, ntraj, perm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_order_multi(const MultiParams &mp, const double *scale, const double *gmax, uint32_t *perm,
+cudaError_t launch_order_multi(const MultiParams &mp, int nmax, int tmax, uint32_t *perm, float *score,
                                cudaStream_t s) {
-    MultiKey key;
-    memset(&key, 0, sizeof(key));
-    key.probs = mp.probs;
-    key.nprob = mp.nprob;
-    double top = 0.0;
-    for (uint32_t q = 0; q < mp.nprob && q < (uint32_t)kMaxBatch; ++q) {
-        key.scale[q] = scale[q];
-        top = top > gmax[q] * scale[q] ? top : gmax[q] * scale[q];
-    }
-    for (uint32_t q = 0; q <= mp.nprob && q <= (uint32_t)kMaxBatch; ++q) key.start[q] = mp.start[q];
-    key.ktop = host_order_key(top);
-    order_kernel<MultiKey><<<1, 1024, 0, s>>>(key, mp.start[mp.nprob], perm);
+    const uint32_t n = mp.start[mp.nprob];
+    score_kernel_multi<<<score_grid(n), 256, 0, s>>>(mp, score);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ScoreKey key;
+    key.score = score;
+    key.ktop = host_score_top(nmax, tmax);
+    order_kernel<ScoreKey><<<1, 1024, 0, s>>>(key, n, perm);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,7 @@
 """Launch order.  A pruned or full launch with more trajectories than CTAs
-hands its trajectories out in descending damping rate (a counting sort on the
-device, then work stealing over that permutation); results must not depend on
-it.  Each launch is compared bitwise, record by record, with the same
+hands its trajectories out longest first (a cost score per trajectory from
+its regenerated damping candidates, a counting sort on the device, then work
+stealing over that permutation); results must not depend on it.  Each launch is compared bitwise, record by record, with the same
 trajectories run in chunks no larger than the grid (index order, no sort),
 eagerly and as a replayed graph, with zero, invalid and repeated rates mixed
 in.  Every record must be written exactly once (the output is pre-filled with
@@ -51,7 +51,7 @@ def test_sorted_launch_equals_index_order(enc, n, k, mode):
     out = torch.full((nt, 48), 0xCD, dtype=torch.uint8, device="cuda:0")
     l0 = sim.launch_count
     sim.run(mode, t0, gt, out)
-    assert sim.launch_count - l0 == 2                 # the sort, then the trajectories
+    assert sim.launch_count - l0 == 3                 # the scores, the sort, then the trajectories
     got = out.cpu().numpy()
     assert not np.any(np.all(got == 0xCD, axis=1))    # every record written
     assert np.array_equal(got, want)
@@ -65,7 +65,7 @@ def test_sorted_launch_equals_index_order(enc, n, k, mode):
         l0 = sim.launch_count
         graph()
         torch.cuda.synchronize()
-        assert sim.launch_count - l0 == 2
+        assert sim.launch_count - l0 == 3
         assert np.array_equal(out.cpu().numpy(), want)
     graph.close()
 
