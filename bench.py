@@ -245,7 +245,12 @@ def main():
                     help="the other workload configurations (qutrit n=3, qubit n=6, qutrit n=10): throughput, "
                          "work and measured peaks")
     ap.add_argument("--only", type=int, default=None, help="with --configs: run only this configuration index")
+    ap.add_argument("--variants", action="store_true",
+                    help="pruned throughput of each launch variant (128/256/512 threads per CTA) over encoding, "
+                         "n = 4..14, k = 1, 2, 4 and gamma 3e-4, 3e-3, each launch filling the device")
     args = ap.parse_args()
+    if args.variants:
+        return run_variants(args)
     if args.profile_case is not None or args.profile_mix:
         return run_profile_case(args.profile_case)
     if args.configs:
@@ -709,6 +714,50 @@ def run_profile_case(gamma):
                       "jumps": float(r["jumps"].mean()), "work": w}))
     sim.close()
     return 0
+
+
+def run_variants(args):
+    """Launch-variant table: for each (encoding, n, k, gamma) the pruned
+    trajectories/s of the 128-, 256- and 512-thread variants, data-loading
+    input, one launch over the whole device (best of three after one
+    untimed), CUDA events on the simulator's stream."""
+    import torch
+    from paper_2609_34935_b300 import QramSim
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    rows = []
+    for enc in (W.QUTRIT, W.QUBIT):
+        for n in (4, 6, 8, 10, 12, 14):
+            for k in (1, 2, 4):
+                p = W.data_loading(enc, n, k, seed=7000 + n * 10 + k)
+                sim = QramSim(p, seed=7000 + n, device=local)
+                for gamma in (3e-4, 3e-3):
+                    nt = 6000 if n <= 8 else 3000
+                    g = torch.full((nt,), gamma, dtype=torch.float64, device=f"cuda:{local}")
+                    row = {"encoding": "qubit" if enc == W.QUBIT else "qutrit", "n": n, "k": k, "gamma": gamma,
+                           "trajectories": nt}
+                    for th in (128, 256, 512):
+                        sim.set_variant(th)
+                        res = sim.run("pruned", 0, g)
+                        sim.sync()
+                        best = float("inf")
+                        for _ in range(3):
+                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            sim.sync()
+                            e0.record(sim.stream)
+                            sim.run("pruned", 0, g, out=res)
+                            e1.record(sim.stream)
+                            e1.synchronize()
+                            best = min(best, e0.elapsed_time(e1))
+                        row[f"traj_per_s_{th}"] = nt / (best * 1e-3)
+                        row["status_ok"] = bool(np.all(QramSim.results(res)["status"] == 0)) and row.get("status_ok", True)
+                    row["best_threads"] = max((128, 256, 512), key=lambda t: row[f"traj_per_s_{t}"])
+                    rows.append(row)
+                sim.close()
+    print(json.dumps({"metric": "pruned trajectories/s per launch variant", "unit": "trajectories/s",
+                      "data": "synthetic", "rows": rows}), flush=True)
 
 
 def run_serving(args):
