@@ -248,7 +248,12 @@ def main():
     ap.add_argument("--variants", action="store_true",
                     help="pruned throughput of each launch variant (128/256/512 threads per CTA) over encoding, "
                          "n = 4..14, k = 1, 2, 4 and gamma 3e-4, 3e-3, each launch filling the device")
+    ap.add_argument("--rate-scan", action="store_true",
+                    help="pruned and full over n = 4..12 and gamma 0..1e-2 (qubit, k=3, the shape of Tab. V), "
+                         "damping only")
     args = ap.parse_args()
+    if args.rate_scan:
+        return run_rate_scan(args)
     if args.variants:
         return run_variants(args)
     if args.profile_case is not None or args.profile_mix:
@@ -758,6 +763,62 @@ def run_variants(args):
                 sim.close()
     print(json.dumps({"metric": "pruned trajectories/s per launch variant", "unit": "trajectories/s",
                       "data": "synthetic", "rows": rows}), flush=True)
+
+
+def run_rate_scan(args):
+    """Pruned against full over address width and damping rate, in the shape
+    of the paper's performance table (Tab. V: qubit encoding, k = 3,
+    data-loading input, n = 4..12), damping only.  Per point: 4000
+    trajectories, both modes on the same indices and rates, each mode on its
+    fastest launch variant (one untimed launch, then one timed with CUDA
+    events); the evolved fraction is the explicit components of the pruned
+    mode over those of the full mode."""
+    import torch
+    from paper_2609_34935_b300 import QramSim
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    nt = 4000
+    rows = []
+    for n in (4, 6, 8, 10, 12):
+        p = W.data_loading(W.QUBIT, n, 3, seed=6000 + n)
+        sim = QramSim(p, seed=6000 + n, device=local)
+        sim.set_gamma_bound(1e-2)
+        g = torch.empty(nt, dtype=torch.float64, device=f"cuda:{local}")
+        out = torch.empty((nt, 48), dtype=torch.uint8, device=f"cuda:{local}")
+        for gamma in (0.0, 1e-5, 1e-4, 1e-3, 1e-2):
+            g.fill_(gamma)
+            row = {"n": n, "k": 3, "gamma": gamma, "trajectories": nt}
+            res = {}
+            for mode in ("pruned", "full"):
+                best, bth = float("inf"), 0
+                for th in (128, 256, 512):
+                    sim.set_variant(th)
+                    sim.run(mode, 0, g, out=out)
+                    sim.sync()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(sim.stream)
+                    sim.run(mode, 0, g, out=out)
+                    e1.record(sim.stream)
+                    e1.synchronize()
+                    if e0.elapsed_time(e1) < best:
+                        best, bth = e0.elapsed_time(e1), th
+                res[mode] = QramSim.results(out)
+                row[f"{mode}_traj_per_s"] = nt / (best * 1e-3)
+                row[f"{mode}_threads"] = bth
+            rp, rf = res["pruned"], res["full"]
+            row["speedup"] = row["pruned_traj_per_s"] / row["full_traj_per_s"]
+            row["evolved_fraction"] = float(np.mean(rp["explicit_comps"]) / np.mean(rf["explicit_comps"]))
+            row["max_abs_fidelity_diff"] = float(np.max(np.abs(rp["fidelity"] - rf["fidelity"])))
+            row["status_ok"] = bool(np.all(rp["status"] == 0) and np.all(rf["status"] == 0))
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+        sim.close()
+    print(json.dumps({"metric": "pruned and full trajectories/s over n and damping rate", "unit": "trajectories/s",
+                      "data": "synthetic", "config": {"workload": "qubit encoding, k=3, data-loading input, "
+                                                                  "damping only, 4000 trajectories per point"},
+                      "rows": rows}), flush=True)
 
 
 def run_serving(args):
