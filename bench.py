@@ -427,7 +427,19 @@ def main():
     for b in range(0, NTRAJ, BATCH * 4):
         gb.copy_(gam[b:b + BATCH])
         lat.append(1e3 * timed(lambda: sim.run_pruned(base + 9_000_000 + b, gb, ob)))
+    lat_tp = np.array(lat)
+    # the same queries on the latency variant: 1024 threads, one trajectory
+    # per SM (a query ends with its slowest trajectory, which then has a
+    # whole SM's threads for its explicit components)
+    lsim = QramSim(p, seed=SEED, device=local, stream=stream)
+    lsim.set_gamma_bound(G_HI)
+    lsim.set_variant(1024)
+    lat = []
+    for b in range(0, NTRAJ, BATCH * 4):
+        gb.copy_(gam[b:b + BATCH])
+        lat.append(1e3 * timed(lambda: lsim.run_pruned(base + 9_000_000 + b, gb, ob)))
     lat = np.array(lat)
+    lsim.close()
 
     # ---- end to end through the C ABI with host buffers --------------------
     g_pin = torch.tensor(gam_h, dtype=torch.float64).pin_memory()
@@ -498,7 +510,10 @@ def main():
                                                 "and mean fidelity over the completed trajectories", **mixed},
             "mixed_launch": mixed_launch,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "query": "one gamma batch of 1000 trajectories launched alone", "n": int(len(lat))},
+                           "query": "one gamma batch of 1000 trajectories launched alone", "n": int(len(lat)),
+                           "variant_threads": 1024,
+                           "throughput_variant": {"threads": variant, "p50": float(np.percentile(lat_tp, 50)),
+                                                  "p99": float(np.percentile(lat_tp, 99))}},
             "mean_fidelity": float(res["fidelity"].mean()), "status_ok": bool(np.all(res["status"] == 0)),
             "mean_bad_fraction": float(res["bad"].mean() / (1 << N)),
             "e2e": {"value": e2e_val, "unit": "trajectories/s", "h2d_bytes_per_step": int(g_pin.numel() * 8),

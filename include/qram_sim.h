@@ -237,10 +237,14 @@ int qram_batch_launch(qram_batch_t *batch);
 int qram_batch_grid(const qram_batch_t *batch);
 void qram_batch_destroy(qram_batch_t *batch);
 
-/* Launch variant: threads per CTA of the trajectory kernel (128, 256 or
- * 512; default 256).  Results do not depend on it except through the order
- * of floating-point block reductions (rounding).  qram_get_variant returns
- * the current one. */
+/* Launch variant: threads per CTA of the trajectory kernel (128, 256, 512
+ * or 1024; default 256).  128-512 are the throughput variants (several CTAs,
+ * i.e. trajectories, per SM; qram_autotune picks among them).  1024 runs one
+ * trajectory per SM with every thread on it: a launch takes about as long as
+ * its slowest trajectory, so a small query (few trajectories per SM) finishes
+ * sooner, while throughput on large launches is lower.  Results do not
+ * depend on the variant except through the order of floating-point block
+ * reductions (rounding).  qram_get_variant returns the current one. */
 int qram_set_variant(qram_sim_t *sim, int threads);
 int qram_get_variant(const qram_sim_t *sim);
 

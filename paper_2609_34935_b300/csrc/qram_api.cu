@@ -675,7 +675,7 @@ int qram_batch_create(qram_sim_t *const *sims, uint32_t nsims, int mode, int thr
     }
     if (total >= 0x7FFFFFFFull) return QRAM_E_ARG;
     if (threads == 0) threads = sims[0]->threads;
-    if (!valid_threads(threads)) return QRAM_E_ARG;
+    if (!valid_threads(threads) || threads > 512) return QRAM_E_ARG;   // (no 1024-thread mixed launch)
     DeviceGuard g(sims[0]->device);
     qram_batch *B = new (std::nothrow) qram_batch();
     if (!B) return QRAM_E_OOM;
@@ -803,10 +803,12 @@ int qram_set_variant(qram_sim_t *S, int threads) {
     if (!S || !valid_threads(threads)) return QRAM_E_ARG;
     if (threads == S->threads) return QRAM_OK;
     DeviceGuard g(S->device);
-    const int b = kernel_blocks_per_sm(threads, S->dyn);
+    const size_t dyn = dyn_smem_bytes(S->n, S->k, threads);   // (1024 threads: a larger block-sum area)
+    const int b = kernel_blocks_per_sm(threads, dyn);
     if (b < 1) return QRAM_E_ARG;
     const bool capped = S->slots < S->sms * S->blocks_per_sm;
     S->threads = threads;
+    S->dyn = dyn;
     S->blocks_per_sm = b;
     S->slots = capped ? std::min(S->slots, S->sms * b) : S->sms * b;
     if (S->scratch) { cudaFreeAsync(S->scratch, S->stream); S->scratch = nullptr; }

@@ -169,9 +169,9 @@ size_t carve_scratch(int enc, int n, int k, int D, int slots, double gmax, int t
 int resident_slots_per_device(int device, int threads, size_t dyn);
 
 int kernel_threads();                                   // default variant
-bool valid_threads(int threads);                        // 128, 256 or 512
+bool valid_threads(int threads);                        // 128, 256, 512 or 1024
 int kernel_blocks_per_sm(int threads, size_t dyn);      // resident CTAs per SM of a variant
 int hist_pad(int n, int k);
-size_t dyn_smem_bytes(int n, int k);
+size_t dyn_smem_bytes(int n, int k, int threads = 512);   // bytes for a variant (at most 512 threads: the same)
 
 }  // namespace qram

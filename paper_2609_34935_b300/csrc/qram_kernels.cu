@@ -121,11 +121,12 @@ __device__ __forceinline__ void mark_leaves(uint32_t *bits, int n, uint32_t v, b
 }
 
 // dynamic shared memory (32-bit words): three exponent histograms, at least
-// the 3 x 512 doubles of a block sum
-__host__ __device__ inline uint32_t dyn_words(int n, int k) {
+// the 3 x max(threads, 512) doubles of a block sum
+__host__ __device__ inline uint32_t dyn_words(int n, int k, int threads = 512) {
     const uint32_t H = (uint32_t)((2 * n + k) * (6 * n + 2 * k - 1) + 1);
     const uint32_t hist = 3u * ((H + 31u) & ~31u);
-    return hist > 3u * 2u * 512u ? hist : 3u * 2u * 512u;
+    const uint32_t part = 3u * 2u * (uint32_t)(threads > 512 ? threads : 512);
+    return hist > part ? hist : part;
 }
 
 // ---------------------------------------------------------------------------
@@ -3248,7 +3249,7 @@ __global__ void __launch_bounds__(NT, MINB) traj_kernel(const __grid_constant__ 
     // 3 exponent histograms of hist_pad bins, or the partials of a block sum;
     // kept zero between uses
     extern __shared__ __align__(16) uint32_t dyn_hist[];
-    for (uint32_t b = threadIdx.x; b < dyn_words(P.n, P.k); b += NT) dyn_hist[b] = 0;
+    for (uint32_t b = threadIdx.x; b < dyn_words(P.n, P.k, NT); b += NT) dyn_hist[b] = 0;
     if (threadIdx.x == 0) S.part = reinterpret_cast<double *>(dyn_hist);
     __syncthreads();
     for (;;) {
@@ -3359,6 +3360,8 @@ static cudaError_t dispatch(int threads, const Params &p, int grid, size_t dyn, 
                            : launch_variant<256, 4, false>(p, grid, dyn, s, occ, blocks);
     case 512: return depol ? launch_variant<512, 2, true>(p, grid, dyn, s, occ, blocks)
                            : launch_variant<512, 2, false>(p, grid, dyn, s, occ, blocks);
+    case 1024: return depol ? launch_variant<1024, 1, true>(p, grid, dyn, s, occ, blocks)
+                            : launch_variant<1024, 1, false>(p, grid, dyn, s, occ, blocks);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -3372,9 +3375,9 @@ int hist_pad(int n, int k) {
     return (H + 31) & ~31;
 }
 
-size_t dyn_smem_bytes(int n, int k) { return (size_t)dyn_words(n, k) * sizeof(uint32_t); }
+size_t dyn_smem_bytes(int n, int k, int threads) { return (size_t)dyn_words(n, k, threads) * sizeof(uint32_t); }
 
-bool valid_threads(int threads) { return threads == 128 || threads == 256 || threads == 512; }
+bool valid_threads(int threads) { return threads == 128 || threads == 256 || threads == 512 || threads == 1024; }
 
 int kernel_threads() { return 256; }
 

@@ -107,6 +107,45 @@ def test_bench_launch_configuration_matches_oracle():
     _cmp(res[pick], _oracle_at(p, seed, pick, gam_h))
 
 
+def test_latency_variant_matches_oracle():
+    """The 1024-thread variant (one trajectory per SM) on single queries of
+    the benchmark problem: 1000 trajectories at one damping rate each, the
+    rates of the benchmark's batches near 1e-3 and 1e-2.  Integer outputs
+    equal the 512-thread variant's bit for bit, fidelities agree within the
+    tolerance, and the trajectories with the most jump sites (explicit sets
+    of thousands of components) match the oracle."""
+    from paper_2609_34935_b300 import QramSim
+    n, k, seed = 12, 4, 4001
+    p = W.data_loading(W.QUBIT, n, k, seed=seed)
+    gam_all = W.gamma_batches(100_000, 1000, 1e-5, 1e-2, seed=seed)
+    rates = gam_all[::1000]
+    sim = _sim(p, seed)
+    sim.set_gamma_bound(1e-2)
+    ints = ("bad", "ref", "ncand", "explicit_comps", "jumps", "first_jump_slice", "jump_sites", "q_ground", "status")
+    pick_all, gam_pick = [], []
+    for target in (1e-3, 1e-2):
+        b = int(np.argmin(np.abs(np.log(rates / target))))
+        gam_h = gam_all[b * 1000:(b + 1) * 1000]
+        g = torch.tensor(gam_h, dtype=torch.float64, device="cuda:0")
+        got = {}
+        for threads in (512, 1024):
+            sim.set_variant(threads)
+            assert sim.variant == threads
+            got[threads] = QramSim.results(sim.run_pruned(b * 1000, g))
+        a, c = got[512], got[1024]
+        assert np.all(c["status"] == 0)
+        for f in ints:
+            assert np.array_equal(a[f], c[f]), f
+        assert np.max(np.abs(a["fidelity"] - c["fidelity"])) < TOL
+        order = np.argsort(-c["jump_sites"].astype(np.int64), kind="stable")[:12]
+        assert np.all(c["jumps"][order] > 0)
+        pick_all.extend(int(b * 1000 + t) for t in order)
+        gam_pick.append(c[order])
+    sim.close()
+    pick = np.array(pick_all)
+    _cmp(np.concatenate(gam_pick), _oracle_at(p, seed, pick, gam_all))
+
+
 def test_qutrit_n10_graph_launch_matches_oracle():
     n, k, ntraj, seed, gamma = 10, 1, 100_000, 3001, 1e-3
     p = W.data_loading(W.QUTRIT, n, k, seed=seed)

@@ -284,10 +284,10 @@ def test_cuda_graph_replay_matches_direct_launch():
     sim.close()
 
 
-@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("threads", [128, 256, 512, 1024])
 def test_launch_variants_match_oracle(threads):
-    """Every launch variant of the autotuner (threads per CTA) gives the
-    oracle's results."""
+    """Every launch variant (threads per CTA: the autotuner's three and the
+    one-trajectory-per-SM latency variant) gives the oracle's results."""
     p = W.data_loading(W.QUBIT, 5, 3, seed=91)
     g = np.full(300, 2e-2)
     ref = core.run(p, 91, 0, g)
